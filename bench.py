@@ -1,0 +1,340 @@
+"""Benchmark of the fused SymNMF solver step on GB300.
+
+A step is one full solver iteration over the whole matrix: the streamed
+S H product, the fused gradient / optimizer / projection epilogue and the
+fixed-order reductions (objective, KKT, Gram of the new iterate).  The
+default workload is the n=20000, k=32 TPDM matrix stored in FP32 with
+full-batch projected AdaGrad (eta=2.0); S (1.6 GB) is larger than L2, so
+no flush is needed between iterations.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                  [--workload NAME]
+
+Under torchrun each rank solves its own copy of the workload on its own
+GPU (replicas only: the solve has no data-parallel exchange on one box);
+the value is the sum of iterations over ranks divided by the slowest rank's
+time.  ``--impl reference`` times the FP64 CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fused SH-step iters/s, HBM GB/s vs peak; time-to-tol at n=1e5 BF16 vs FP32"
+UNIT = "iters/s"
+
+WORKLOADS = {
+    # name: (generator, n, k, dtype, method, eta)
+    "tpdm_n20000_k32_fp32_adagrad": ("tpdm", 20000, 32, "f32", 0, 2.0),
+    "tpdm_n20000_k32_fp32_rmsprop": ("tpdm", 20000, 32, "f32", 1, 0.05),
+    "corr_n100000_k32_fp32_adagrad": ("corr", 100000, 32, "f32", 0, 2.0),
+    "corr_n100000_k32_bf16_adagrad": ("corr", 100000, 32, "bf16", 0, 2.0),
+}
+DEFAULT = "tpdm_n20000_k32_fp32_adagrad"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def make_input(name, device):
+    import torch
+    import gen
+    kind, n, k, dt, method, eta = WORKLOADS[name]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dt]
+    if kind == "tpdm":
+        inst = gen.tpdm_groups(n=n, groups=32, T=5000, q=0.05, seed=0, device=device,
+                               dtype=tdt, materialize="torch")
+    else:
+        inst = gen.corr_factor(n=n, T=500, seed=0, device=device, dtype=tdt, materialize="torch")
+    S = inst.S
+    mean = float(S.double().mean()) if n <= 30000 else float(S[:4096].double().mean())
+    H0 = gen.init_scaled(mean, n, k, seed=0)
+    return S, H0, inst
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(int(x.get("num_threads", 1)) for x in info)
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def oracle_rate(S64, H0, method, eta, budget_s=15.0, min_iters=2, max_iters=None):
+    """Iterations/s of the FP64 oracle on the host cores (bounded sample)."""
+    from oracle import symnmf_oracle as O
+    hp = O.HParams.paper(method)
+    hp.eta = eta
+    hp.tau_g = 1e-30
+    s = O.Solver(S64, H0, hp)
+    s.step()  # warm-up (first touch of S)
+    t0 = time.perf_counter()
+    it = 0
+    while True:
+        s.step()
+        it += 1
+        el = time.perf_counter() - t0
+        if (it >= min_iters and el >= budget_s) or (max_iters and it >= max_iters):
+            break
+    return it / el, it, el
+
+
+def run_native(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2607_24518_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2607_24518_gb300 import symnmf as L
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    kind, n, k, dt, method, eta = WORKLOADS[args.workload]
+    S, H0, inst = make_input(args.workload, dev)
+    dtype = L.F32 if dt == "f32" else L.BF16
+    H0_t = torch.tensor(H0, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = L.symnmf_create(S, n, k, dtype)
+    L.symnmf_set_stream(h, stream)
+    hp = L.symnmf_hparams_default(method, eta=eta, tau_g=1e-30)  # never stop early: fixed work
+    L.symnmf_set_H(h, H0_t)
+    L.symnmf_step(h, hp, args.warmup)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank) if rank == 0 else None
+    time.sleep(0.3 if clocks else 0)
+    L.symnmf_set_profiling(h, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    status, st = L.symnmf_step(h, hp, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prod_ms, prod_launches, prod_bytes = L.symnmf_get_profile(h)
+    L.symnmf_set_profiling(h, False)
+    ck = clocks.stop() if clocks else None
+    iters = int(st.iter) - args.warmup
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        it_t = torch.tensor([iters], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(it_t)
+        total_iters = int(it_t.item())
+    else:
+        total_iters = iters
+    impl = L.symnmf_get_impl(h)
+
+    # end to end through the public API with host buffers: every e2e step
+    # uploads S and H0 from pinned memory, runs one check interval (10
+    # iterations) and reads H and the record back
+    e2e = None
+    if rank == 0:
+        S_host = S.cpu().pin_memory()
+        H_host = H0_t.cpu().pin_memory()
+        H_out = torch.empty_like(H_host).pin_memory()
+        S_dev = torch.empty_like(S)
+        H_dev = torch.empty_like(H0_t)
+        H_res = torch.empty_like(H0_t)
+        he = L.symnmf_create(S_dev, n, k, dtype)
+        L.symnmf_set_stream(he, stream)
+        per = 10
+        reps = max(2, min(5, args.steps // per))
+        for rep in range(reps + 1):
+            if rep == 1:
+                torch.cuda.synchronize()
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+            S_dev.copy_(S_host, non_blocking=True)
+            H_dev.copy_(H_host, non_blocking=True)
+            L.symnmf_set_H(he, H_dev)
+            L.symnmf_step(he, hp, per)
+            L.symnmf_get_H(he, H_res)
+            H_out.copy_(H_res, non_blocking=True)
+            stream.synchronize()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = a0.elapsed_time(a1)
+        L.symnmf_destroy(he)
+        e2e = {"value": reps * per / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(S.numel() * S.element_size() + H0_t.numel() * 4) // per,
+               "d2h_bytes_per_step": int(H0_t.numel() * 4 + 72) // per,
+               "note": "per 10-iteration solve: S and H0 uploaded from pinned host memory, "
+                       "H and diagnostics read back; bytes shown per iteration"}
+        del S_host
+    L.symnmf_destroy(h)
+
+    out = None
+    if rank == 0:
+        peak, src = peaks()
+        per_launch_ms = prod_ms / max(1, prod_launches)
+        per_launch_bytes = prod_bytes / max(1, prod_launches)
+        achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
+        traffic = None
+        prof_json = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(prof_json):
+            tj = json.load(open(prof_json))
+            key = f"{args.workload}:{['', 'simt', 'tc'][impl]}"
+            if key in tj:
+                traffic = tj[key]
+        cpu = None
+        if args.cpu_baseline:
+            S64 = S.double().cpu().numpy()
+            rate, it, el = oracle_rate(S64, H0_t.double().cpu().numpy(), method, eta,
+                                       budget_s=args.cpu_budget)
+            del S64
+            cpu = {"value": rate, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                   "sample": f"{it} FP64 oracle iterations of the same workload ({el:.1f} s, "
+                             "numpy float64 on the host cores)"}
+        out = {
+            "metric": METRIC, "value": total_iters / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / max(1, iters),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f32": "f32", "bf16": "bf16"}[dt] + " storage, f32 accumulate, f64 reductions",
+            "data": "synthetic (seeded TPDM / correlation generator)",
+            "config": {"workload": args.workload, "n": n, "k": k, "method": ["adagrad", "rmsprop"][method],
+                       "eta": eta, "storage": dt, "l2": "S larger than L2 (no flush needed)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "product_impl": ["", "simt", "tcgen05"][impl]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": src,
+                         "kernel": "S H product", "bytes_per_launch": per_launch_bytes,
+                         "ms_per_launch": per_launch_ms, "frac_of_8TBps_nominal": achieved / 8000.0},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": ck,
+            "gpu_launches": int(prod_launches) * 4,
+            "status": L.symnmf_status_string(status),
+        }
+    return out
+
+
+def run_reference(args, rank):
+    """The FP64 CPU oracle on the same workload, bounded per step."""
+    if rank != 0:
+        return None
+    import torch
+    import numpy as np
+    kind, n, k, dt, method, eta = WORKLOADS[args.workload]
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    S, H0, inst = make_input(args.workload, dev)
+    S64 = S.double().cpu().numpy()
+    H0_64 = torch.tensor(H0, dtype=torch.float32).double().numpy()
+    del S
+    from oracle import symnmf_oracle as O
+    hp = O.HParams.paper(method)
+    hp.eta = eta
+    hp.tau_g = 1e-30
+    s = O.Solver(S64, H0_64, hp)
+    for _ in range(args.warmup):
+        s.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step()
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded TPDM / correlation generator)",
+            "config": {"workload": args.workload, "n": n, "k": k, "storage": dt},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} timed FP64 oracle iterations after {args.warmup} warm-up"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_native(args, rank, world, local_rank)
+    if out:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * symnmf.h -- C ABI of the GB300 SymNMF solver hot path.
+ *
+ * Problem (Sec. 2, Eq. 1): given a symmetric, entrywise non-negative
+ * S in R^{n x n}, minimise f(H) = ||S - H H^T||_F^2 over H in R_+^{n x k}.
+ * The library evaluates f through the trace identity of Eq. 2,
+ *     f(H) = ||S||_F^2 - 2 tr(H^T S H) + ||H^T H||_F^2,
+ * and the gradient of Sec. 2.1, grad f = 4 (H (H^T H) - S H), without ever
+ * forming an n x n intermediate, and runs the projected adaptive solvers of
+ * the appendix (Family 3) with the stopping rule of Sec. 4.1.
+ *
+ * Conventions shared by every call:
+ *  - Device pointers are CUDA device addresses on the current device; host
+ *    pointers are ordinary process memory.  Each argument says which.
+ *  - S is BORROWED: the caller keeps it alive and unmodified until
+ *    symnmf_destroy.  It is never copied.  Every other buffer (H ping-pong,
+ *    optimizer state, snapshot, partial sums, diagnostics) is owned by the
+ *    handle and freed by symnmf_destroy.
+ *  - Work is ordered on the handle's stream (symnmf_set_stream; default the
+ *    legacy default stream).  Calls that return host scalars synchronise
+ *    that stream before returning; the others only enqueue.
+ *  - Every call returns a symnmf_status; nothing throws across the ABI.
+ *    SYMNMF_ERR_INVALID / SYMNMF_ERR_UNSUPPORTED leave the handle unchanged
+ *    and usable.  SYMNMF_ERR_CUDA, _TIMEOUT and _NONFINITE put the handle in
+ *    an error state in which solver calls return SYMNMF_ERR_STATE until
+ *    symnmf_set_H or symnmf_set_state.  symnmf_last_error gives the text.
+ *  - Handles are not thread-safe; distinct handles may be used from
+ *    distinct threads.
+ */
+#ifndef SYMNMF_H
+#define SYMNMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct symnmf_ctx *symnmf_t;
+
+/* Storage type of S.  FP32: 4-byte IEEE.  BF16: bfloat16.  FP8E4M3: OCP
+ * E4M3 (bias 7, max 448) with one FP32 scale per 128 x 128 tile, so that
+ * S_ij = scale[i/128][j/128] * q_ij (symnmf_set_tile_scales). */
+enum symnmf_dtype { SYMNMF_F32 = 0, SYMNMF_BF16 = 1, SYMNMF_FP8E4M3 = 2 };
+
+/* Solvers (appendix, Family 3; Sec. 5.1). */
+enum symnmf_method {
+  SYMNMF_ADAGRAD = 0,             /* G += g*g; H = [H - eta g/(sqrt(G)+eps)]_+      */
+  SYMNMF_RMSPROP = 1,             /* v = a v + (1-a) g*g; m = mu m + eta g/(sqrt(v)+eps); H = [H - m]_+ */
+  SYMNMF_PIECEWISE_ADAGRAD = 2,   /* AdaGrad + stagnation-triggered accumulator reset */
+  SYMNMF_ROW_SVRG = 3,            /* fresh rows on sampled I, snapshot mu elsewhere   */
+  SYMNMF_BLOCK_SVRG_ADAPTGROW = 4 /* I x J block estimate, snapshot elsewhere, phi growth */
+};
+
+enum symnmf_status {
+  SYMNMF_OK = 0,
+  SYMNMF_CONVERGED = 1,        /* informative: the AND rule (Eq. 11) held at a check */
+  SYMNMF_ERR_INVALID = -1,     /* null pointer, n < 1, bad enum, bad size            */
+  SYMNMF_ERR_UNSUPPORTED = -2, /* k outside 1..64, S row stride not 16-byte aligned for the tensor-core path, ... */
+  SYMNMF_ERR_OOM = -3,         /* a device or pinned allocation failed              */
+  SYMNMF_ERR_CUDA = -4,        /* a CUDA runtime call failed                         */
+  SYMNMF_ERR_TIMEOUT = -5,     /* a bounded device wait gave up                      */
+  SYMNMF_ERR_NONFINITE = -6,   /* a NaN/Inf appeared in the gradient                 */
+  SYMNMF_ERR_STATE = -7        /* the handle is in an error state                    */
+};
+
+/* Handle-owned n x k buffers that tests and checkpoints can read/write.
+ * All are FP32, row-major n x k (row pitch k) in caller memory. */
+enum symnmf_buffer {
+  SYMNMF_BUF_H = 0,        /* current factor H_t                                    */
+  SYMNMF_BUF_ACC = 1,      /* AdaGrad accumulator G (RMSprop: second moment v)      */
+  SYMNMF_BUF_MOM = 2,      /* RMSprop momentum m                                    */
+  SYMNMF_BUF_SNAPSHOT = 3, /* SVRG snapshot mu                                      */
+  SYMNMF_BUF_GRAD = 4      /* gradient g used by the last update (read-only)        */
+};
+
+/* Solver hyper-parameters (appendix, Family 3; Sec. 4.1; Tab. phase2_config).
+ * symnmf_hparams_default fills the paper's Phase-1 anchors. */
+typedef struct symnmf_hparams {
+  int32_t method;          /* enum symnmf_method */
+  int32_t check_interval;  /* delta of Eq. 10 (default 10)                       */
+  int32_t warmup;          /* stagnation suppressed while t < warmup (default 50) */
+  int32_t snapshot_period; /* s: full pass every s iterations (SVRG methods)    */
+  int32_t block_rows;      /* sampling granularity in rows, multiple of 128     */
+  int32_t reserved0;
+  double eta;              /* learning rate                                     */
+  double eps;              /* epsilon of sqrt(G)+eps (AdaGrad 1e-10, RMSprop 1e-8) */
+  double alpha;            /* RMSprop EMA factor                                */
+  double mu;               /* RMSprop momentum                                  */
+  double c;                /* Piecewise reset scale                             */
+  double c_r;              /* Piecewise gradient-margin multiplier              */
+  double row_frac;         /* Row-SVRG |I|/n                                    */
+  double phi0;             /* Block-SVRG initial entry fraction                 */
+  double tau_E;            /* loss gate (Eq. 7), default 0.1                    */
+  double tau_g;            /* KKT gate (Eq. 8); <= 0 selects tau_g(n) of Eq. 9   */
+  double tau_stag;         /* stagnation threshold tau of Eq. 10, default 1e-5  */
+  double growth_kkt_mult;  /* AdaptGrow grows only while KKT > mult * tau_g (3) */
+  uint64_t seed;           /* sampling seed (SplitMix64 counter streams)        */
+} symnmf_hparams;
+
+/* Scalar controller state carried between iterations (part of a checkpoint). */
+typedef struct symnmf_ctrl {
+  int64_t t;               /* next iteration index                              */
+  double E0;               /* E at H_0 (NaN until the first check)              */
+  double E_prev;           /* E at the previous check                           */
+  double phi;              /* Block-SVRG entry fraction                         */
+  double sumA_post;        /* Piecewise: sum(G) right after the last reset       */
+  double E_at_reset;       /* Piecewise: E at the last reset                     */
+  int32_t have_prev;
+  int32_t stag_count;      /* consecutive stagnating checks (AdaptGrow)          */
+  int32_t resets;          /* Piecewise resets fired                             */
+  int32_t resets_enabled;
+  int32_t cooldown;
+  int32_t converged;
+} symnmf_ctrl;
+
+/* One iteration's diagnostics (Sec. 4.1, "At each check interval ..."). f,
+ * E and kkt are those of H_t, the iterate the step started from; they are
+ * NaN for sampled (non-full) iterations. */
+typedef struct symnmf_record {
+  int64_t t;
+  double f, E, kkt;        /* objective, E_t = f/||S||^2, ||grad_proj||_F/(nk)  */
+  double stag_ratio;       /* (E_{t-delta} - E_t)/E_0 at checks, else NaN        */
+  double phi;              /* entry fraction used by iteration t                */
+  double sumA;             /* sum of the accumulator after the update           */
+  int32_t full, check, reset, converged;
+  int32_t nonfinite;       /* NaN/Inf gradient entries seen                     */
+  int32_t reserved;
+} symnmf_record;
+
+typedef struct symnmf_stats {
+  int64_t iter;            /* ctrl.t after the call                             */
+  int64_t last_check;      /* iteration of the last check (-1 if none)          */
+  double f, E, kkt, stag_ratio, phi;  /* at the last check                      */
+  int32_t converged, resets;
+} symnmf_stats;
+
+/* ---------------------------------------------------------------- handles */
+
+/* Create a handle for S (device, n x n, row pitch n elements, dtype) and
+ * rank k.  Computes ||S||_F^2 in FP64 (a single streaming pass; for FP8 at
+ * symnmf_set_tile_scales).  Returns INVALID for n < 1 or null S/out,
+ * UNSUPPORTED for k outside 1..64. */
+int symnmf_create(const void *S, int64_t n, int32_t k, int32_t dtype, symnmf_t *out);
+/* As symnmf_create with an explicit row pitch lds >= n (elements).  The
+ * tensor-core path needs lds * sizeof(element) to be a multiple of 16 bytes
+ * and S 16-byte aligned; otherwise the handle uses the SIMT product. */
+int symnmf_create_ld(const void *S, int64_t n, int64_t lds, int32_t k, int32_t dtype,
+                     symnmf_t *out);
+void symnmf_destroy(symnmf_t h);
+/* stream: a cudaStream_t passed as void* (NULL = legacy default stream). */
+int symnmf_set_stream(symnmf_t h, void *stream);
+/* FP8 only: scales (device, FP32, ceil(n/128) x ceil(n/128), row pitch
+ * ld_scales) with S_ij = scales[i/128][j/128] * q_ij.  Borrowed like S.
+ * Recomputes ||S||^2 from the dequantised values. */
+int symnmf_set_tile_scales(symnmf_t h, const float *scales, int64_t ld_scales);
+/* Override / read ||S||_F^2 used by the objective (e.g. the norm of the
+ * unquantised matrix when S is stored in BF16 or FP8). */
+int symnmf_set_norm(symnmf_t h, double normS2);
+int symnmf_get_norm(symnmf_t h, double *normS2);
+/* Force the product implementation: 0 = automatic, 1 = SIMT, 2 = tensor
+ * core (UNSUPPORTED if the layout does not allow it). */
+int symnmf_set_impl(symnmf_t h, int32_t impl);
+int symnmf_get_impl(symnmf_t h, int32_t *impl);
+
+/* ------------------------------------------------------------ the factor */
+
+/* H (device, FP32, n x k row-major) becomes H_0; optimizer state, snapshot
+ * and controller are reset (G = v = m = mu = 0, t = 0). */
+int symnmf_set_H(symnmf_t h, const float *H);
+/* Copy the current factor to H (device, FP32, n x k). */
+int symnmf_get_H(symnmf_t h, float *H);
+/* Read / write one handle buffer (enum symnmf_buffer) from / to device
+ * memory (FP32 n x k).  Writing SYMNMF_BUF_H replaces H_t without touching
+ * the optimizer state (teacher forcing); SYMNMF_BUF_GRAD is read-only. */
+int symnmf_get_buffer(symnmf_t h, int32_t which, float *dst);
+int symnmf_set_buffer(symnmf_t h, int32_t which, const float *src);
+int symnmf_get_ctrl(symnmf_t h, symnmf_ctrl *out);
+int symnmf_set_ctrl(symnmf_t h, const symnmf_ctrl *in);
+
+/* ------------------------------------------------------------ the hot path */
+
+/* G (device, FP32, n x k) = 4 (H (H^T H) - S H) at the current H (Sec. 2.1).
+ * No state changes. */
+int symnmf_grad(symnmf_t h, float *G);
+/* f (host) = ||S||^2 - 2 tr(H^T S H) + ||H^T H||^2 at the current H (Eq. 2),
+ * tr and the Gram reduced in FP64 across tiles; E (host) = f / ||S||^2.
+ * Either pointer may be NULL. */
+int symnmf_objective(symnmf_t h, double *f, double *E);
+/* Fill hp with the paper's anchors for method (appendix; Sec. 5.1). */
+int symnmf_hparams_default(int32_t method, symnmf_hparams *hp);
+/* Run up to iters iterations of hp->method from the handle's state.  Checks
+ * (every check_interval iterations) evaluate the AND rule of Eq. 11 and the
+ * method's control (Piecewise reset, AdaptGrow growth).  Returns
+ * SYMNMF_CONVERGED when the rule holds; the handle's H is then the certified
+ * iterate H_t.  stats (host) may be NULL. */
+int symnmf_step(symnmf_t h, const symnmf_hparams *hp, int32_t iters, symnmf_stats *stats);
+/* Step count handles together: each iteration of every handle is launched
+ * back to back on each handle's own stream, sharing one host loop.  hps and
+ * outs are arrays of count (outs may be NULL).  Returns the first error, or
+ * SYMNMF_OK; per-handle convergence is in outs[i].converged. */
+int symnmf_batch_step(symnmf_t *hs, int32_t count, const symnmf_hparams *hps, int32_t iters,
+                      symnmf_stats *outs);
+/* Time every product-kernel launch (the S H stream, the dominant kernel)
+ * with a CUDA event pair on the handle's stream.  enable != 0 starts a new
+ * accumulation; enable == 0 stops recording. */
+int symnmf_set_profiling(symnmf_t h, int32_t enable);
+/* Synchronise the stream and return the accumulated product-kernel time in
+ * milliseconds (host), the number of timed launches, and the algorithmic
+ * bytes of S those launches streamed (rows x columns x element size). */
+int symnmf_get_profile(symnmf_t h, double *product_ms, int64_t *launches, double *s_bytes);
+/* Copy up to max per-iteration records (oldest first) to out (host) and the
+ * number available to *count.  The handle keeps the last 1<<20 records. */
+int symnmf_get_trace(symnmf_t h, symnmf_record *out, int64_t max, int64_t *count);
+
+/* ------------------------------------------------------------ checkpoints */
+
+/* Size in bytes of a checkpoint blob (controller + H, G/v, m, mu). */
+int symnmf_state_bytes(symnmf_t h, size_t *bytes);
+/* Serialise into / restore from a host buffer of symnmf_state_bytes bytes.
+ * Restoring clears an error state. */
+int symnmf_get_state(symnmf_t h, void *buf, size_t bytes);
+int symnmf_set_state(symnmf_t h, const void *buf, size_t bytes);
+
+const char *symnmf_last_error(symnmf_t h);
+const char *symnmf_status_string(int32_t status);
+
+/* ---------------------------------------------- host-only pure functions */
+
+/* SplitMix64 (Steele, Lea & Flood 2014): the (index+1)-th output of the
+ * generator started at state. */
+uint64_t symnmf_splitmix64(uint64_t state, uint64_t index);
+/* m distinct sorted block indices of 0..nb-1 drawn for iteration t on a
+ * stream (0: Row-SVRG I; 1, 2: Block-SVRG I, J) by a partial Fisher-Yates
+ * shuffle whose d-th swap partner is d + u_d mod (nb - d), u_d the d-th
+ * output started at seed*0x9E3779B97F4A7C15 + t*0xBF58476D1CE4E5B9 +
+ * stream*0x94D049BB133111EB.  out (host) holds m entries. */
+int symnmf_sample_blocks(uint64_t seed, int64_t t, int32_t stream, int64_t nb, int64_t m,
+                         int64_t *out);
+/* The controller's decision at a check (Sec. 4.1 AND rule; Piecewise reset
+ * and AdaptGrow growth control), as a pure function for replay: updates
+ * *c in place given iteration t, E_t, the KKT norm, sum(G) and the lower
+ * median of g_t^2.  decisions[0..2] (host) receive converged, reset, grow;
+ * *stag_ratio the stagnation ratio (may be NULL). */
+int symnmf_controller_check(symnmf_ctrl *c, const symnmf_hparams *hp, int64_t n, int64_t t,
+                            double E, double kkt, double sumA, double median_g2,
+                            int32_t *decisions, double *stag_ratio);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYMNMF_H */

@@ -237,6 +237,51 @@ def stopping_rule(ctrl: Ctrl, hp: HParams, n: int, t: int, E: float, kkt: float)
     return converged, stagnating, ratio
 
 
+def controller_check(c: Ctrl, hp: HParams, n: int, t: int, E: float, kkt: float,
+                     sumA: float, median_fn) -> CheckResult:
+    """Scalar decisions at a check iteration t (t % delta == 0).
+
+    E_0 is taken at the first check.  The AND rule of Eq. 11 decides
+    convergence.  Piecewise AdaGrad (Sec. 5.1; appendix): the cooldown
+    after a reset lasts until sum(G) reaches twice its post-reset value;
+    a reset fires on stagnation while ||grad_proj||/(nk) > c_r tau_g and
+    median(g_t^2) > eps, unless the previous reset brought no measurable
+    loss reduction (E_t >= E_at_reset - tau E_0), which disables resets for
+    good.  AdaptGrow: phi <- min(2 phi, 1) after 3 consecutive stagnating
+    checks while ||grad_proj||/(nk) > growth_kkt_mult tau_g.  The caller
+    applies the reset to G and sets c.sumA_post.
+    """
+    if t == 0 or not (c.E0 == c.E0):
+        c.E0 = E
+    conv, stag, ratio = stopping_rule(c, hp, n, t, E, kkt)
+    out = CheckResult(converged=conv, stagnating=stag, stag_ratio=ratio)
+    if conv:
+        c.converged = True
+        return out
+    tau_g = hp.tau_g if hp.tau_g > 0 else tau_g_default(n)
+    if hp.method == PIECEWISE:
+        if c.cooldown and sumA >= 2.0 * c.sumA_post:
+            c.cooldown = False
+        if not c.cooldown and c.resets_enabled and stag and kkt > hp.c_r * tau_g:
+            med = median_fn()
+            if med > hp.eps:
+                if c.resets > 0 and not (E < c.E_at_reset - hp.tau_stag * c.E0):
+                    c.resets_enabled = False
+                else:
+                    out.reset = True
+                    c.cooldown = True
+                    c.E_at_reset = E
+                    c.resets += 1
+    if hp.method == BLOCK_SVRG:
+        c.stag_count = c.stag_count + 1 if stag else 0
+        if c.stag_count >= 3 and kkt > hp.growth_kkt_mult * tau_g and c.phi < 1.0:
+            c.phi = min(2.0 * c.phi, 1.0)
+            c.stag_count = 0
+            out.grow = True
+    c.E_prev, c.have_prev = E, True
+    return out
+
+
 # --------------------------------------------------------------------------
 # the solver
 # --------------------------------------------------------------------------
@@ -366,44 +411,16 @@ class Solver:
         return rec
 
     def _check(self, rec, g, H_t):
-        hp, c = self.hp, self.ctrl
-        t = rec.t
-        if t == 0 or not (c.E0 == c.E0):
-            c.E0 = rec.E
-        conv, stag, ratio = stopping_rule(c, hp, self.n, t, rec.E, rec.kkt)
-        rec.stag_ratio = ratio
-        if conv:
-            rec.converged = c.converged = True
-            return
-        tau_g = hp.tau_g if hp.tau_g > 0 else tau_g_default(self.n)
-        if hp.method == PIECEWISE:
-            self._piecewise(rec, g, stag, tau_g)
-        if hp.method == BLOCK_SVRG:
-            c.stag_count = c.stag_count + 1 if stag else 0
-            if c.stag_count >= 3 and rec.kkt > hp.growth_kkt_mult * tau_g and c.phi < 1.0:
-                c.phi = min(2.0 * c.phi, 1.0)
-                c.stag_count = 0
-        c.E_prev, c.have_prev = rec.E, True
-
-    def _piecewise(self, rec, g, stag, tau_g):
-        """Stagnation-triggered accumulator reset (Sec. 5.1; Appendix)."""
-        hp, c = self.hp, self.ctrl
-        if c.cooldown and float(np.sum(self.A)) >= 2.0 * c.sumA_post:
-            c.cooldown = False
-        if c.cooldown or not c.resets_enabled or not stag or not (rec.kkt > hp.c_r * tau_g):
-            return
-        med = lower_median(g * g)
-        if not (med > hp.eps):
-            return
-        if c.resets > 0 and not (rec.E < c.E_at_reset - hp.tau_stag * c.E0):
-            c.resets_enabled = False
-            return
-        self.A = np.maximum(hp.c * g * g, hp.c * med)
-        c.sumA_post = float(np.sum(self.A))
-        c.cooldown = True
-        c.E_at_reset = rec.E
-        c.resets += 1
-        rec.reset = True
+        out = controller_check(self.ctrl, self.hp, self.n, rec.t, rec.E, rec.kkt,
+                               float(np.sum(self.A)), lambda: lower_median(g * g))
+        rec.stag_ratio = out.stag_ratio
+        rec.converged = out.converged
+        if out.reset:
+            # G_i <- max(c g_i^2, c median(g^2)) (appendix, Piecewise AdaGrad)
+            med = lower_median(g * g)
+            self.A = np.maximum(self.hp.c * g * g, self.hp.c * med)
+            self.ctrl.sumA_post = float(np.sum(self.A))
+            rec.reset = True
 
     def run(self, iters):
         for _ in range(iters):

@@ -1,0 +1,1046 @@
+// Host runtime of libsymnmf: handle lifecycle, the per-iteration launch
+// sequence, the scalar controller (Sec. 4.1 AND rule; Piecewise reset and
+// AdaptGrow growth control of Sec. 5.1 and the appendix), counter-based
+// sampling of row blocks, and checkpoints.  Every arithmetic step of the
+// solver runs in the kernels; this file only orders launches and makes the
+// scalar decisions at check iterations.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <string>
+#include <vector>
+
+#include "../../include/symnmf.h"
+#include "symnmf_internal.h"
+
+using namespace symnmf;
+
+namespace {
+
+constexpr int kStages = 8;          // pinned/device staging slots for sampled lists
+constexpr size_t kTraceCap = 1u << 20;
+constexpr uint64_t kMagic = 0x31764D4E4D59534EULL;  // "NSYMNMv1"
+
+int pad_k(int k) { return k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64; }
+size_t esize(int dtype) { return dtype == SYMNMF_F32 ? 4 : dtype == SYMNMF_BF16 ? 2 : 1; }
+
+}  // namespace
+
+struct symnmf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  const void *S = nullptr;
+  int64_t n = 0, lds = 0;
+  int k = 0, kp = 0, dtype = 0;
+  const float *scales = nullptr;
+  int64_t ld_scales = 0;
+  double normS2 = NAN;
+  int ntiles = 0;
+  int64_t ldb = 0;
+  int num_sms = 0;
+  int impl_req = 0;   // 0 auto, 1 simt, 2 tc
+  bool tc_layout_ok = false;
+  // owned device memory
+  float *H[2] = {nullptr, nullptr};
+  uint16_t *Bt[2] = {nullptr, nullptr};
+  float *gram_part[2] = {nullptr, nullptr};
+  double *gram64[2] = {nullptr, nullptr};
+  float *gram32[2] = {nullptr, nullptr};
+  int cur = 0;
+  float *A = nullptr, *M = nullptr, *mu = nullptr, *g = nullptr, *tmp = nullptr;
+  float *P = nullptr, *Q = nullptr;
+  int64_t pq_cap_tiles = 0;
+  double *slots = nullptr, *chunk = nullptr;
+  int nchunks = 1;
+  float *gramI = nullptr, *gramJ = nullptr;
+  int *dlists = nullptr;    // kStages x 4 x ntiles
+  int *hlists = nullptr;    // pinned mirror
+  cudaEvent_t stage_ev[kStages] = {};
+  bool stage_used[kStages] = {};
+  DevRecord *ring = nullptr;  // kRing + 1 (last = scratch)
+  DevRecord *hring = nullptr; // pinned
+  unsigned *hist = nullptr, *sel = nullptr;
+  float *dmed = nullptr;
+  double *dsum = nullptr, *hsum = nullptr;  // dsum[0..3], pinned hsum
+  float *hmed = nullptr;
+  double *norm_parts = nullptr;
+  int n_norm_parts = 0;
+  // host state
+  symnmf_ctrl ctrl{};
+  std::deque<symnmf_record> trace;
+  int64_t copied_upto = 0;
+  std::string err;
+  bool bad = false;
+  int64_t last_check = -1;
+  symnmf_record last_check_rec{};
+  // product-kernel timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_ev;   // pairs
+  size_t prof_used = 0;                // events used (2 per launch)
+  double prof_bytes = 0.0;
+};
+
+namespace {
+
+int fail(symnmf_t h, int status, const std::string &msg) {
+  if (h) {
+    h->err = msg;
+    if (status == SYMNMF_ERR_CUDA || status == SYMNMF_ERR_TIMEOUT ||
+        status == SYMNMF_ERR_NONFINITE)
+      h->bad = true;
+  }
+  return status;
+}
+
+int cuda_fail(symnmf_t h, cudaError_t e, const char *where) {
+  return fail(h, SYMNMF_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                     \
+  do {                                                               \
+    cudaError_t e_ = (call);                                         \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);           \
+  } while (0)
+
+void reset_ctrl(symnmf_ctrl *c) {
+  std::memset(c, 0, sizeof(*c));
+  c->t = 0;
+  c->E0 = NAN;
+  c->E_prev = NAN;
+  c->phi = 1.0;
+  c->E_at_reset = NAN;
+  c->resets_enabled = 1;
+}
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+  cudaError_t e = cudaMalloc((void **)p, std::max<size_t>(1, count) * sizeof(T));
+  if (e == cudaSuccess) e = cudaMemset(*p, 0, std::max<size_t>(1, count) * sizeof(T));
+  return e;
+}
+
+void free_all(symnmf_t h) {
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(h->H[i]);
+    cudaFree(h->Bt[i]);
+    cudaFree(h->gram_part[i]);
+    cudaFree(h->gram64[i]);
+    cudaFree(h->gram32[i]);
+  }
+  for (void *p : {(void *)h->A, (void *)h->M, (void *)h->mu, (void *)h->g, (void *)h->tmp,
+                  (void *)h->P, (void *)h->Q, (void *)h->slots, (void *)h->chunk,
+                  (void *)h->gramI, (void *)h->gramJ, (void *)h->dlists, (void *)h->ring,
+                  (void *)h->hist, (void *)h->sel, (void *)h->dmed, (void *)h->dsum,
+                  (void *)h->norm_parts})
+    cudaFree(p);
+  for (void *p : {(void *)h->hlists, (void *)h->hring, (void *)h->hsum, (void *)h->hmed})
+    if (p) cudaFreeHost(p);
+  for (int i = 0; i < kStages; ++i)
+    if (h->stage_ev[i]) cudaEventDestroy(h->stage_ev[i]);
+  for (cudaEvent_t ev : h->prof_ev) cudaEventDestroy(ev);
+}
+
+cudaError_t prof_event(symnmf_t h, cudaEvent_t *ev) {
+  if (h->prof_used >= h->prof_ev.size()) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    h->prof_ev.push_back(e);
+  }
+  *ev = h->prof_ev[h->prof_used++];
+  return cudaSuccess;
+}
+
+bool use_tc(symnmf_t h) {
+  if (h->impl_req == 1) return false;
+  return h->tc_layout_ok && tc_supported(h->dtype, h->kp);
+}
+
+int compute_norm(symnmf_t h) {
+  CK(launch_norm_s2(h->S, h->n, h->lds, h->dtype, h->scales, h->ld_scales, h->norm_parts,
+                    h->n_norm_parts, h->dsum, h->stream));
+  CK(cudaMemcpyAsync(h->hsum, h->dsum, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->normS2 = h->hsum[0];
+  return SYMNMF_OK;
+}
+
+// Bt copy, per-tile Gram partials and the reduced Gram of H[cur]
+int refresh_derived(symnmf_t h) {
+  const int c = h->cur;
+  CK(launch_prepare_tiles(h->H[c], h->n, h->k, h->kp, h->Bt[c], h->ldb, h->gram_part[c],
+                          h->stream));
+  CK(launch_reduce(nullptr, h->gram_part[c], h->ntiles, h->kp, h->k, h->n, h->normS2, 0, 0,
+                   h->chunk, h->nchunks, h->gram64[c], h->gram64[c], h->gram32[c], nullptr,
+                   h->stream));
+  return SYMNMF_OK;
+}
+
+// --------------------------------------------------------------- sampling
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
+
+void sample(uint64_t seed, int64_t t, int stream, int64_t nb, int64_t m, std::vector<int64_t> &out) {
+  m = std::min(m, nb);
+  std::vector<int64_t> perm(nb);
+  for (int64_t i = 0; i < nb; ++i) perm[i] = i;
+  const uint64_t st = seed * kGamma + (uint64_t)t * 0xBF58476D1CE4E5B9ULL +
+                      (uint64_t)stream * 0x94D049BB133111EBULL;
+  for (int64_t d = 0; d < m; ++d) {
+    const uint64_t u = mix64(st + (uint64_t)(d + 1) * kGamma);
+    const int64_t j = d + (int64_t)(u % (uint64_t)(nb - d));
+    std::swap(perm[d], perm[j]);
+  }
+  out.assign(perm.begin(), perm.begin() + m);
+  std::sort(out.begin(), out.end());
+}
+
+int64_t sample_count(double frac, int64_t n, int64_t block_rows) {
+  const int64_t nb = (n + block_rows - 1) / block_rows;
+  const int64_t rows = (int64_t)std::ceil(frac * (double)n);
+  return std::min(nb, (rows + block_rows - 1) / block_rows);
+}
+
+// ------------------------------------------------------------- controller
+struct CheckOut {
+  bool converged = false, reset = false, grow = false;
+  double ratio = NAN;
+};
+
+template <class MedianFn>
+void ctrl_check(symnmf_ctrl *c, const symnmf_hparams *hp, int64_t n, int64_t t, double E,
+                double kkt, double sumA, MedianFn median, CheckOut *o) {
+  if (t == 0 || !(c->E0 == c->E0)) c->E0 = E;
+  const double tau_g = hp->tau_g > 0 ? hp->tau_g : 1e-4 * std::max(1.0, 1e4 / (double)n);
+  const double ratio = c->have_prev ? (c->E_prev - E) / c->E0 : NAN;
+  const bool stag = c->have_prev && t >= hp->warmup && ratio < hp->tau_stag;
+  o->ratio = ratio;
+  if (E < hp->tau_E && kkt < tau_g && stag) {
+    c->converged = 1;
+    o->converged = true;
+    return;
+  }
+  if (hp->method == SYMNMF_PIECEWISE_ADAGRAD) {
+    if (c->cooldown && sumA >= 2.0 * c->sumA_post) c->cooldown = 0;
+    if (!c->cooldown && c->resets_enabled && stag && kkt > hp->c_r * tau_g) {
+      const double med = median();
+      if (med > hp->eps) {
+        if (c->resets > 0 && !(E < c->E_at_reset - hp->tau_stag * c->E0)) {
+          c->resets_enabled = 0;
+        } else {
+          o->reset = true;
+          c->cooldown = 1;
+          c->E_at_reset = E;
+          c->resets += 1;
+        }
+      }
+    }
+  }
+  if (hp->method == SYMNMF_BLOCK_SVRG_ADAPTGROW) {
+    c->stag_count = stag ? c->stag_count + 1 : 0;
+    if (c->stag_count >= 3 && kkt > hp->growth_kkt_mult * tau_g && c->phi < 1.0) {
+      c->phi = std::min(2.0 * c->phi, 1.0);
+      c->stag_count = 0;
+      o->grow = true;
+    }
+  }
+  c->E_prev = E;
+  c->have_prev = 1;
+}
+
+int validate_hp(const symnmf_hparams *hp) {
+  if (!hp) return SYMNMF_ERR_INVALID;
+  if (hp->method < 0 || hp->method > 4) return SYMNMF_ERR_INVALID;
+  if (hp->check_interval < 1 || hp->snapshot_period < 1 || hp->warmup < 0)
+    return SYMNMF_ERR_INVALID;
+  if (hp->block_rows < kTileRows || hp->block_rows % kTileRows) return SYMNMF_ERR_INVALID;
+  if (!(hp->eta > 0) || !(hp->eps >= 0)) return SYMNMF_ERR_INVALID;
+  if (hp->method == SYMNMF_ROW_SVRG && !(hp->row_frac > 0 && hp->row_frac <= 1))
+    return SYMNMF_ERR_INVALID;
+  if (hp->method == SYMNMF_BLOCK_SVRG_ADAPTGROW && !(hp->phi0 > 0 && hp->phi0 <= 1))
+    return SYMNMF_ERR_INVALID;
+  return SYMNMF_OK;
+}
+
+// ------------------------------------------------------------ iteration
+int stage_slot(symnmf_t h, int64_t t, int **hl, int **dl) {
+  const int s = (int)(t % kStages);
+  if (h->stage_used[s]) CK(cudaEventSynchronize(h->stage_ev[s]));
+  *hl = h->hlists + (size_t)s * 4 * h->ntiles;
+  *dl = h->dlists + (size_t)s * 4 * h->ntiles;
+  return SYMNMF_OK;
+}
+
+int upload_slot(symnmf_t h, int64_t t, int *hl, int *dl) {
+  const int s = (int)(t % kStages);
+  CK(cudaMemcpyAsync(dl, hl, sizeof(int) * 4 * h->ntiles, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaEventRecord(h->stage_ev[s], h->stream));
+  h->stage_used[s] = true;
+  return SYMNMF_OK;
+}
+
+// tile list of the sampled blocks
+void blocks_to_tiles(symnmf_t h, const std::vector<int64_t> &blocks, int64_t block_rows,
+                     std::vector<int> &tiles) {
+  const int bt = (int)(block_rows / kTileRows);
+  tiles.clear();
+  for (int64_t b : blocks)
+    for (int i = 0; i < bt; ++i) {
+      const int64_t tt = b * bt + i;
+      if (tt < h->ntiles) tiles.push_back((int)tt);
+    }
+}
+
+int prod(symnmf_t h, const int *row_list, int n_rows, const int *col_list, int n_cols, float *out,
+         int *nsplit_out) {
+  ProdArgs a{};
+  a.S = h->S;
+  a.lds = h->lds;
+  a.dtype = h->dtype;
+  a.scales = h->scales;
+  a.ld_scales = h->ld_scales;
+  a.n = h->n;
+  a.k = h->k;
+  a.kp = h->kp;
+  a.H = h->H[h->cur];
+  a.Bt = h->Bt[h->cur];
+  a.ldb = h->ldb;
+  a.row_list = row_list;
+  a.n_rows_list = n_rows;
+  a.col_list = col_list;
+  a.n_cols_list = n_cols;
+  a.out = out;
+  const int target = 3 * h->num_sms;
+  int ns = (target + n_rows - 1) / std::max(1, n_rows);
+  ns = std::max(1, std::min(ns, std::min(64, n_cols)));
+  if ((int64_t)ns * n_rows > h->pq_cap_tiles) ns = (int)std::max<int64_t>(1, h->pq_cap_tiles / n_rows);
+  a.nsplit = ns;
+  *nsplit_out = ns;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->profiling) {
+    CK(prof_event(h, &e0));
+    CK(prof_event(h, &e1));
+    CK(cudaEventRecord(e0, h->stream));
+  }
+  cudaError_t e = use_tc(h) ? launch_prod_tc(a, h->stream, h->num_sms) : launch_prod_simt(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "product kernel");
+  if (h->profiling) {
+    CK(cudaEventRecord(e1, h->stream));
+    const double rows = std::min<double>((double)n_rows * kTileRows, (double)h->n);
+    const double cols = std::min<double>((double)n_cols * kTileRows, (double)h->n);
+    h->prof_bytes += rows * cols * (double)esize(h->dtype);
+  }
+  return SYMNMF_OK;
+}
+
+EpiArgs base_epi(symnmf_t h, const symnmf_hparams *hp) {
+  EpiArgs e{};
+  e.n = h->n;
+  e.k = h->k;
+  e.kp = h->kp;
+  e.ntiles = h->ntiles;
+  e.method = hp ? hp->method : 0;
+  e.eta = hp ? (float)hp->eta : 0.f;
+  e.eps = hp ? (float)hp->eps : 0.f;
+  e.alpha = hp ? (float)hp->alpha : 0.f;
+  e.mom = hp ? (float)hp->mu : 0.f;
+  e.H = h->H[h->cur];
+  e.ldb = h->ldb;
+  e.A = h->A;
+  e.M = h->M;
+  e.mu = h->mu;
+  e.coef = 4.f;
+  return e;
+}
+
+bool is_full(symnmf_t h, const symnmf_hparams *hp, int64_t t) {
+  if (hp->method == SYMNMF_ROW_SVRG)
+    return hp->row_frac >= 1.0 || t % hp->snapshot_period == 0 || t % hp->check_interval == 0;
+  if (hp->method == SYMNMF_BLOCK_SVRG_ADAPTGROW)
+    return h->ctrl.phi >= 1.0 || t % hp->snapshot_period == 0 || t % hp->check_interval == 0;
+  return true;
+}
+
+int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t) {
+  const int cur = h->cur, nxt = 1 - cur;
+  const bool full = is_full(h, hp, t);
+  EpiArgs e = base_epi(h, hp);
+  e.Hn = h->H[nxt];
+  e.Btn = h->Bt[nxt];
+  e.gram_part = h->gram_part[nxt];
+  e.slots = h->slots;
+  e.gout = h->g;
+  e.update = 1;
+  int rc;
+  if (full) {
+    int ns = 1;
+    if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ns))) return rc;
+    e.mode = MODE_FULL;
+    e.gram = h->gram32[cur];
+    e.P = h->P;
+    e.nsplit = ns;
+    e.n1 = h->ntiles;
+    e.store_mu = (hp->method == SYMNMF_ROW_SVRG || hp->method == SYMNMF_BLOCK_SVRG_ADAPTGROW);
+  } else {
+    int *hl, *dl;
+    if ((rc = stage_slot(h, t, &hl, &dl))) return rc;
+    int *hI = hl, *hJ = hl + h->ntiles, *hposI = hl + 2 * h->ntiles, *hposJ = hl + 3 * h->ntiles;
+    const int64_t br = hp->block_rows;
+    const int64_t nb = (h->n + br - 1) / br;
+    std::vector<int64_t> bI, bJ;
+    std::vector<int> tI, tJ;
+    for (int i = 0; i < h->ntiles; ++i) hposI[i] = hposJ[i] = -1;
+    if (hp->method == SYMNMF_ROW_SVRG) {
+      sample(hp->seed, t, 0, nb, sample_count(hp->row_frac, h->n, br), bI);
+    } else {
+      const int64_t m = sample_count(std::sqrt(h->ctrl.phi), h->n, br);
+      sample(hp->seed, t, 1, nb, m, bI);
+      sample(hp->seed, t, 2, nb, m, bJ);
+    }
+    blocks_to_tiles(h, bI, br, tI);
+    blocks_to_tiles(h, bJ, br, tJ);
+    for (size_t i = 0; i < tI.size(); ++i) {
+      hI[i] = tI[i];
+      hposI[tI[i]] = (int)i;
+    }
+    for (size_t i = 0; i < tJ.size(); ++i) {
+      hJ[i] = tJ[i];
+      hposJ[tJ[i]] = (int)i;
+    }
+    if ((rc = upload_slot(h, t, hl, dl))) return rc;
+    int *dI = dl, *dJ = dl + h->ntiles, *dposI = dl + 2 * h->ntiles, *dposJ = dl + 3 * h->ntiles;
+    if (hp->method == SYMNMF_ROW_SVRG) {
+      int ns = 1;
+      if ((rc = prod(h, dI, (int)tI.size(), nullptr, h->ntiles, h->P, &ns))) return rc;
+      e.mode = MODE_ROWS;
+      e.gram = h->gram32[cur];
+      e.P = h->P;
+      e.nsplit = ns;
+      e.pos1 = dposI;
+      e.n1 = (int)tI.size();
+    } else {
+      CK(launch_gram_subset(h->gram_part[cur], h->kp, dI, (int)tI.size(), dJ, (int)tJ.size(),
+                            h->gramI, h->gramJ, h->stream));
+      int ns1 = 1, ns2 = 1;
+      if ((rc = prod(h, dI, (int)tI.size(), dJ, (int)tJ.size(), h->P, &ns1))) return rc;
+      if ((rc = prod(h, dJ, (int)tJ.size(), dI, (int)tI.size(), h->Q, &ns2))) return rc;
+      e.mode = MODE_BLOCK;
+      e.coef = 2.f;
+      e.gramI = h->gramI;
+      e.gramJ = h->gramJ;
+      e.P = h->P;
+      e.nsplit = ns1;
+      e.pos1 = dposI;
+      e.n1 = (int)tI.size();
+      e.Q = h->Q;
+      e.nsplit2 = ns2;
+      e.pos2 = dposJ;
+      e.n2 = (int)tJ.size();
+    }
+  }
+  CK(launch_epilogue(e, h->stream));
+  CK(launch_reduce(h->slots, h->gram_part[nxt], h->ntiles, h->kp, h->k, h->n, h->normS2, t,
+                   full ? 1 : 0, h->chunk, h->nchunks, h->gram64[cur], h->gram64[nxt],
+                   h->gram32[nxt], h->ring + (t % kRing), h->stream));
+  h->cur = nxt;
+  return SYMNMF_OK;
+}
+
+symnmf_record to_record(const DevRecord &d, double phi) {
+  symnmf_record r{};
+  r.t = d.t;
+  r.full = d.full;
+  r.f = d.full ? d.f : NAN;
+  r.E = d.full ? d.E : NAN;
+  r.kkt = d.full ? d.kkt : NAN;
+  r.sumA = d.sumA;
+  r.nonfinite = d.nonfinite;
+  r.stag_ratio = NAN;
+  r.phi = phi;
+  return r;
+}
+
+// copy device records [h->copied_upto, upto) into the host trace
+int sync_records(symnmf_t h, int64_t upto, const std::vector<double> &phis) {
+  const int64_t from = h->copied_upto;
+  if (upto <= from) return SYMNMF_OK;
+  int64_t a = from;
+  while (a < upto) {
+    const int64_t s = a % kRing;
+    const int64_t len = std::min<int64_t>(upto - a, kRing - s);
+    CK(cudaMemcpyAsync(h->hring + s, h->ring + s, sizeof(DevRecord) * len,
+                       cudaMemcpyDeviceToHost, h->stream));
+    a += len;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  for (int64_t t = from; t < upto; ++t) {
+    const double phi = (t - from) < (int64_t)phis.size() ? phis[t - from] : h->ctrl.phi;
+    h->trace.push_back(to_record(h->hring[t % kRing], phi));
+    if (h->trace.size() > kTraceCap) h->trace.pop_front();
+  }
+  h->copied_upto = upto;
+  return SYMNMF_OK;
+}
+
+int median_g2(symnmf_t h, double *out) {
+  CK(launch_median_g2(h->g, h->n, h->k, h->kp, h->hist, h->sel, h->dmed, h->stream));
+  CK(cudaMemcpyAsync(h->hmed, h->dmed, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *out = (double)h->hmed[0];
+  return SYMNMF_OK;
+}
+
+int apply_reset(symnmf_t h, const symnmf_hparams *hp) {
+  CK(launch_reset(h->A, h->g, h->dmed, (float)hp->c, h->n, h->k, h->kp, h->slots, h->stream));
+  CK(launch_sum_slot(h->slots, h->ntiles, 2, h->dsum, h->stream));
+  CK(cudaMemcpyAsync(h->hsum, h->dsum, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->ctrl.sumA_post = h->hsum[0];
+  return SYMNMF_OK;
+}
+
+int check_handle(symnmf_t h) {
+  if (!h) return SYMNMF_ERR_INVALID;
+  if (h->bad) return fail(h, SYMNMF_ERR_STATE, "handle is in an error state: " + h->err);
+  if (h->dtype == SYMNMF_FP8E4M3 && !h->scales)
+    return fail(h, SYMNMF_ERR_INVALID, "FP8 storage needs symnmf_set_tile_scales first");
+  return SYMNMF_OK;
+}
+
+void fill_stats(symnmf_t h, symnmf_stats *st) {
+  if (!st) return;
+  std::memset(st, 0, sizeof(*st));
+  st->iter = h->ctrl.t;
+  st->last_check = h->last_check;
+  st->f = h->last_check_rec.f;
+  st->E = h->last_check_rec.E;
+  st->kkt = h->last_check_rec.kkt;
+  st->stag_ratio = h->last_check_rec.stag_ratio;
+  st->phi = h->ctrl.phi;
+  st->converged = h->ctrl.converged;
+  st->resets = h->ctrl.resets;
+}
+
+// one iteration plus its check; returns OK, CONVERGED or an error
+int iterate_once(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &phis) {
+  const int64_t t = h->ctrl.t;
+  if (t == 0 && h->copied_upto == 0 && h->trace.empty())
+    h->ctrl.phi = hp->method == SYMNMF_BLOCK_SVRG_ADAPTGROW ? hp->phi0 : 1.0;
+  phis.push_back(h->ctrl.phi);
+  int rc = run_iteration(h, hp, t);
+  if (rc) return rc;
+  if (t % hp->check_interval == 0) {
+    if ((rc = sync_records(h, t + 1, phis))) return rc;
+    phis.clear();
+    symnmf_record &rec = h->trace.back();
+    if (rec.nonfinite > 0) {
+      h->ctrl.t = t + 1;
+      return fail(h, SYMNMF_ERR_NONFINITE, "non-finite gradient entries at iteration " + std::to_string(t));
+    }
+    CheckOut o;
+    int mrc = SYMNMF_OK;
+    auto med = [&]() {
+      double m = NAN;
+      mrc = median_g2(h, &m);
+      return m;
+    };
+    ctrl_check(&h->ctrl, hp, h->n, t, rec.E, rec.kkt, rec.sumA, med, &o);
+    if (mrc) return mrc;
+    rec.check = 1;
+    rec.stag_ratio = o.ratio;
+    rec.converged = o.converged ? 1 : 0;
+    rec.reset = o.reset ? 1 : 0;
+    h->last_check = t;
+    h->last_check_rec = rec;
+    if (o.converged) {
+      h->cur = 1 - h->cur;  // the certified iterate is H_t (its buffers are intact)
+      return SYMNMF_CONVERGED;
+    }
+    if (o.reset && (rc = apply_reset(h, hp))) return rc;
+  } else if (t + 1 - h->copied_upto >= kRing / 2) {
+    if ((rc = sync_records(h, t + 1, phis))) return rc;
+    phis.clear();
+  }
+  h->ctrl.t = t + 1;
+  return SYMNMF_OK;
+}
+
+}  // namespace
+
+// ====================================================================== API
+extern "C" {
+
+const char *symnmf_status_string(int32_t s) {
+  switch (s) {
+    case SYMNMF_OK: return "ok";
+    case SYMNMF_CONVERGED: return "converged";
+    case SYMNMF_ERR_INVALID: return "invalid argument";
+    case SYMNMF_ERR_UNSUPPORTED: return "unsupported";
+    case SYMNMF_ERR_OOM: return "out of memory";
+    case SYMNMF_ERR_CUDA: return "CUDA error";
+    case SYMNMF_ERR_TIMEOUT: return "device wait timed out";
+    case SYMNMF_ERR_NONFINITE: return "non-finite values";
+    case SYMNMF_ERR_STATE: return "handle in error state";
+    default: return "unknown status";
+  }
+}
+
+const char *symnmf_last_error(symnmf_t h) { return h ? h->err.c_str() : "null handle"; }
+
+int symnmf_hparams_default(int32_t method, symnmf_hparams *hp) {
+  if (!hp || method < 0 || method > 4) return SYMNMF_ERR_INVALID;
+  std::memset(hp, 0, sizeof(*hp));
+  hp->method = method;
+  hp->check_interval = 10;
+  hp->warmup = 50;
+  hp->snapshot_period = 10;
+  hp->block_rows = kTileRows;
+  hp->eta = 2.0;
+  hp->eps = 1e-10;
+  hp->alpha = 0.99;
+  hp->mu = 0.5;
+  hp->c = 10.0;
+  hp->c_r = 10.0;
+  hp->row_frac = 0.5;
+  hp->phi0 = 0.5;
+  hp->tau_E = 0.1;
+  hp->tau_g = 0.0;
+  hp->tau_stag = 1e-5;
+  hp->growth_kkt_mult = 3.0;
+  hp->seed = 0;
+  if (method == SYMNMF_RMSPROP) {
+    hp->eta = 0.05;
+    hp->eps = 1e-8;
+  } else if (method == SYMNMF_PIECEWISE_ADAGRAD) {
+    hp->eta = 1.0;
+  } else if (method == SYMNMF_BLOCK_SVRG_ADAPTGROW) {
+    hp->snapshot_period = 2;  // ~1/phi0
+  }
+  return SYMNMF_OK;
+}
+
+int symnmf_create_ld(const void *S, int64_t n, int64_t lds, int32_t k, int32_t dtype,
+                     symnmf_t *out) {
+  if (!out) return SYMNMF_ERR_INVALID;
+  *out = nullptr;
+  if (!S || n < 1 || lds < n || dtype < 0 || dtype > 2) return SYMNMF_ERR_INVALID;
+  if (k < 1 || k > 64) return SYMNMF_ERR_UNSUPPORTED;
+  if (n > (int64_t)INT32_MAX * kTileRows / 4) return SYMNMF_ERR_UNSUPPORTED;
+  symnmf_ctx *h = new (std::nothrow) symnmf_ctx();
+  if (!h) return SYMNMF_ERR_OOM;
+  h->S = S;
+  h->n = n;
+  h->lds = lds;
+  h->k = k;
+  h->kp = pad_k(k);
+  h->dtype = dtype;
+  h->ntiles = (int)((n + kTileRows - 1) / kTileRows);
+  h->ldb = (int64_t)h->ntiles * kTileRows;
+  h->tc_layout_ok = ((uintptr_t)S % 16 == 0) && ((lds * (int64_t)esize(dtype)) % 16 == 0);
+  reset_ctrl(&h->ctrl);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  const int64_t nkp = n * h->kp;
+  h->pq_cap_tiles = h->ntiles + 3 * (int64_t)std::max(1, h->num_sms);
+  h->nchunks = std::max(1, std::min(h->ntiles, 64));
+  h->n_norm_parts = 4 * std::max(1, h->num_sms);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = dalloc(&h->H[i], nkp);
+    if (e == cudaSuccess) e = dalloc(&h->Bt[i], (size_t)2 * h->kp * h->ldb);
+    if (e == cudaSuccess) e = dalloc(&h->gram_part[i], (size_t)h->ntiles * h->kp * h->kp);
+    if (e == cudaSuccess) e = dalloc(&h->gram64[i], (size_t)h->kp * h->kp);
+    if (e == cudaSuccess) e = dalloc(&h->gram32[i], (size_t)h->kp * h->kp);
+  }
+  if (e == cudaSuccess) e = dalloc(&h->A, nkp);
+  if (e == cudaSuccess) e = dalloc(&h->M, nkp);
+  if (e == cudaSuccess) e = dalloc(&h->mu, nkp);
+  if (e == cudaSuccess) e = dalloc(&h->g, nkp);
+  if (e == cudaSuccess) e = dalloc(&h->tmp, nkp);
+  if (e == cudaSuccess) e = dalloc(&h->P, (size_t)h->pq_cap_tiles * kTileRows * h->kp);
+  if (e == cudaSuccess) e = dalloc(&h->Q, (size_t)h->pq_cap_tiles * kTileRows * h->kp);
+  if (e == cudaSuccess) e = dalloc(&h->slots, (size_t)h->ntiles * kSlotStride);
+  if (e == cudaSuccess) e = dalloc(&h->chunk, (size_t)h->nchunks * (4 + h->kp * h->kp));
+  if (e == cudaSuccess) e = dalloc(&h->gramI, (size_t)h->kp * h->kp);
+  if (e == cudaSuccess) e = dalloc(&h->gramJ, (size_t)h->kp * h->kp);
+  if (e == cudaSuccess) e = dalloc(&h->dlists, (size_t)kStages * 4 * h->ntiles);
+  if (e == cudaSuccess) e = dalloc(&h->ring, (size_t)kRing + 1);
+  if (e == cudaSuccess) e = dalloc(&h->hist, 2048);
+  if (e == cudaSuccess) e = dalloc(&h->sel, 4);
+  if (e == cudaSuccess) e = dalloc(&h->dmed, 1);
+  if (e == cudaSuccess) e = dalloc(&h->dsum, 4);
+  if (e == cudaSuccess) e = dalloc(&h->norm_parts, (size_t)h->n_norm_parts);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hlists, sizeof(int) * kStages * 4 * h->ntiles);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hring, sizeof(DevRecord) * (kRing + 1));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hsum, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hmed, sizeof(float) * 4);
+  for (int i = 0; i < kStages && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&h->stage_ev[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    const int st = (e == cudaErrorMemoryAllocation) ? SYMNMF_ERR_OOM : SYMNMF_ERR_CUDA;
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    return st;
+  }
+  if (dtype != SYMNMF_FP8E4M3) {
+    const int rc = compute_norm(h);
+    if (rc) {
+      free_all(h);
+      delete h;
+      return rc;
+    }
+  }
+  *out = h;
+  return SYMNMF_OK;
+}
+
+int symnmf_create(const void *S, int64_t n, int32_t k, int32_t dtype, symnmf_t *out) {
+  return symnmf_create_ld(S, n, n, k, dtype, out);
+}
+
+void symnmf_destroy(symnmf_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+int symnmf_set_stream(symnmf_t h, void *stream) {
+  if (!h) return SYMNMF_ERR_INVALID;
+  h->stream = (cudaStream_t)stream;
+  return SYMNMF_OK;
+}
+
+int symnmf_set_tile_scales(symnmf_t h, const float *scales, int64_t ld_scales) {
+  if (!h || !scales || ld_scales < h->ntiles) return SYMNMF_ERR_INVALID;
+  if (h->dtype != SYMNMF_FP8E4M3) return fail(h, SYMNMF_ERR_INVALID, "tile scales apply to FP8 storage only");
+  h->scales = scales;
+  h->ld_scales = ld_scales;
+  return compute_norm(h);
+}
+
+int symnmf_set_norm(symnmf_t h, double normS2) {
+  if (!h || !(normS2 > 0) || !std::isfinite(normS2)) return SYMNMF_ERR_INVALID;
+  h->normS2 = normS2;
+  return SYMNMF_OK;
+}
+
+int symnmf_get_norm(symnmf_t h, double *normS2) {
+  if (!h || !normS2) return SYMNMF_ERR_INVALID;
+  *normS2 = h->normS2;
+  return SYMNMF_OK;
+}
+
+int symnmf_set_impl(symnmf_t h, int32_t impl) {
+  if (!h || impl < 0 || impl > 2) return SYMNMF_ERR_INVALID;
+  if (impl == 2 && !(h->tc_layout_ok && tc_supported(h->dtype, h->kp)))
+    return fail(h, SYMNMF_ERR_UNSUPPORTED, "tensor-core product unavailable for this layout");
+  h->impl_req = impl;
+  return SYMNMF_OK;
+}
+
+int symnmf_get_impl(symnmf_t h, int32_t *impl) {
+  if (!h || !impl) return SYMNMF_ERR_INVALID;
+  *impl = use_tc(h) ? 2 : 1;
+  return SYMNMF_OK;
+}
+
+int symnmf_set_H(symnmf_t h, const float *H) {
+  if (!h || !H) return SYMNMF_ERR_INVALID;
+  h->bad = false;
+  h->err.clear();
+  h->cur = 0;
+  CK(launch_pack(H, h->H[0], h->n, h->k, h->kp, h->stream));
+  const size_t bytes = sizeof(float) * h->n * h->kp;
+  CK(cudaMemsetAsync(h->H[1], 0, bytes, h->stream));
+  CK(cudaMemsetAsync(h->A, 0, bytes, h->stream));
+  CK(cudaMemsetAsync(h->M, 0, bytes, h->stream));
+  CK(cudaMemsetAsync(h->mu, 0, bytes, h->stream));
+  CK(cudaMemsetAsync(h->g, 0, bytes, h->stream));
+  reset_ctrl(&h->ctrl);
+  h->trace.clear();
+  h->copied_upto = 0;
+  h->last_check = -1;
+  std::memset(&h->last_check_rec, 0, sizeof(h->last_check_rec));
+  int rc = refresh_derived(h);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  return SYMNMF_OK;
+}
+
+int symnmf_get_H(symnmf_t h, float *H) {
+  if (!h || !H) return SYMNMF_ERR_INVALID;
+  CK(launch_unpack(h->H[h->cur], H, h->n, h->k, h->kp, h->stream));
+  return SYMNMF_OK;
+}
+
+int symnmf_get_buffer(symnmf_t h, int32_t which, float *dst) {
+  if (!h || !dst) return SYMNMF_ERR_INVALID;
+  const float *src = which == SYMNMF_BUF_H ? h->H[h->cur]
+                     : which == SYMNMF_BUF_ACC ? h->A
+                     : which == SYMNMF_BUF_MOM ? h->M
+                     : which == SYMNMF_BUF_SNAPSHOT ? h->mu
+                     : which == SYMNMF_BUF_GRAD ? h->g : nullptr;
+  if (!src) return SYMNMF_ERR_INVALID;
+  CK(launch_unpack(src, dst, h->n, h->k, h->kp, h->stream));
+  return SYMNMF_OK;
+}
+
+int symnmf_set_buffer(symnmf_t h, int32_t which, const float *src) {
+  if (!h || !src) return SYMNMF_ERR_INVALID;
+  float *dst = which == SYMNMF_BUF_H ? h->H[h->cur]
+               : which == SYMNMF_BUF_ACC ? h->A
+               : which == SYMNMF_BUF_MOM ? h->M
+               : which == SYMNMF_BUF_SNAPSHOT ? h->mu : nullptr;
+  if (!dst) return SYMNMF_ERR_INVALID;
+  CK(launch_pack(src, dst, h->n, h->k, h->kp, h->stream));
+  if (which == SYMNMF_BUF_H) {
+    int rc = refresh_derived(h);
+    if (rc) return rc;
+  }
+  return SYMNMF_OK;
+}
+
+int symnmf_get_ctrl(symnmf_t h, symnmf_ctrl *out) {
+  if (!h || !out) return SYMNMF_ERR_INVALID;
+  *out = h->ctrl;
+  return SYMNMF_OK;
+}
+
+int symnmf_set_ctrl(symnmf_t h, const symnmf_ctrl *in) {
+  if (!h || !in || in->t < 0) return SYMNMF_ERR_INVALID;
+  h->ctrl = *in;
+  h->copied_upto = in->t;
+  return SYMNMF_OK;
+}
+
+int symnmf_grad(symnmf_t h, float *G) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!G) return SYMNMF_ERR_INVALID;
+  int ns = 1;
+  if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ns))) return rc;
+  EpiArgs e = base_epi(h, nullptr);
+  e.mode = MODE_GRAD_ONLY;
+  e.gram = h->gram32[h->cur];
+  e.P = h->P;
+  e.nsplit = ns;
+  e.n1 = h->ntiles;
+  e.gcaller = G;
+  CK(launch_epilogue(e, h->stream));
+  return SYMNMF_OK;
+}
+
+int symnmf_objective(symnmf_t h, double *f, double *E) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  int ns = 1;
+  if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ns))) return rc;
+  EpiArgs e = base_epi(h, nullptr);
+  e.mode = MODE_GRAD_ONLY;
+  e.gram = h->gram32[h->cur];
+  e.P = h->P;
+  e.nsplit = ns;
+  e.n1 = h->ntiles;
+  e.slots = h->slots;
+  CK(launch_epilogue(e, h->stream));
+  CK(launch_reduce(h->slots, nullptr, h->ntiles, h->kp, h->k, h->n, h->normS2, -1, 1, h->chunk,
+                   h->nchunks, h->gram64[h->cur], nullptr, nullptr, h->ring + kRing, h->stream));
+  CK(cudaMemcpyAsync(h->hring + kRing, h->ring + kRing, sizeof(DevRecord),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (f) *f = h->hring[kRing].f;
+  if (E) *E = h->hring[kRing].E;
+  return SYMNMF_OK;
+}
+
+int symnmf_step(symnmf_t h, const symnmf_hparams *hp, int32_t iters, symnmf_stats *stats) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if ((rc = validate_hp(hp))) return fail(h, rc, "invalid hyper-parameters");
+  if (iters < 0) return fail(h, SYMNMF_ERR_INVALID, "iters < 0");
+  std::vector<double> phis;
+  rc = SYMNMF_OK;
+  for (int32_t i = 0; i < iters; ++i) {
+    rc = iterate_once(h, hp, phis);
+    if (rc) break;
+  }
+  if (rc == SYMNMF_OK || rc == SYMNMF_CONVERGED) {
+    const int64_t upto = h->ctrl.converged && rc == SYMNMF_CONVERGED ? h->ctrl.t + 1 : h->ctrl.t;
+    int rc2 = sync_records(h, std::max(upto, h->copied_upto), phis);
+    if (rc2) rc = rc2;
+  }
+  fill_stats(h, stats);
+  return rc;
+}
+
+int symnmf_batch_step(symnmf_t *hs, int32_t count, const symnmf_hparams *hps, int32_t iters,
+                      symnmf_stats *outs) {
+  if (!hs || !hps || count < 0 || iters < 0) return SYMNMF_ERR_INVALID;
+  std::vector<int> live(count, 1);
+  std::vector<std::vector<double>> phis(count);
+  int first_err = SYMNMF_OK;
+  for (int32_t i = 0; i < count; ++i) {
+    int rc = check_handle(hs[i]);
+    if (!rc) rc = validate_hp(&hps[i]);
+    if (rc) {
+      live[i] = 0;
+      if (!first_err) first_err = rc;
+    }
+  }
+  for (int32_t it = 0; it < iters; ++it) {
+    bool any = false;
+    for (int32_t i = 0; i < count; ++i) {
+      if (!live[i]) continue;
+      const int rc = iterate_once(hs[i], &hps[i], phis[i]);
+      if (rc == SYMNMF_CONVERGED) {
+        live[i] = 0;
+      } else if (rc) {
+        live[i] = 0;
+        if (!first_err) first_err = rc;
+      } else {
+        any = true;
+      }
+    }
+    if (!any) break;
+  }
+  for (int32_t i = 0; i < count; ++i) {
+    if (!hs[i]) continue;
+    if (!hs[i]->bad) {
+      symnmf_t h = hs[i];
+      const int64_t upto = h->ctrl.converged ? h->ctrl.t + 1 : h->ctrl.t;
+      int rc = sync_records(h, std::max(upto, h->copied_upto), phis[i]);
+      if (rc && !first_err) first_err = rc;
+    }
+    if (outs) fill_stats(hs[i], &outs[i]);
+  }
+  return first_err;
+}
+
+int symnmf_set_profiling(symnmf_t h, int32_t enable) {
+  if (!h) return SYMNMF_ERR_INVALID;
+  if (enable) {
+    h->prof_used = 0;
+    h->prof_bytes = 0.0;
+  }
+  h->profiling = enable != 0;
+  return SYMNMF_OK;
+}
+
+int symnmf_get_profile(symnmf_t h, double *product_ms, int64_t *launches, double *s_bytes) {
+  if (!h) return SYMNMF_ERR_INVALID;
+  CK(cudaStreamSynchronize(h->stream));
+  double ms = 0.0;
+  for (size_t i = 0; i + 1 < h->prof_used; i += 2) {
+    float x = 0.f;
+    CK(cudaEventElapsedTime(&x, h->prof_ev[i], h->prof_ev[i + 1]));
+    ms += x;
+  }
+  if (product_ms) *product_ms = ms;
+  if (launches) *launches = (int64_t)(h->prof_used / 2);
+  if (s_bytes) *s_bytes = h->prof_bytes;
+  return SYMNMF_OK;
+}
+
+int symnmf_get_trace(symnmf_t h, symnmf_record *out, int64_t max, int64_t *count) {
+  if (!h || !count || max < 0 || (max > 0 && !out)) return SYMNMF_ERR_INVALID;
+  *count = (int64_t)h->trace.size();
+  const int64_t m = std::min<int64_t>(max, *count);
+  for (int64_t i = 0; i < m; ++i) out[i] = h->trace[i];
+  return SYMNMF_OK;
+}
+
+int symnmf_state_bytes(symnmf_t h, size_t *bytes) {
+  if (!h || !bytes) return SYMNMF_ERR_INVALID;
+  *bytes = 4 * sizeof(int64_t) + sizeof(symnmf_ctrl) + 4 * sizeof(float) * (size_t)h->n * h->k;
+  return SYMNMF_OK;
+}
+
+int symnmf_get_state(symnmf_t h, void *buf, size_t bytes) {
+  size_t need = 0;
+  if (!h || !buf || symnmf_state_bytes(h, &need) || bytes < need) return SYMNMF_ERR_INVALID;
+  char *p = (char *)buf;
+  const int64_t hdr[4] = {(int64_t)kMagic, h->n, h->k, (int64_t)sizeof(symnmf_ctrl)};
+  std::memcpy(p, hdr, sizeof(hdr));
+  p += sizeof(hdr);
+  std::memcpy(p, &h->ctrl, sizeof(symnmf_ctrl));
+  p += sizeof(symnmf_ctrl);
+  const size_t nk = sizeof(float) * (size_t)h->n * h->k;
+  const float *srcs[4] = {h->H[h->cur], h->A, h->M, h->mu};
+  for (int i = 0; i < 4; ++i) {
+    CK(launch_unpack(srcs[i], h->tmp, h->n, h->k, h->kp, h->stream));
+    CK(cudaMemcpyAsync(p, h->tmp, nk, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    p += nk;
+  }
+  return SYMNMF_OK;
+}
+
+int symnmf_set_state(symnmf_t h, const void *buf, size_t bytes) {
+  size_t need = 0;
+  if (!h || !buf || symnmf_state_bytes(h, &need) || bytes < need) return SYMNMF_ERR_INVALID;
+  const char *p = (const char *)buf;
+  int64_t hdr[4];
+  std::memcpy(hdr, p, sizeof(hdr));
+  if (hdr[0] != (int64_t)kMagic || hdr[1] != h->n || hdr[2] != h->k ||
+      hdr[3] != (int64_t)sizeof(symnmf_ctrl))
+    return fail(h, SYMNMF_ERR_INVALID, "checkpoint does not match this handle");
+  p += sizeof(hdr);
+  symnmf_ctrl c;
+  std::memcpy(&c, p, sizeof(c));
+  p += sizeof(symnmf_ctrl);
+  const size_t nk = sizeof(float) * (size_t)h->n * h->k;
+  float *dsts[4] = {h->H[h->cur], h->A, h->M, h->mu};
+  for (int i = 0; i < 4; ++i) {
+    CK(cudaMemcpyAsync(h->tmp, p, nk, cudaMemcpyHostToDevice, h->stream));
+    CK(launch_pack(h->tmp, dsts[i], h->n, h->k, h->kp, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    p += nk;
+  }
+  h->ctrl = c;
+  h->trace.clear();
+  h->copied_upto = c.t;
+  h->bad = false;
+  h->err.clear();
+  int rc = refresh_derived(h);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  return SYMNMF_OK;
+}
+
+uint64_t symnmf_splitmix64(uint64_t state, uint64_t index) {
+  return mix64(state + (index + 1) * kGamma);
+}
+
+int symnmf_sample_blocks(uint64_t seed, int64_t t, int32_t stream, int64_t nb, int64_t m,
+                         int64_t *out) {
+  if (!out || nb < 1 || m < 0 || t < 0) return SYMNMF_ERR_INVALID;
+  std::vector<int64_t> v;
+  sample(seed, t, stream, nb, m, v);
+  std::copy(v.begin(), v.end(), out);
+  return SYMNMF_OK;
+}
+
+int symnmf_controller_check(symnmf_ctrl *c, const symnmf_hparams *hp, int64_t n, int64_t t,
+                            double E, double kkt, double sumA, double median_g2,
+                            int32_t *decisions, double *stag_ratio) {
+  if (!c || !hp || !decisions || n < 1 || t < 0) return SYMNMF_ERR_INVALID;
+  CheckOut o;
+  ctrl_check(c, hp, n, t, E, kkt, sumA, [&]() { return median_g2; }, &o);
+  decisions[0] = o.converged;
+  decisions[1] = o.reset;
+  decisions[2] = o.grow;
+  if (stag_ratio) *stag_ratio = o.ratio;
+  return SYMNMF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,515 @@
+// Per-tile epilogue of one solver iteration and the fixed-order reductions.
+//
+// For each 128-row tile I the epilogue forms the gradient rows
+//   g_I = 4 (H_I Gram_t - (S H)_I)                          (Sec. 2.1)
+// or the Row-SVRG / Block-SVRG estimates (Sec. 5.1; appendix), applies the
+// AdaGrad or RMSprop update with the max(0, .) projection (appendix,
+// Family 3; Sec. 2.4 "Projected space") into the other H buffer, writes the
+// bf16 hi/lo MMA copy of the new rows, and produces the per-tile partials
+// tr_I = sum H_I * (S H)_I (Eq. 2), ||grad_proj||^2_I (Eq. 6), sum(G)_I, the
+// NaN/Inf count and the Gram partial H'_I^T H'_I.  Within a tile sums are
+// FP32 in a fixed order; across tiles they are FP64 in tile order
+// (launch_reduce), so every result is bit-reproducible run to run.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+
+#include "../../include/symnmf.h"
+#include "symnmf_internal.h"
+
+namespace symnmf {
+namespace {
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  // fixed-order: xor tree within the warp, then warp 0 adds warps in order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) r += sh[i];
+    sh[32] = r;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  __nv_bfloat16 b = __float2bfloat16_rn(x);
+  return *reinterpret_cast<uint16_t *>(&b);
+}
+__device__ __forceinline__ float bf16_val(uint16_t u) {
+  __nv_bfloat16 b = *reinterpret_cast<__nv_bfloat16 *>(&u);
+  return __bfloat162float(b);
+}
+
+// writes the bf16 hi/lo transposed copy and the Gram partial of the tile
+// held in smem Hn[128][KP+1]
+template <int KP>
+__device__ void tile_tail(const float (*Hn)[KP + 1], int64_t r0, uint16_t *Bt, int64_t ldb,
+                          float *gram_part, int tile) {
+  const int tid = threadIdx.x;
+  if (Bt) {
+    for (int e = tid; e < KP * kTileRows; e += blockDim.x) {
+      const int c = e / kTileRows, r = e % kTileRows;
+      const float v = Hn[r][c];
+      const uint16_t hi = bf16_bits(v);
+      const uint16_t lo = bf16_bits(v - bf16_val(hi));
+      Bt[(int64_t)c * ldb + r0 + r] = hi;
+      Bt[(int64_t)(KP + c) * ldb + r0 + r] = lo;
+    }
+  }
+  if (gram_part) {
+    for (int q = tid; q < KP * KP; q += blockDim.x) {
+      const int c = q / KP, d = q % KP;
+      float s = 0.f;
+#pragma unroll 8
+      for (int r = 0; r < kTileRows; ++r) s = fmaf(Hn[r][c], Hn[r][d], s);
+      gram_part[(int64_t)tile * KP * KP + q] = s;
+    }
+  }
+}
+
+template <int KP>
+constexpr size_t epi_smem_bytes() {
+  return (size_t)(2 * kTileRows * (KP + 1) + 2 * KP * (KP + 1)) * sizeof(float);
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) epilogue_kernel(EpiArgs a) {
+  extern __shared__ float smem_epi[];
+  float(*Hs)[KP + 1] = reinterpret_cast<float(*)[KP + 1]>(smem_epi);
+  float(*Hn)[KP + 1] = reinterpret_cast<float(*)[KP + 1]>(smem_epi + kTileRows * (KP + 1));
+  float(*G1)[KP + 1] = reinterpret_cast<float(*)[KP + 1]>(smem_epi + 2 * kTileRows * (KP + 1));
+  float(*G2)[KP + 1] =
+      reinterpret_cast<float(*)[KP + 1]>(smem_epi + 2 * kTileRows * (KP + 1) + KP * (KP + 1));
+  __shared__ double red[40];
+  const int tile = blockIdx.x, tid = threadIdx.x;
+  const int64_t r0 = (int64_t)tile * kTileRows;
+  const int rows = (int)((a.n - r0) < kTileRows ? (a.n - r0) : kTileRows);
+  for (int e = tid; e < kTileRows * KP; e += blockDim.x) {
+    const int r = e / KP, c = e % KP;
+    Hs[r][c] = (r < rows) ? a.H[(r0 + r) * KP + c] : 0.f;
+  }
+  const bool block = (a.mode == MODE_BLOCK);
+  const float *g1src = block ? a.gramJ : a.gram;
+  for (int e = tid; e < KP * KP; e += blockDim.x) {
+    G1[e / KP][e % KP] = g1src[e];
+    if (block) G2[e / KP][e % KP] = a.gramI[e];
+  }
+  int p1 = -1, p2 = -1;
+  if (a.mode == MODE_FULL || a.mode == MODE_GRAD_ONLY) {
+    p1 = tile;
+  } else {
+    p1 = a.pos1[tile];
+    if (block) p2 = a.pos2[tile];
+  }
+  __syncthreads();
+
+  float tr = 0.f, kkt2 = 0.f, sumA = 0.f;
+  int nonfin = 0;
+  for (int e = tid; e < kTileRows * KP; e += blockDim.x) {
+    const int r = e / KP, c = e % KP;
+    float hn = 0.f;
+    if (r < rows && c < a.k) {
+      const int64_t gi = (r0 + r) * KP + c;
+      const float h = Hs[r][c];
+      float g;
+      if (p1 >= 0 || p2 >= 0) {
+        g = 0.f;
+        if (p1 >= 0) {
+          float p = 0.f;
+          for (int s = 0; s < a.nsplit; ++s)
+            p += a.P[(((int64_t)s * a.n1 + p1) * kTileRows + r) * KP + c];
+          float hg = 0.f;
+#pragma unroll
+          for (int d = 0; d < KP; ++d) hg = fmaf(Hs[r][d], G1[d][c], hg);
+          g = a.coef * (hg - p);
+          tr = fmaf(h, p, tr);
+        }
+        if (p2 >= 0) {
+          float q = 0.f;
+          for (int s = 0; s < a.nsplit2; ++s)
+            q += a.Q[(((int64_t)s * a.n2 + p2) * kTileRows + r) * KP + c];
+          float hg = 0.f;
+#pragma unroll
+          for (int d = 0; d < KP; ++d) hg = fmaf(Hs[r][d], G2[d][c], hg);
+          g += a.coef * (hg - q);
+        }
+      } else {
+        g = a.mu[gi];
+      }
+      const float pg = (h > 0.f) ? g : fminf(0.f, g);
+      kkt2 = fmaf(pg, pg, kkt2);
+      if (!isfinite(g)) ++nonfin;
+      if (a.gout) a.gout[gi] = g;
+      if (a.gcaller) a.gcaller[(r0 + r) * a.k + c] = g;
+      if (a.store_mu) a.mu[gi] = g;
+      if (a.update) {
+        float x;
+        if (a.method == SYMNMF_RMSPROP) {
+          const float v = a.alpha * a.A[gi] + (1.f - a.alpha) * (g * g);
+          a.A[gi] = v;
+          const float m = a.mom * a.M[gi] + a.eta * g / (sqrtf(v) + a.eps);
+          a.M[gi] = m;
+          x = h - m;
+          sumA += v;
+        } else {
+          const float acc = a.A[gi] + g * g;
+          a.A[gi] = acc;
+          x = h - a.eta * g / (sqrtf(acc) + a.eps);
+          sumA += acc;
+        }
+        hn = (x > 0.f) ? x : 0.f;
+        a.Hn[gi] = hn;
+      } else {
+        hn = h;
+      }
+    }
+    Hn[r][c] = hn;
+  }
+  __syncthreads();
+  if (a.update) tile_tail<KP>(Hn, r0, a.Btn, a.ldb, a.gram_part, tile);
+  const double s_tr = block_sum((double)tr, red);
+  const double s_kkt = block_sum((double)kkt2, red);
+  const double s_a = block_sum((double)sumA, red);
+  const double s_nf = block_sum((double)nonfin, red);
+  if (tid == 0 && a.slots) {
+    double *sl = a.slots + (int64_t)tile * kSlotStride;
+    sl[0] = s_tr;
+    sl[1] = s_kkt;
+    sl[2] = s_a;
+    sl[3] = s_nf;
+  }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) prepare_kernel(const float *H, int64_t n, uint16_t *Bt,
+                                                      int64_t ldb, float *gram_part) {
+  __shared__ float Hn[kTileRows][KP + 1];
+  const int tile = blockIdx.x;
+  const int64_t r0 = (int64_t)tile * kTileRows;
+  const int rows = (int)((n - r0) < kTileRows ? (n - r0) : kTileRows);
+  for (int e = threadIdx.x; e < kTileRows * KP; e += blockDim.x) {
+    const int r = e / KP, c = e % KP;
+    Hn[r][c] = (r < rows) ? H[(r0 + r) * KP + c] : 0.f;
+  }
+  __syncthreads();
+  tile_tail<KP>(Hn, r0, Bt, ldb, gram_part, tile);
+}
+
+// stage 1: chunk c sums tiles [c*per, (c+1)*per) in order (FP64)
+__global__ void __launch_bounds__(256) reduce_stage1(const double *slots, const float *gram_part,
+                                                     int ntiles, int kp, int per,
+                                                     double *chunk_buf) {
+  const int c = blockIdx.x;
+  const int t0 = c * per, t1 = min(ntiles, t0 + per);
+  const int stride = 4 + kp * kp;
+  double *out = chunk_buf + (int64_t)c * stride;
+  const int tid = threadIdx.x;
+  if (slots && tid < 4) {
+    double s = 0.0;
+    for (int t = t0; t < t1; ++t) s += slots[(int64_t)t * kSlotStride + tid];
+    out[tid] = s;
+  }
+  if (gram_part) {
+    for (int e = tid; e < kp * kp; e += blockDim.x) {
+      double s = 0.0;
+      for (int t = t0; t < t1; ++t) s += (double)gram_part[(int64_t)t * kp * kp + e];
+      out[4 + e] = s;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) reduce_stage2(const double *chunk_buf, int nchunks, int kp,
+                                                     int k, int64_t n, double normS2, long long t,
+                                                     int full, int have_slots, int have_gram,
+                                                     const double *gram64_cur, double *gram64_next,
+                                                     float *gram32_next, DevRecord *rec) {
+  __shared__ double red[40];
+  __shared__ double sc[4];
+  const int stride = 4 + kp * kp;
+  const int tid = threadIdx.x;
+  if (have_slots && tid < 4) {
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += chunk_buf[(int64_t)c * stride + tid];
+    sc[tid] = s;
+  }
+  if (have_gram) {
+    for (int e = tid; e < kp * kp; e += blockDim.x) {
+      double s = 0.0;
+      for (int c = 0; c < nchunks; ++c) s += chunk_buf[(int64_t)c * stride + 4 + e];
+      gram64_next[e] = s;
+      gram32_next[e] = (float)s;
+    }
+  }
+  double g2 = 0.0;
+  for (int e = tid; e < kp * kp; e += blockDim.x) g2 += gram64_cur[e] * gram64_cur[e];
+  g2 = block_sum(g2, red);
+  if (tid == 0 && have_slots && rec) {
+    DevRecord r;
+    r.t = t;
+    r.tr = sc[0];
+    r.gram2 = g2;
+    r.f = normS2 - 2.0 * sc[0] + g2;
+    r.E = r.f / normS2;
+    r.kkt = sqrt(sc[1]) / ((double)n * (double)k);
+    r.sumA = sc[2];
+    r.nonfinite = (int)sc[3];
+    r.full = full;
+    *rec = r;
+  }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) gram_subset_kernel(const float *gram_part, const int *l1,
+                                                          int n1, const int *l2, int n2,
+                                                          float *o1, float *o2) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= KP * KP) return;
+  const int *l = blockIdx.y == 0 ? l1 : l2;
+  const int m = blockIdx.y == 0 ? n1 : n2;
+  float *o = blockIdx.y == 0 ? o1 : o2;
+  double s = 0.0;
+  for (int i = 0; i < m; ++i) s += (double)gram_part[(int64_t)l[i] * KP * KP + e];
+  o[e] = (float)s;
+}
+
+template <int DT>
+__device__ __forceinline__ double s_value(const void *S, int64_t idx, double scale) {
+  if constexpr (DT == 0) {
+    return (double)reinterpret_cast<const float *>(S)[idx];
+  } else if constexpr (DT == 1) {
+    return (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(S)[idx]);
+  } else {
+    __nv_fp8_e4m3 q;
+    q.__x = reinterpret_cast<const __nv_fp8_storage_t *>(S)[idx];
+    return (double)static_cast<float>(q) * scale;
+  }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) norm_s2_kernel(const void *S, int64_t n, int64_t lds,
+                                                      const float *scales, int64_t ld_scales,
+                                                      double *partials) {
+  __shared__ double red[40];
+  double acc = 0.0;
+  for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+      const double sc = (DT == 2) ? (double)scales[(r / kTileRows) * ld_scales + c / kTileRows] : 1.0;
+      const double v = s_value<DT>(S, r * lds + c, sc);
+      acc += v * v;
+    }
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void sum_array_kernel(const double *x, int m, int stride, int off, double *out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s += x[(int64_t)i * stride + off];
+    *out = s;
+  }
+}
+
+__global__ void pack_kernel(const float *src, float *dst, int64_t n, int k, int kp) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * kp) return;
+  const int64_t r = e / kp;
+  const int c = (int)(e % kp);
+  dst[e] = (c < k) ? src[r * k + c] : 0.f;
+}
+
+__global__ void unpack_kernel(const float *src, float *dst, int64_t n, int k, int kp) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  const int64_t r = e / k;
+  const int c = (int)(e % k);
+  dst[e] = src[r * kp + c];
+}
+
+// radix select of the lower median of g^2 (FP32 bit patterns of non-negative
+// floats order like unsigned integers); three passes of 11, 11, 10 bits
+__global__ void __launch_bounds__(256) hist_kernel(const float *g, int64_t n, int k, int kp,
+                                                   int shift, int nbits, const unsigned *sel,
+                                                   unsigned *hist) {
+  __shared__ unsigned sh[2048];
+  const int nb = 1 << nbits;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0u;
+  __syncthreads();
+  const unsigned mask = sel[0], val = sel[1];
+  const int64_t total = n * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / k;
+    const int c = (int)(e % k);
+    const float x = g[r * kp + c];
+    const float x2 = x * x;
+    const unsigned u = __float_as_uint(x2);
+    if ((u & mask) == val) atomicAdd(&sh[(u >> shift) & (nb - 1)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+__global__ void select_kernel(unsigned *hist, int shift, int nbits, unsigned *sel, float *out,
+                              int last) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int nb = 1 << nbits;
+  unsigned rank = sel[2];
+  unsigned cum = 0;
+  int b = 0;
+  for (; b < nb; ++b) {
+    if (cum + hist[b] > rank) break;
+    cum += hist[b];
+  }
+  if (b >= nb) b = nb - 1;
+  sel[2] = rank - cum;
+  sel[0] |= (unsigned)(nb - 1) << shift;
+  sel[1] |= (unsigned)b << shift;
+  for (int i = 0; i < nb; ++i) hist[i] = 0u;
+  if (last) *out = __uint_as_float(sel[1]);
+}
+
+__global__ void init_sel_kernel(unsigned *sel, unsigned rank, unsigned *hist) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sel[0] = 0u;
+    sel[1] = 0u;
+    sel[2] = rank;
+  }
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x) hist[i] = 0u;
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) reset_kernel(float *A, const float *g, const float *med,
+                                                    float c, int64_t n, int k, double *slots) {
+  __shared__ double red[40];
+  const int tile = blockIdx.x;
+  const int64_t r0 = (int64_t)tile * kTileRows;
+  const int rows = (int)((n - r0) < kTileRows ? (n - r0) : kTileRows);
+  const float m = *med;
+  float s = 0.f;
+  for (int e = threadIdx.x; e < kTileRows * KP; e += blockDim.x) {
+    const int r = e / KP, cc = e % KP;
+    if (r < rows && cc < k) {
+      const int64_t gi = (r0 + r) * KP + cc;
+      const float x = g[gi];
+      const float v = c * fmaxf(x * x, m);
+      A[gi] = v;
+      s += v;
+    }
+  }
+  const double tot = block_sum((double)s, red);
+  if (threadIdx.x == 0) slots[(int64_t)tile * kSlotStride + 2] = tot;
+}
+
+}  // namespace
+
+#define KP_SWITCH(kp, ...)                              \
+  switch (kp) {                                         \
+    case 8: { constexpr int KPV = 8; __VA_ARGS__; } break;   \
+    case 16: { constexpr int KPV = 16; __VA_ARGS__; } break; \
+    case 32: { constexpr int KPV = 32; __VA_ARGS__; } break; \
+    case 64: { constexpr int KPV = 64; __VA_ARGS__; } break; \
+    default: return cudaErrorInvalidValue;              \
+  }
+
+cudaError_t launch_epilogue(const EpiArgs &a, cudaStream_t s) {
+  KP_SWITCH(a.kp, {
+    constexpr size_t bytes = epi_smem_bytes<KPV>();
+    cudaError_t e = cudaFuncSetAttribute(epilogue_kernel<KPV>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    epilogue_kernel<KPV><<<a.ntiles, 256, bytes, s>>>(a);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_tiles(const float *H, int64_t n, int k, int kp, uint16_t *Bt,
+                                 int64_t ldb, float *gram_part, cudaStream_t s) {
+  (void)k;
+  const int ntiles = (int)((n + kTileRows - 1) / kTileRows);
+  KP_SWITCH(kp, prepare_kernel<KPV><<<ntiles, 256, 0, s>>>(H, n, Bt, ldb, gram_part));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double *slots, const float *gram_part, int ntiles, int kp, int k,
+                          int64_t n, double normS2, long long t, int full, double *chunk_buf,
+                          int nchunks, const double *gram64_cur, double *gram64_next,
+                          float *gram32_next, DevRecord *rec, cudaStream_t s) {
+  const int per = (ntiles + nchunks - 1) / nchunks;
+  const int nc = (ntiles + per - 1) / per;
+  reduce_stage1<<<nc, 256, 0, s>>>(slots, gram_part, ntiles, kp, per, chunk_buf);
+  reduce_stage2<<<1, 256, 0, s>>>(chunk_buf, nc, kp, k, n, normS2, t, full, slots != nullptr,
+                                  gram_part != nullptr, gram64_cur, gram64_next, gram32_next, rec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_subset(const float *gram_part, int kp, const int *l1, int n1,
+                               const int *l2, int n2, float *o1, float *o2, cudaStream_t s) {
+  dim3 grid((kp * kp + 255) / 256, 2);
+  KP_SWITCH(kp, gram_subset_kernel<KPV><<<grid, 256, 0, s>>>(gram_part, l1, n1, l2, n2, o1, o2));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm_s2(const void *S, int64_t n, int64_t lds, int dtype, const float *scales,
+                           int64_t ld_scales, double *partials, int nparts, double *out,
+                           cudaStream_t s) {
+  switch (dtype) {
+    case 0: norm_s2_kernel<0><<<nparts, 256, 0, s>>>(S, n, lds, scales, ld_scales, partials); break;
+    case 1: norm_s2_kernel<1><<<nparts, 256, 0, s>>>(S, n, lds, scales, ld_scales, partials); break;
+    case 2: norm_s2_kernel<2><<<nparts, 256, 0, s>>>(S, n, lds, scales, ld_scales, partials); break;
+    default: return cudaErrorInvalidValue;
+  }
+  sum_array_kernel<<<1, 32, 0, s>>>(partials, nparts, 1, 0, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const float *src, float *dst, int64_t n, int k, int kp, cudaStream_t s) {
+  const int64_t tot = n * kp;
+  pack_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, dst, n, k, kp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const float *src, float *dst, int64_t n, int k, int kp, cudaStream_t s) {
+  const int64_t tot = n * k;
+  unpack_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, dst, n, k, kp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_median_g2(const float *g, int64_t n, int k, int kp, unsigned *hist,
+                             unsigned *sel, float *out, cudaStream_t s) {
+  const int64_t total = n * k;
+  const unsigned rank = (unsigned)((total - 1) / 2);
+  init_sel_kernel<<<1, 256, 0, s>>>(sel, rank, hist);
+  const int grid = (int)std::min<int64_t>(1024, (total + 255) / 256);
+  const int shifts[3] = {21, 10, 0};
+  const int bits[3] = {11, 11, 10};
+  for (int p = 0; p < 3; ++p) {
+    hist_kernel<<<grid, 256, 0, s>>>(g, n, k, kp, shifts[p], bits[p], sel, hist);
+    select_kernel<<<1, 1, 0, s>>>(hist, shifts[p], bits[p], sel, out, p == 2);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset(float *A, const float *g, const float *med, float c, int64_t n, int k,
+                         int kp, double *slots, cudaStream_t s) {
+  const int ntiles = (int)((n + kTileRows - 1) / kTileRows);
+  KP_SWITCH(kp, reset_kernel<KPV><<<ntiles, 256, 0, s>>>(A, g, med, c, n, k, slots));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_slot(const double *slots, int ntiles, int which, double *out,
+                            cudaStream_t s) {
+  sum_array_kernel<<<1, 32, 0, s>>>(slots, ntiles, kSlotStride, which, out);
+  return cudaGetLastError();
+}
+
+}  // namespace symnmf

@@ -1,0 +1,117 @@
+// Internal declarations shared by the host runtime (capi.cu) and the kernels.
+// Layout conventions (all owned buffers):
+//   * row tiles are 128 rows; ntiles = ceil(n / 128)
+//   * n x k state arrays are stored n x kp (kp = 8, 16, 32 or 64 >= k), the
+//     columns k..kp-1 held at exactly 0, so the padded columns never move
+//   * the MMA copy of H is stored transposed, [2*kp][ldb] bfloat16 with
+//     rows 0..kp-1 = hi(H^T) and kp..2kp-1 = lo(H^T) = bf16(H - hi), ldb =
+//     ntiles * 128 (columns past n are 0)
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace symnmf {
+
+constexpr int kTileRows = 128;
+constexpr int kRing = 1024;  // device record ring (iterations)
+
+enum Mode : int { MODE_FULL = 0, MODE_ROWS = 1, MODE_BLOCK = 2, MODE_GRAD_ONLY = 3 };
+
+struct DevRecord {
+  long long t;
+  double f, E, kkt, tr, gram2, sumA;
+  int nonfinite;
+  int full;
+};
+
+// S x H product over a list of 128-row tiles and a list of 128-column tiles.
+// out[(split * n_rows_list + row_pos) * 128 * kp + r * kp + c] holds the
+// partial sum of split `split` (a contiguous share of the column list).
+struct ProdArgs {
+  const void *S;
+  int64_t lds;           // row pitch of S in elements
+  int dtype;
+  const float *scales;   // FP8 tile scales or nullptr
+  int64_t ld_scales;
+  int64_t n;
+  int k, kp;
+  const float *H;        // FP32 master, n x kp (SIMT path)
+  const uint16_t *Bt;    // bf16 hi/lo transposed copy (tensor-core path)
+  int64_t ldb;
+  const int *row_list;   // row tile indices (nullptr: all tiles in order)
+  int n_rows_list;
+  const int *col_list;   // column tile indices (nullptr: all tiles in order)
+  int n_cols_list;
+  int nsplit;
+  float *out;
+};
+
+struct EpiArgs {
+  int64_t n;
+  int k, kp, ntiles;
+  int mode;              // Mode
+  int method;            // symnmf_method
+  int update;            // 0: gradient only, no state change
+  int store_mu;          // write mu = g (full pass of an SVRG method)
+  float eta, eps, alpha, mom;
+  const float *H;        // H_t (n x kp)
+  float *Hn;             // H_{t+1}
+  uint16_t *Btn;         // MMA copy of H_{t+1}
+  int64_t ldb;
+  float *A, *M, *mu;     // state (n x kp)
+  float *gout;           // g (n x kp) or nullptr
+  float *gcaller;        // g in caller layout n x k (symnmf_grad) or nullptr
+  const float *gram;     // Gram of H_t, kp x kp FP32 (full / rows)
+  const float *gramI;    // block mode: H_I^T H_I
+  const float *gramJ;    // block mode: H_J^T H_J
+  const float *P;        // product partials for rows in list 1
+  int nsplit;
+  const int *pos1;       // tile -> position in list 1 (or -1); nullptr in full mode
+  int n1;                // length of list 1
+  const float *Q;        // block mode: partials of S_{J,I} H_I, list 2 = J
+  int nsplit2;
+  const int *pos2;
+  int n2;
+  float coef;            // 4 (full/rows) or 2 (block)
+  double *slots;         // per tile: [tr, kkt2, sumA, nonfinite]
+  float *gram_part;      // per tile kp x kp partial of H_{t+1}^T H_{t+1} (nullptr: skip)
+};
+
+constexpr int kSlotStride = 4;
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_prod_simt(const ProdArgs &a, cudaStream_t s);
+cudaError_t launch_prod_tc(const ProdArgs &a, cudaStream_t s, int num_sms);
+bool tc_supported(int dtype, int kp);
+cudaError_t launch_epilogue(const EpiArgs &a, cudaStream_t s);
+// per-tile Bt copy and Gram partial of H (init / teacher forcing)
+cudaError_t launch_prepare_tiles(const float *H, int64_t n, int k, int kp, uint16_t *Bt,
+                                 int64_t ldb, float *gram_part, cudaStream_t s);
+// two-level fixed-order reduction of per-tile slots and Gram partials; writes
+// the record of iteration t (ring slot t % kRing), Gram64/Gram32 of the next
+// iterate, and reads Gram64 of the current iterate for ||Gram_t||^2.
+cudaError_t launch_reduce(const double *slots, const float *gram_part, int ntiles, int kp, int k,
+                          int64_t n, double normS2, long long t, int full, double *chunk_buf,
+                          int nchunks, const double *gram64_cur, double *gram64_next,
+                          float *gram32_next, DevRecord *ring, cudaStream_t s);
+// Gram of a subset of tiles (lists of tile indices) -> FP32 kp x kp, two lists
+cudaError_t launch_gram_subset(const float *gram_part, int kp, const int *list1, int n1,
+                               const int *list2, int n2, float *out1, float *out2,
+                               cudaStream_t s);
+cudaError_t launch_norm_s2(const void *S, int64_t n, int64_t lds, int dtype, const float *scales,
+                           int64_t ld_scales, double *partials, int nparts, double *out,
+                           cudaStream_t s);
+// n x k (pitch k) <-> n x kp (pitch kp, pads zeroed)
+cudaError_t launch_pack(const float *src, float *dst, int64_t n, int k, int kp, cudaStream_t s);
+cudaError_t launch_unpack(const float *src, float *dst, int64_t n, int k, int kp, cudaStream_t s);
+// lower median of g^2 over the n x k valid entries (radix select on the
+// FP32 bit patterns); result in *out (device)
+cudaError_t launch_median_g2(const float *g, int64_t n, int k, int kp, unsigned *hist,
+                             unsigned *sel, float *out, cudaStream_t s);
+// Piecewise reset: A = c * max(g^2, med); per-tile sum(A) into slots[.][2]
+cudaError_t launch_reset(float *A, const float *g, const float *med, float c, int64_t n, int k,
+                         int kp, double *slots, cudaStream_t s);
+cudaError_t launch_sum_slot(const double *slots, int ntiles, int which, double *out,
+                            cudaStream_t s);
+
+}  // namespace symnmf

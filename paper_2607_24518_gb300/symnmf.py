@@ -1,0 +1,308 @@
+"""ctypes binding of libsymnmf (include/symnmf.h), same names as the C ABI.
+
+Argument marshalling only: pointers may be given as integers or as torch
+tensors (their ``data_ptr()``), structures mirror the C structs field by
+field, and a negative status becomes a ``SymNMFError``.  Every step of the
+solver runs in the library's CUDA kernels; if the library is missing this
+module raises at import time instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsymnmf.so")
+
+F32, BF16, FP8E4M3 = 0, 1, 2
+ADAGRAD, RMSPROP, PIECEWISE_ADAGRAD, ROW_SVRG, BLOCK_SVRG_ADAPTGROW = 0, 1, 2, 3, 4
+OK, CONVERGED = 0, 1
+ERR_INVALID, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = (
+    -1, -2, -3, -4, -5, -6, -7)
+BUF_H, BUF_ACC, BUF_MOM, BUF_SNAPSHOT, BUF_GRAD = 0, 1, 2, 3, 4
+
+
+class symnmf_hparams(C.Structure):
+    _fields_ = [("method", C.c_int32), ("check_interval", C.c_int32), ("warmup", C.c_int32),
+                ("snapshot_period", C.c_int32), ("block_rows", C.c_int32),
+                ("reserved0", C.c_int32), ("eta", C.c_double), ("eps", C.c_double),
+                ("alpha", C.c_double), ("mu", C.c_double), ("c", C.c_double),
+                ("c_r", C.c_double), ("row_frac", C.c_double), ("phi0", C.c_double),
+                ("tau_E", C.c_double), ("tau_g", C.c_double), ("tau_stag", C.c_double),
+                ("growth_kkt_mult", C.c_double), ("seed", C.c_uint64)]
+
+
+class symnmf_ctrl(C.Structure):
+    _fields_ = [("t", C.c_int64), ("E0", C.c_double), ("E_prev", C.c_double),
+                ("phi", C.c_double), ("sumA_post", C.c_double), ("E_at_reset", C.c_double),
+                ("have_prev", C.c_int32), ("stag_count", C.c_int32), ("resets", C.c_int32),
+                ("resets_enabled", C.c_int32), ("cooldown", C.c_int32),
+                ("converged", C.c_int32)]
+
+
+class symnmf_record(C.Structure):
+    _fields_ = [("t", C.c_int64), ("f", C.c_double), ("E", C.c_double), ("kkt", C.c_double),
+                ("stag_ratio", C.c_double), ("phi", C.c_double), ("sumA", C.c_double),
+                ("full", C.c_int32), ("check", C.c_int32), ("reset", C.c_int32),
+                ("converged", C.c_int32), ("nonfinite", C.c_int32), ("reserved", C.c_int32)]
+
+
+class symnmf_stats(C.Structure):
+    _fields_ = [("iter", C.c_int64), ("last_check", C.c_int64), ("f", C.c_double),
+                ("E", C.c_double), ("kkt", C.c_double), ("stag_ratio", C.c_double),
+                ("phi", C.c_double), ("converged", C.c_int32), ("resets", C.c_int32)]
+
+
+class SymNMFError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsymnmf.so not built at {LIB_PATH}; run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+    P = C.POINTER
+    sig = {
+        "symnmf_create": [vp, i64, i32, i32, P(vp)],
+        "symnmf_create_ld": [vp, i64, i64, i32, i32, P(vp)],
+        "symnmf_destroy": [vp],
+        "symnmf_set_stream": [vp, vp],
+        "symnmf_set_tile_scales": [vp, vp, i64],
+        "symnmf_set_norm": [vp, dbl],
+        "symnmf_get_norm": [vp, P(dbl)],
+        "symnmf_set_impl": [vp, i32],
+        "symnmf_get_impl": [vp, P(i32)],
+        "symnmf_set_H": [vp, vp],
+        "symnmf_get_H": [vp, vp],
+        "symnmf_get_buffer": [vp, i32, vp],
+        "symnmf_set_buffer": [vp, i32, vp],
+        "symnmf_get_ctrl": [vp, P(symnmf_ctrl)],
+        "symnmf_set_ctrl": [vp, P(symnmf_ctrl)],
+        "symnmf_grad": [vp, vp],
+        "symnmf_objective": [vp, P(dbl), P(dbl)],
+        "symnmf_hparams_default": [i32, P(symnmf_hparams)],
+        "symnmf_step": [vp, P(symnmf_hparams), i32, P(symnmf_stats)],
+        "symnmf_batch_step": [P(vp), i32, P(symnmf_hparams), i32, P(symnmf_stats)],
+        "symnmf_get_trace": [vp, P(symnmf_record), i64, P(i64)],
+        "symnmf_set_profiling": [vp, i32],
+        "symnmf_get_profile": [vp, P(dbl), P(i64), P(dbl)],
+        "symnmf_state_bytes": [vp, P(C.c_size_t)],
+        "symnmf_get_state": [vp, vp, C.c_size_t],
+        "symnmf_set_state": [vp, vp, C.c_size_t],
+        "symnmf_last_error": [vp],
+        "symnmf_status_string": [i32],
+        "symnmf_splitmix64": [u64, u64],
+        "symnmf_sample_blocks": [u64, i64, i32, i64, i64, P(i64)],
+        "symnmf_controller_check": [P(symnmf_ctrl), P(symnmf_hparams), i64, i64, dbl, dbl, dbl,
+                                    dbl, P(i32), P(dbl)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.symnmf_destroy.restype = None
+    lib.symnmf_last_error.restype = C.c_char_p
+    lib.symnmf_status_string.restype = C.c_char_p
+    lib.symnmf_splitmix64.restype = C.c_uint64
+    return lib
+
+
+LIB = _load()
+DECLARED = [
+    "symnmf_create", "symnmf_create_ld", "symnmf_destroy", "symnmf_set_stream",
+    "symnmf_set_tile_scales", "symnmf_set_norm", "symnmf_get_norm", "symnmf_set_impl",
+    "symnmf_get_impl", "symnmf_set_H", "symnmf_get_H", "symnmf_get_buffer", "symnmf_set_buffer",
+    "symnmf_get_ctrl", "symnmf_set_ctrl", "symnmf_grad", "symnmf_objective",
+    "symnmf_hparams_default", "symnmf_step", "symnmf_batch_step", "symnmf_get_trace",
+    "symnmf_set_profiling", "symnmf_get_profile",
+    "symnmf_state_bytes", "symnmf_get_state", "symnmf_set_state", "symnmf_last_error",
+    "symnmf_status_string", "symnmf_splitmix64", "symnmf_sample_blocks",
+    "symnmf_controller_check",
+]
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _check(status, h=None):
+    if status < 0:
+        msg = LIB.symnmf_last_error(h).decode() if h else ""
+        raise SymNMFError(status, msg or LIB.symnmf_status_string(status).decode())
+    return status
+
+
+def symnmf_status_string(status):
+    return LIB.symnmf_status_string(status).decode()
+
+
+def symnmf_last_error(h):
+    return LIB.symnmf_last_error(h).decode()
+
+
+def symnmf_create(S, n, k, dtype):
+    h = C.c_void_p()
+    _check(LIB.symnmf_create(_ptr(S), n, k, dtype, C.byref(h)))
+    return h
+
+
+def symnmf_create_ld(S, n, lds, k, dtype):
+    h = C.c_void_p()
+    _check(LIB.symnmf_create_ld(_ptr(S), n, lds, k, dtype, C.byref(h)))
+    return h
+
+
+def symnmf_destroy(h):
+    LIB.symnmf_destroy(h)
+
+
+def symnmf_set_stream(h, stream):
+    """stream: a torch.cuda.Stream, an int handle, or None."""
+    s = getattr(stream, "cuda_stream", stream)
+    return _check(LIB.symnmf_set_stream(h, s), h)
+
+
+def symnmf_set_tile_scales(h, scales, ld_scales):
+    return _check(LIB.symnmf_set_tile_scales(h, _ptr(scales), ld_scales), h)
+
+
+def symnmf_set_norm(h, normS2):
+    return _check(LIB.symnmf_set_norm(h, float(normS2)), h)
+
+
+def symnmf_get_norm(h):
+    v = C.c_double()
+    _check(LIB.symnmf_get_norm(h, C.byref(v)), h)
+    return v.value
+
+
+def symnmf_set_impl(h, impl):
+    return _check(LIB.symnmf_set_impl(h, impl), h)
+
+
+def symnmf_get_impl(h):
+    v = C.c_int32()
+    _check(LIB.symnmf_get_impl(h, C.byref(v)), h)
+    return v.value
+
+
+def symnmf_set_H(h, H):
+    return _check(LIB.symnmf_set_H(h, _ptr(H)), h)
+
+
+def symnmf_get_H(h, H):
+    return _check(LIB.symnmf_get_H(h, _ptr(H)), h)
+
+
+def symnmf_get_buffer(h, which, dst):
+    return _check(LIB.symnmf_get_buffer(h, which, _ptr(dst)), h)
+
+
+def symnmf_set_buffer(h, which, src):
+    return _check(LIB.symnmf_set_buffer(h, which, _ptr(src)), h)
+
+
+def symnmf_get_ctrl(h):
+    c = symnmf_ctrl()
+    _check(LIB.symnmf_get_ctrl(h, C.byref(c)), h)
+    return c
+
+
+def symnmf_set_ctrl(h, c):
+    return _check(LIB.symnmf_set_ctrl(h, C.byref(c)), h)
+
+
+def symnmf_grad(h, G):
+    return _check(LIB.symnmf_grad(h, _ptr(G)), h)
+
+
+def symnmf_objective(h):
+    f, E = C.c_double(), C.c_double()
+    _check(LIB.symnmf_objective(h, C.byref(f), C.byref(E)), h)
+    return f.value, E.value
+
+
+def symnmf_hparams_default(method, **overrides):
+    hp = symnmf_hparams()
+    _check(LIB.symnmf_hparams_default(method, C.byref(hp)))
+    for k_, v in overrides.items():
+        setattr(hp, k_, v)
+    return hp
+
+
+def symnmf_step(h, hp, iters):
+    st = symnmf_stats()
+    status = _check(LIB.symnmf_step(h, C.byref(hp), iters, C.byref(st)), h)
+    return status, st
+
+
+def symnmf_batch_step(hs, hps, iters):
+    n = len(hs)
+    harr = (C.c_void_p * n)(*[x.value if isinstance(x, C.c_void_p) else x for x in hs])
+    parr = (symnmf_hparams * n)(*hps)
+    sarr = (symnmf_stats * n)()
+    status = _check(LIB.symnmf_batch_step(harr, n, parr, iters, sarr))
+    return status, list(sarr)
+
+
+def symnmf_get_trace(h, max_records=None):
+    cnt = C.c_int64()
+    _check(LIB.symnmf_get_trace(h, None, 0, C.byref(cnt)), h)
+    m = cnt.value if max_records is None else min(max_records, cnt.value)
+    arr = (symnmf_record * max(1, m))()
+    _check(LIB.symnmf_get_trace(h, arr, m, C.byref(cnt)), h)
+    return list(arr)[:m]
+
+
+def symnmf_set_profiling(h, enable):
+    return _check(LIB.symnmf_set_profiling(h, int(bool(enable))), h)
+
+
+def symnmf_get_profile(h):
+    ms, n, b = C.c_double(), C.c_int64(), C.c_double()
+    _check(LIB.symnmf_get_profile(h, C.byref(ms), C.byref(n), C.byref(b)), h)
+    return ms.value, n.value, b.value
+
+
+def symnmf_state_bytes(h):
+    v = C.c_size_t()
+    _check(LIB.symnmf_state_bytes(h, C.byref(v)), h)
+    return v.value
+
+
+def symnmf_get_state(h):
+    nb = symnmf_state_bytes(h)
+    buf = (C.c_char * nb)()
+    _check(LIB.symnmf_get_state(h, buf, nb), h)
+    return bytes(buf)
+
+
+def symnmf_set_state(h, blob):
+    buf = (C.c_char * len(blob)).from_buffer_copy(blob)
+    return _check(LIB.symnmf_set_state(h, buf, len(blob)), h)
+
+
+def symnmf_splitmix64(state, index):
+    return int(LIB.symnmf_splitmix64(state, index))
+
+
+def symnmf_sample_blocks(seed, t, stream, nb, m):
+    out = (C.c_int64 * max(1, min(m, nb)))()
+    _check(LIB.symnmf_sample_blocks(seed, t, stream, nb, m, out))
+    return list(out)[:min(m, nb)]
+
+
+def symnmf_controller_check(ctrl, hp, n, t, E, kkt, sumA, median_g2):
+    dec = (C.c_int32 * 3)()
+    ratio = C.c_double()
+    _check(LIB.symnmf_controller_check(C.byref(ctrl), C.byref(hp), n, t, E, kkt, sumA,
+                                       median_g2, dec, C.byref(ratio)))
+    return {"converged": bool(dec[0]), "reset": bool(dec[1]), "grow": bool(dec[2]),
+            "stag_ratio": ratio.value}

@@ -1,0 +1,133 @@
+"""C-ABI tests that need no GPU: the library loads, every symbol declared in
+include/symnmf.h is exported, argument errors are reported before any CUDA
+call, and the host-side pure functions (SplitMix64 sampling, controller)
+agree with the oracle on the same inputs."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2607_24518_gb300 import build
+    build.build()
+    from paper_2607_24518_gb300 import symnmf
+    return symnmf
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "symnmf.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(symnmf_[A-Za-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_symbols()
+    assert len(names) >= 25
+    for name in names:
+        assert hasattr(L.LIB, name), name
+    assert sorted(L.DECLARED) == names
+
+
+def test_argument_errors_without_gpu(L):
+    with pytest.raises(L.SymNMFError) as e:
+        L.symnmf_create(None, 10, 4, L.F32)
+    assert e.value.status == L.ERR_INVALID
+    with pytest.raises(L.SymNMFError) as e:
+        L.symnmf_create(4096, 0, 4, L.F32)
+    assert e.value.status == L.ERR_INVALID
+    with pytest.raises(L.SymNMFError) as e:
+        L.symnmf_create(4096, 10, 65, L.F32)
+    assert e.value.status == L.ERR_UNSUPPORTED
+    with pytest.raises(L.SymNMFError) as e:
+        L.symnmf_create(4096, 10, 0, L.F32)
+    assert e.value.status == L.ERR_UNSUPPORTED
+    with pytest.raises(L.SymNMFError) as e:
+        L.symnmf_create(4096, 10, 4, 7)
+    assert e.value.status == L.ERR_INVALID
+    with pytest.raises(L.SymNMFError) as e:
+        L.symnmf_hparams_default(9)
+    assert e.value.status == L.ERR_INVALID
+
+
+def test_status_strings(L):
+    assert L.symnmf_status_string(L.OK) == "ok"
+    assert L.symnmf_status_string(L.ERR_TIMEOUT) == "device wait timed out"
+
+
+def test_hparams_default_match_oracle(L):
+    from oracle import symnmf_oracle as O
+    for m in range(5):
+        hp = L.symnmf_hparams_default(m)
+        ref = O.HParams.paper(m)
+        for f in ("eta", "eps", "alpha", "mu", "c", "c_r", "row_frac", "phi0", "tau_E",
+                  "tau_g", "tau_stag", "growth_kkt_mult", "check_interval", "warmup",
+                  "snapshot_period", "block_rows", "method"):
+            assert getattr(hp, f) == getattr(ref, f), (m, f)
+
+
+def test_splitmix64_matches_published_vectors(L):
+    vals = [int(l, 16) for l in open(os.path.join(ROOT, "tests", "golden", "splitmix64_state0.txt"))
+            if l[0] != "#"]
+    assert [L.symnmf_splitmix64(0, i) for i in range(4)] == vals
+
+
+def test_sampling_matches_oracle(L):
+    from oracle import symnmf_oracle as O
+    rng = np.random.default_rng(0)
+    for _ in range(300):
+        seed = int(rng.integers(0, 2**63))
+        t = int(rng.integers(0, 10**6))
+        stream = int(rng.integers(0, 3))
+        nb = int(rng.integers(1, 400))
+        m = int(rng.integers(0, nb + 3))
+        assert L.symnmf_sample_blocks(seed, t, stream, nb, m) == O.sample_blocks(seed, t, stream, nb, m)
+
+
+def _ctrl_pair(L, O, method, n):
+    hp = L.symnmf_hparams_default(method)
+    hpo = O.HParams.paper(method)
+    c = L.symnmf_ctrl()
+    c.E0 = c.E_prev = c.E_at_reset = float("nan")
+    c.phi = hpo.phi0 if method == O.BLOCK_SVRG else 1.0
+    c.resets_enabled = 1
+    co = O.Ctrl(phi=c.phi)
+    return hp, hpo, c, co
+
+
+@pytest.mark.parametrize("method", [0, 1, 2, 3, 4])
+def test_controller_replay_matches_oracle(L, method):
+    """The same recorded scalar trace drives both controllers to identical
+    decisions (converged / reset / grow) and identical stagnation ratios."""
+    from oracle import symnmf_oracle as O
+    rng = np.random.default_rng(100 + method)
+    for trial in range(20):
+        n = int(rng.choice([100, 1000, 20000]))
+        hp, hpo, c, co = _ctrl_pair(L, O, method, n)
+        E = 0.9
+        sumA = 1.0
+        for t in range(0, 600, 10):
+            # a trace that descends, stalls, and sometimes jumps back
+            r = rng.random()
+            E = E * (0.5 if r < 0.2 else 1.0 - 1e-6 if r < 0.8 else 1.0 + 1e-3)
+            kkt = float(10 ** rng.uniform(-6, -1))
+            sumA *= float(rng.uniform(1.0, 3.0))
+            med = float(10 ** rng.uniform(-12, -2))
+            d = L.symnmf_controller_check(c, hp, n, t, E, kkt, sumA, med)
+            out = O.controller_check(co, hpo, n, t, E, kkt, sumA, lambda: med)
+            assert d["converged"] == out.converged
+            assert d["reset"] == out.reset
+            assert d["grow"] == out.grow
+            assert (math.isnan(d["stag_ratio"]) and math.isnan(out.stag_ratio)) or \
+                d["stag_ratio"] == out.stag_ratio
+            if out.reset:
+                co.sumA_post = c.sumA_post = sumA * 0.1
+            assert c.phi == co.phi and c.resets == co.resets
+            assert bool(c.cooldown) == co.cooldown and bool(c.resets_enabled) == co.resets_enabled
+            if out.converged:
+                break

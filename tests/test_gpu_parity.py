@@ -1,0 +1,325 @@
+"""GPU-vs-oracle parity through the C ABI.
+
+Tolerances (FP32 path): the product S H is accumulated in FP32 over n terms
+of non-negative values, so its relative error is a few units of 2^-24 times
+a slowly growing factor; 1e-5 relative on the gradient (the target the
+method's FP32 path is held to) leaves two orders of margin.  The objective is
+checked as |f_gpu - f_ref| <= 1e-6 ||S||^2: the trace form cancels three
+terms of size ~||S||^2 (Sec. 2.1, "Numerical consideration"), so the error
+is bounded relative to ||S||^2, not to f.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import gen
+from oracle import symnmf_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+REL_FP32 = 1e-5
+OBJ_ABS = 1e-6
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2607_24518_gb300 import build
+    build.build()
+    from paper_2607_24518_gb300 import symnmf
+    return symnmf
+
+
+DEV = "cuda:0"
+
+
+def to_dev(x, dtype=torch.float32):
+    return torch.tensor(np.asarray(x), dtype=dtype, device=DEV)
+
+
+def dequant(St):
+    return St.double().cpu().numpy()
+
+
+class Handle:
+    def __init__(self, L, S_t, n, k, dtype, lds=None):
+        self.L = L
+        self.S_t = S_t
+        self.n, self.k = n, k
+        self.h = L.symnmf_create(S_t, n, k, dtype) if lds is None else \
+            L.symnmf_create_ld(S_t, n, lds, k, dtype)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.L.symnmf_destroy(self.h)
+
+    def get(self, which=None):
+        out = torch.empty(self.n, self.k, dtype=torch.float32, device=DEV)
+        if which is None:
+            self.L.symnmf_get_H(self.h, out)
+        else:
+            self.L.symnmf_get_buffer(self.h, which, out)
+        torch.cuda.synchronize()
+        return out.double().cpu().numpy()
+
+
+def problem(n, k, kind="tpdm", seed=0, dtype=torch.float32):
+    if kind == "tpdm":
+        inst = gen.tpdm_groups(n=n, groups=max(2, k), T=max(400, 4 * n), q=0.05, seed=seed)
+    else:
+        inst = gen.corr_planted(n=n, groups=max(2, k), T=1000, seed=seed)
+    S_t = to_dev(inst.S, dtype)
+    S64 = dequant(S_t)
+    H0 = gen.init_scaled(float(S64.mean()), n, k, seed=seed)
+    H0_t = to_dev(H0)
+    return S_t, S64, H0_t, H0_t.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (7, 3), (127, 8), (128, 8), (129, 5), (300, 16),
+                                 (1000, 32), (2000, 64), (2500, 1)])
+def test_grad_and_objective_fp32(L, n, k):
+    S_t, S64, H0_t, H64 = problem(n, k, seed=n)
+    with Handle(L, S_t, n, k, L.F32) as hd:
+        L.symnmf_set_H(hd.h, H0_t)
+        G = torch.empty(n, k, dtype=torch.float32, device=DEV)
+        L.symnmf_grad(hd.h, G)
+        f, E = L.symnmf_objective(hd.h)
+        torch.cuda.synchronize()
+        Gref = O.gradient(S64, H64)
+        assert O.rel_err(G.double().cpu().numpy(), Gref) < REL_FP32
+        normS2 = float(np.sum(S64 * S64))
+        assert abs(L.symnmf_get_norm(hd.h) - normS2) <= 1e-12 * normS2
+        fref = O.objective_trace(S64, H64)
+        assert abs(f - fref) <= OBJ_ABS * normS2
+        assert abs(E - fref / normS2) <= OBJ_ABS
+
+
+@pytest.mark.parametrize("n,k", [(300, 8), (1031, 32)])
+def test_grad_bf16_storage(L, n, k):
+    """BF16-stored S: the kernel error against the oracle on the same
+    (dequantised) matrix is FP32-level."""
+    S_t, S64, H0_t, H64 = problem(n, k, seed=3, dtype=torch.bfloat16)
+    with Handle(L, S_t, n, k, L.BF16) as hd:
+        L.symnmf_set_H(hd.h, H0_t)
+        G = torch.empty(n, k, dtype=torch.float32, device=DEV)
+        L.symnmf_grad(hd.h, G)
+        torch.cuda.synchronize()
+        assert O.rel_err(G.double().cpu().numpy(), O.gradient(S64, H64)) < REL_FP32
+
+
+def _teacher_state(method, S64, H64, steps, hp):
+    s = O.Solver(S64, H64, hp)
+    for _ in range(steps):
+        s.step()
+    return s
+
+
+def _load_state(L, hd, s):
+    """Load the oracle state (rounded to FP32) into the handle."""
+    L.symnmf_set_H(hd.h, to_dev(s.H))
+    L.symnmf_set_buffer(hd.h, L.BUF_ACC, to_dev(s.A))
+    L.symnmf_set_buffer(hd.h, L.BUF_MOM, to_dev(s.M))
+    L.symnmf_set_buffer(hd.h, L.BUF_SNAPSHOT, to_dev(s.mu))
+    c = L.symnmf_ctrl()
+    oc = s.ctrl
+    c.t, c.E0, c.E_prev, c.phi = oc.t, oc.E0, oc.E_prev, oc.phi
+    c.sumA_post, c.E_at_reset = oc.sumA_post, oc.E_at_reset
+    c.have_prev, c.stag_count, c.resets = int(oc.have_prev), oc.stag_count, oc.resets
+    c.resets_enabled, c.cooldown, c.converged = int(oc.resets_enabled), int(oc.cooldown), 0
+    L.symnmf_set_ctrl(hd.h, c)
+
+
+def _rounded(s):
+    """The oracle state rounded to FP32, as the GPU holds it."""
+    for name in ("H", "A", "M", "mu"):
+        setattr(s, name, getattr(s, name).astype(np.float32).astype(np.float64))
+    return s
+
+
+@pytest.mark.parametrize("method", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("t0", [0, 7, 13])
+def test_teacher_forced_single_step(L, method, t0):
+    """From the same (FP32-rounded) state at iteration t0 both sides take one
+    step; H, G/v, m and the snapshot agree to 1e-5 relative."""
+    n, k = 700, 8
+    S_t, S64, H0_t, H64 = problem(n, k, seed=11)
+    hp = O.HParams.paper(method)
+    hp.eta = 0.05 if method != O.RMSPROP else 0.01
+    hp.snapshot_period = 3
+    hp.phi0 = 0.3
+    s = _teacher_state(method, S64, H64, t0, hp)
+    s = _rounded(s)
+    with Handle(L, S_t, n, k, L.F32) as hd:
+        _load_state(L, hd, s)
+        lhp = L.symnmf_hparams_default(method, eta=hp.eta, snapshot_period=3, phi0=0.3)
+        L.symnmf_step(hd.h, lhp, 1)
+        s.step()
+        for which, ref in [(None, s.H), (L.BUF_ACC, s.A), (L.BUF_MOM, s.M), (L.BUF_SNAPSHOT, s.mu),
+                           (L.BUF_GRAD, s.g)]:
+            got = hd.get(which)
+            assert O.rel_err(got, ref) < REL_FP32, (which, O.rel_err(got, ref))
+
+
+def test_free_running_adagrad_n512(L):
+    """The n=512, k=8 planted correlation workload: 500 AdaGrad iterations
+    from H0 ~ U[0, 0.1] (seed 0), eta = 2.0 and 0.1, against the oracle."""
+    inst = gen.corr_planted(n=512, groups=8, T=2000, seed=0)
+    S_t = to_dev(inst.S)
+    S64 = dequant(S_t)
+    H0_t = to_dev(gen.init_uniform(512, 8, 0.1, seed=0))
+    H64 = H0_t.double().cpu().numpy()
+    for eta in (2.0, 0.1):
+        hp = O.HParams.paper(O.ADAGRAD)
+        hp.eta = eta
+        s = O.Solver(S64, H64, hp)
+        s.run(500)
+        with Handle(L, S_t, 512, 8, L.F32) as hd:
+            L.symnmf_set_H(hd.h, H0_t)
+            L.symnmf_step(hd.h, L.symnmf_hparams_default(O.ADAGRAD, eta=eta), 500)
+            Hg = hd.get()
+            tr = L.symnmf_get_trace(hd.h)
+        assert len(tr) == len(s.records) == 500
+        Eg = np.array([r.E for r in tr])
+        Er = np.array([r.E for r in s.records])
+        assert np.max(np.abs(Eg - Er) / np.abs(Er)) < 1e-5
+        assert O.rel_err(Hg, s.H) < 1e-4
+        assert O.boundary_disagreement(Hg, s.H) <= 2
+
+
+def test_checkpoint_restore_is_bitwise(L):
+    n, k = 600, 8
+    S_t, S64, H0_t, _ = problem(n, k, seed=5)
+    hp = L.symnmf_hparams_default(L.PIECEWISE_ADAGRAD)
+    with Handle(L, S_t, n, k, L.F32) as a, Handle(L, S_t, n, k, L.F32) as b:
+        L.symnmf_set_H(a.h, H0_t)
+        L.symnmf_step(a.h, hp, 80)
+        L.symnmf_set_H(b.h, H0_t)
+        L.symnmf_step(b.h, hp, 40)
+        blob = L.symnmf_get_state(b.h)
+        L.symnmf_set_H(b.h, torch.zeros_like(H0_t))
+        L.symnmf_set_state(b.h, blob)
+        L.symnmf_step(b.h, hp, 40)
+        assert np.array_equal(a.get(), b.get())
+        assert np.array_equal(a.get(L.BUF_ACC), b.get(L.BUF_ACC))
+
+
+def test_runs_are_deterministic(L):
+    n, k = 900, 16
+    S_t, _, H0_t, _ = problem(n, k, seed=6)
+    outs = []
+    for _ in range(2):
+        with Handle(L, S_t, n, k, L.F32) as hd:
+            L.symnmf_set_H(hd.h, H0_t)
+            L.symnmf_step(hd.h, L.symnmf_hparams_default(L.ADAGRAD), 30)
+            outs.append((hd.get(), [r.f for r in L.symnmf_get_trace(hd.h)]))
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+
+
+@pytest.mark.parametrize("method", [0, 1, 2, 3, 4])
+def test_zero_factor_is_fixed_point(L, method):
+    n, k = 256, 4
+    S_t, _, _, _ = problem(n, k, seed=7)
+    with Handle(L, S_t, n, k, L.F32) as hd:
+        L.symnmf_set_H(hd.h, torch.zeros(n, k, device=DEV))
+        L.symnmf_step(hd.h, L.symnmf_hparams_default(method), 25)
+        assert np.all(hd.get() == 0)
+        assert L.symnmf_get_trace(hd.h)[0].E == 1.0
+
+
+def test_planted_exact_converges(L):
+    H0, S = gen.planted_exact(400, 6, seed=2)
+    S_t = to_dev(S)
+    Hs = H0 + np.random.default_rng(0).uniform(0, 0.05, H0.shape)
+    with Handle(L, S_t, 400, 6, L.F32) as hd:
+        L.symnmf_set_H(hd.h, to_dev(Hs))
+        st, stats = L.symnmf_step(hd.h, L.symnmf_hparams_default(L.ADAGRAD, eta=0.05), 3000)
+        assert st == L.CONVERGED and stats.E < 1e-3
+        Hg = hd.get()
+    assert O.objective_explicit(S, Hg) / float(np.sum(S * S)) < 1e-3
+
+
+def test_converged_solve_matches_oracle(L):
+    """A converging TPDM solve: the GPU stops at the same check as the
+    oracle and the factors agree after optimal column matching."""
+    n, k = 256, 4
+    inst = gen.tpdm_groups(n=n, groups=k, T=2000, q=0.05, seed=3)
+    S_t = to_dev(inst.S)
+    S64 = dequant(S_t)
+    H0_t = to_dev(gen.init_scaled(float(S64.mean()), n, k, seed=3))
+    H64 = H0_t.double().cpu().numpy()
+    for method in (O.ADAGRAD, O.RMSPROP, O.PIECEWISE):
+        s = O.Solver(S64, H64, O.HParams.paper(method))
+        s.run(4000)
+        with Handle(L, S_t, n, k, L.F32) as hd:
+            L.symnmf_set_H(hd.h, H0_t)
+            st, stats = L.symnmf_step(hd.h, L.symnmf_hparams_default(method), 4000)
+            Hg = hd.get()
+        assert s.records[-1].converged and st == L.CONVERGED
+        assert stats.iter == s.ctrl.t
+        assert O.factor_error(Hg, s.H) < 1e-3
+
+
+def test_invalid_calls(L):
+    n, k = 64, 4
+    S_t, _, H0_t, _ = problem(n, k, seed=8)
+    with Handle(L, S_t, n, k, L.F32) as hd:
+        L.symnmf_set_H(hd.h, H0_t)
+        bad = L.symnmf_hparams_default(L.ADAGRAD, block_rows=100)
+        with pytest.raises(L.SymNMFError) as e:
+            L.symnmf_step(hd.h, bad, 1)
+        assert e.value.status == L.ERR_INVALID
+        with pytest.raises(L.SymNMFError) as e:
+            L.symnmf_set_buffer(hd.h, L.BUF_GRAD, H0_t)
+        assert e.value.status == L.ERR_INVALID
+        L.symnmf_step(hd.h, L.symnmf_hparams_default(L.ADAGRAD), 2)   # still usable
+    S8 = torch.zeros(128, 128, dtype=torch.uint8, device=DEV)
+    h = L.symnmf_create(S8, 128, 4, L.FP8E4M3)
+    try:
+        L.symnmf_set_H(h, torch.zeros(128, 4, device=DEV))
+        with pytest.raises(L.SymNMFError) as e:
+            L.symnmf_step(h, L.symnmf_hparams_default(L.ADAGRAD), 1)
+        assert e.value.status == L.ERR_INVALID
+    finally:
+        L.symnmf_destroy(h)
+
+
+def test_nonfinite_input_reported(L):
+    n, k = 200, 4
+    S_t, _, H0_t, _ = problem(n, k, seed=9)
+    S_bad = S_t.clone()
+    S_bad[3, 5] = float("nan")
+    with Handle(L, S_bad, n, k, L.F32) as hd:
+        L.symnmf_set_H(hd.h, H0_t)
+        with pytest.raises(L.SymNMFError) as e:
+            L.symnmf_step(hd.h, L.symnmf_hparams_default(L.ADAGRAD), 5)
+        assert e.value.status == L.ERR_NONFINITE
+        with pytest.raises(L.SymNMFError) as e:
+            L.symnmf_step(hd.h, L.symnmf_hparams_default(L.ADAGRAD), 1)
+        assert e.value.status == L.ERR_STATE
+        L.symnmf_set_H(hd.h, H0_t)      # clears the error state
+        hd.S_t = S_bad
+
+
+def test_full_size_sampled_rows_n20000(L):
+    """n=20000, k=32 TPDM at full size: sampled gradient rows against the
+    oracle's row formula g_i = 4 (h_i (H^T H) - S_i H)."""
+    n, k = 20000, 32
+    inst = gen.tpdm_groups(n=n, groups=32, T=5000, q=0.05, seed=0, device=DEV,
+                           dtype=torch.float32, materialize="torch")
+    S_t = inst.S
+    H0_t = to_dev(gen.init_scaled(float(S_t.double().mean()), n, k, seed=0))
+    H64 = H0_t.double().cpu().numpy()
+    with Handle(L, S_t, n, k, L.F32) as hd:
+        L.symnmf_set_H(hd.h, H0_t)
+        G = torch.empty(n, k, dtype=torch.float32, device=DEV)
+        L.symnmf_grad(hd.h, G)
+        torch.cuda.synchronize()
+        rows = np.random.default_rng(0).choice(n, 64, replace=False)
+        Srows = S_t[torch.tensor(rows, device=DEV)].double().cpu().numpy()
+        gram = H64.T @ H64
+        ref = 4.0 * (H64[rows] @ gram - Srows @ H64)
+        got = G.double().cpu().numpy()[rows]
+        assert O.rel_err(got, ref) < REL_FP32
