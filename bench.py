@@ -37,6 +37,7 @@ WORKLOADS = {
     # name: (generator, n, k, dtype, method, eta)
     "tpdm_n20000_k32_fp32_adagrad": ("tpdm", 20000, 32, "f32", 0, 2.0),
     "tpdm_n20000_k32_fp32_rmsprop": ("tpdm", 20000, 32, "f32", 1, 0.05),
+    "tpdm_n20000_k32_bf16_adagrad": ("tpdm", 20000, 32, "bf16", 0, 2.0),
     "corr_n100000_k32_fp32_adagrad": ("corr", 100000, 32, "f32", 0, 2.0),
     "corr_n100000_k32_bf16_adagrad": ("corr", 100000, 32, "bf16", 0, 2.0),
 }

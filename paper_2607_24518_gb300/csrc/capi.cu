@@ -69,6 +69,8 @@ struct symnmf_ctx {
   float *hmed = nullptr;
   double *norm_parts = nullptr;
   int n_norm_parts = 0;
+  int *dev_err = nullptr;     // device error word (bounded-wait timeouts)
+  int *host_err = nullptr;    // pinned mirror
   // host state
   symnmf_ctrl ctrl{};
   std::deque<symnmf_record> trace;
@@ -135,9 +137,10 @@ void free_all(symnmf_t h) {
                   (void *)h->P, (void *)h->Q, (void *)h->slots, (void *)h->chunk,
                   (void *)h->gramI, (void *)h->gramJ, (void *)h->dlists, (void *)h->ring,
                   (void *)h->hist, (void *)h->sel, (void *)h->dmed, (void *)h->dsum,
-                  (void *)h->norm_parts})
+                  (void *)h->norm_parts, (void *)h->dev_err})
     cudaFree(p);
-  for (void *p : {(void *)h->hlists, (void *)h->hring, (void *)h->hsum, (void *)h->hmed})
+  for (void *p : {(void *)h->hlists, (void *)h->hring, (void *)h->hsum, (void *)h->hmed,
+                  (void *)h->host_err})
     if (p) cudaFreeHost(p);
   for (int i = 0; i < kStages; ++i)
     if (h->stage_ev[i]) cudaEventDestroy(h->stage_ev[i]);
@@ -301,7 +304,7 @@ void blocks_to_tiles(symnmf_t h, const std::vector<int64_t> &blocks, int64_t blo
 }
 
 int prod(symnmf_t h, const int *row_list, int n_rows, const int *col_list, int n_cols, float *out,
-         int *nsplit_out) {
+         PartLayout *lay) {
   ProdArgs a{};
   a.S = h->S;
   a.lds = h->lds;
@@ -324,14 +327,24 @@ int prod(symnmf_t h, const int *row_list, int n_rows, const int *col_list, int n
   ns = std::max(1, std::min(ns, std::min(64, n_cols)));
   if ((int64_t)ns * n_rows > h->pq_cap_tiles) ns = (int)std::max<int64_t>(1, h->pq_cap_tiles / n_rows);
   a.nsplit = ns;
-  *nsplit_out = ns;
+  lay->nsplit = ns;
+  lay->skG = 0;
+  lay->ncols = n_cols;
+  const bool tc = use_tc(h);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (h->profiling) {
     CK(prof_event(h, &e0));
     CK(prof_event(h, &e1));
     CK(cudaEventRecord(e0, h->stream));
   }
-  cudaError_t e = use_tc(h) ? launch_prod_tc(a, h->stream, h->num_sms) : launch_prod_simt(a, h->stream);
+  cudaError_t e;
+  if (tc) {
+    a.nsplit = 1;
+    lay->nsplit = 1;
+    e = launch_prod_tc(a, h->stream, h->num_sms, &lay->skG, h->dev_err);
+  } else {
+    e = launch_prod_simt(a, h->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "product kernel");
   if (h->profiling) {
     CK(cudaEventRecord(e1, h->stream));
@@ -382,12 +395,14 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t) {
   e.update = 1;
   int rc;
   if (full) {
-    int ns = 1;
-    if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ns))) return rc;
+    PartLayout ly;
+    if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly))) return rc;
     e.mode = MODE_FULL;
     e.gram = h->gram32[cur];
     e.P = h->P;
-    e.nsplit = ns;
+    e.nsplit = ly.nsplit;
+    e.skG1 = ly.skG;
+    e.ncols1 = ly.ncols;
     e.n1 = h->ntiles;
     e.store_mu = (hp->method == SYMNMF_ROW_SVRG || hp->method == SYMNMF_BLOCK_SVRG_ADAPTGROW);
   } else {
@@ -419,30 +434,36 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t) {
     if ((rc = upload_slot(h, t, hl, dl))) return rc;
     int *dI = dl, *dJ = dl + h->ntiles, *dposI = dl + 2 * h->ntiles, *dposJ = dl + 3 * h->ntiles;
     if (hp->method == SYMNMF_ROW_SVRG) {
-      int ns = 1;
-      if ((rc = prod(h, dI, (int)tI.size(), nullptr, h->ntiles, h->P, &ns))) return rc;
+      PartLayout ly;
+      if ((rc = prod(h, dI, (int)tI.size(), nullptr, h->ntiles, h->P, &ly))) return rc;
       e.mode = MODE_ROWS;
       e.gram = h->gram32[cur];
       e.P = h->P;
-      e.nsplit = ns;
+      e.nsplit = ly.nsplit;
+      e.skG1 = ly.skG;
+      e.ncols1 = ly.ncols;
       e.pos1 = dposI;
       e.n1 = (int)tI.size();
     } else {
       CK(launch_gram_subset(h->gram_part[cur], h->kp, dI, (int)tI.size(), dJ, (int)tJ.size(),
                             h->gramI, h->gramJ, h->stream));
-      int ns1 = 1, ns2 = 1;
-      if ((rc = prod(h, dI, (int)tI.size(), dJ, (int)tJ.size(), h->P, &ns1))) return rc;
-      if ((rc = prod(h, dJ, (int)tJ.size(), dI, (int)tI.size(), h->Q, &ns2))) return rc;
+      PartLayout l1, l2;
+      if ((rc = prod(h, dI, (int)tI.size(), dJ, (int)tJ.size(), h->P, &l1))) return rc;
+      if ((rc = prod(h, dJ, (int)tJ.size(), dI, (int)tI.size(), h->Q, &l2))) return rc;
       e.mode = MODE_BLOCK;
       e.coef = 2.f;
       e.gramI = h->gramI;
       e.gramJ = h->gramJ;
       e.P = h->P;
-      e.nsplit = ns1;
+      e.nsplit = l1.nsplit;
+      e.skG1 = l1.skG;
+      e.ncols1 = l1.ncols;
       e.pos1 = dposI;
       e.n1 = (int)tI.size();
       e.Q = h->Q;
-      e.nsplit2 = ns2;
+      e.nsplit2 = l2.nsplit;
+      e.skG2 = l2.skG;
+      e.ncols2 = l2.ncols;
       e.pos2 = dposJ;
       e.n2 = (int)tJ.size();
     }
@@ -481,7 +502,11 @@ int sync_records(symnmf_t h, int64_t upto, const std::vector<double> &phis) {
                        cudaMemcpyDeviceToHost, h->stream));
     a += len;
   }
+  CK(cudaMemcpyAsync(h->host_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (h->host_err[0] != 0)
+    return fail(h, SYMNMF_ERR_TIMEOUT,
+                "a bounded device wait gave up (code " + std::to_string(h->host_err[0]) + ")");
   for (int64_t t = from; t < upto; ++t) {
     const double phi = (t - from) < (int64_t)phis.size() ? phis[t - from] : h->ctrl.phi;
     h->trace.push_back(to_record(h->hring[t % kRing], phi));
@@ -678,6 +703,8 @@ int symnmf_create_ld(const void *S, int64_t n, int64_t lds, int32_t k, int32_t d
   if (e == cudaSuccess) e = dalloc(&h->dmed, 1);
   if (e == cudaSuccess) e = dalloc(&h->dsum, 4);
   if (e == cudaSuccess) e = dalloc(&h->norm_parts, (size_t)h->n_norm_parts);
+  if (e == cudaSuccess) e = dalloc(&h->dev_err, 4);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_err, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hlists, sizeof(int) * kStages * 4 * h->ntiles);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hring, sizeof(DevRecord) * (kRing + 1));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hsum, sizeof(double) * 4);
@@ -827,13 +854,15 @@ int symnmf_grad(symnmf_t h, float *G) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!G) return SYMNMF_ERR_INVALID;
-  int ns = 1;
-  if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ns))) return rc;
+  PartLayout ly;
+  if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly))) return rc;
   EpiArgs e = base_epi(h, nullptr);
   e.mode = MODE_GRAD_ONLY;
   e.gram = h->gram32[h->cur];
   e.P = h->P;
-  e.nsplit = ns;
+  e.nsplit = ly.nsplit;
+  e.skG1 = ly.skG;
+  e.ncols1 = ly.ncols;
   e.n1 = h->ntiles;
   e.gcaller = G;
   CK(launch_epilogue(e, h->stream));
@@ -843,13 +872,15 @@ int symnmf_grad(symnmf_t h, float *G) {
 int symnmf_objective(symnmf_t h, double *f, double *E) {
   int rc = check_handle(h);
   if (rc) return rc;
-  int ns = 1;
-  if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ns))) return rc;
+  PartLayout ly;
+  if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly))) return rc;
   EpiArgs e = base_epi(h, nullptr);
   e.mode = MODE_GRAD_ONLY;
   e.gram = h->gram32[h->cur];
   e.P = h->P;
-  e.nsplit = ns;
+  e.nsplit = ly.nsplit;
+  e.skG1 = ly.skG;
+  e.ncols1 = ly.ncols;
   e.n1 = h->ntiles;
   e.slots = h->slots;
   CK(launch_epilogue(e, h->stream));

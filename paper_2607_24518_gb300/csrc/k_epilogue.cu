@@ -75,6 +75,27 @@ __device__ void tile_tail(const float (*Hn)[KP + 1], int64_t r0, uint16_t *Bt, i
   }
 }
 
+// CTA of a stream-K launch whose unit range holds unit x
+__device__ __forceinline__ int64_t sk_cta(int64_t x, int64_t W, int64_t G) {
+  int64_t b = x * G / W;
+  while (b + 1 < G && (b + 1) * W / G <= x) ++b;
+  while (b > 0 && b * W / G > x) --b;
+  return b;
+}
+
+// sum of the partials of row r, column c of list position p (fixed order)
+template <int KP>
+__device__ __forceinline__ float part_sum(const float *P, int nsplit, int skG, int ncols, int nlist,
+                                          int p, int r, int c, int64_t b0, int64_t b1) {
+  float v = 0.f;
+  if (skG > 0) {
+    for (int64_t b = b0; b <= b1; ++b) v += P[((b + p) * kTileRows + r) * KP + c];
+  } else {
+    for (int s = 0; s < nsplit; ++s) v += P[(((int64_t)s * nlist + p) * kTileRows + r) * KP + c];
+  }
+  return v;
+}
+
 template <int KP>
 constexpr size_t epi_smem_bytes() {
   return (size_t)(2 * kTileRows * (KP + 1) + 2 * KP * (KP + 1)) * sizeof(float);
@@ -109,6 +130,17 @@ __global__ void __launch_bounds__(256) epilogue_kernel(EpiArgs a) {
     p1 = a.pos1[tile];
     if (block) p2 = a.pos2[tile];
   }
+  int64_t b10 = 0, b11 = 0, b20 = 0, b21 = 0;
+  if (p1 >= 0 && a.skG1 > 0) {
+    const int64_t W = (int64_t)a.n1 * a.ncols1;
+    b10 = sk_cta((int64_t)p1 * a.ncols1, W, a.skG1);
+    b11 = sk_cta((int64_t)p1 * a.ncols1 + a.ncols1 - 1, W, a.skG1);
+  }
+  if (p2 >= 0 && a.skG2 > 0) {
+    const int64_t W = (int64_t)a.n2 * a.ncols2;
+    b20 = sk_cta((int64_t)p2 * a.ncols2, W, a.skG2);
+    b21 = sk_cta((int64_t)p2 * a.ncols2 + a.ncols2 - 1, W, a.skG2);
+  }
   __syncthreads();
 
   float tr = 0.f, kkt2 = 0.f, sumA = 0.f;
@@ -123,9 +155,8 @@ __global__ void __launch_bounds__(256) epilogue_kernel(EpiArgs a) {
       if (p1 >= 0 || p2 >= 0) {
         g = 0.f;
         if (p1 >= 0) {
-          float p = 0.f;
-          for (int s = 0; s < a.nsplit; ++s)
-            p += a.P[(((int64_t)s * a.n1 + p1) * kTileRows + r) * KP + c];
+          const float p =
+              part_sum<KP>(a.P, a.nsplit, a.skG1, a.ncols1, a.n1, p1, r, c, b10, b11);
           float hg = 0.f;
 #pragma unroll
           for (int d = 0; d < KP; ++d) hg = fmaf(Hs[r][d], G1[d][c], hg);
@@ -133,9 +164,8 @@ __global__ void __launch_bounds__(256) epilogue_kernel(EpiArgs a) {
           tr = fmaf(h, p, tr);
         }
         if (p2 >= 0) {
-          float q = 0.f;
-          for (int s = 0; s < a.nsplit2; ++s)
-            q += a.Q[(((int64_t)s * a.n2 + p2) * kTileRows + r) * KP + c];
+          const float q =
+              part_sum<KP>(a.Q, a.nsplit2, a.skG2, a.ncols2, a.n2, p2, r, c, b20, b21);
           float hg = 0.f;
 #pragma unroll
           for (int d = 0; d < KP; ++d) hg = fmaf(Hs[r][d], G2[d][c], hg);

@@ -46,6 +46,16 @@ struct ProdArgs {
   float *out;
 };
 
+// Partial-sum layout of a product launch: split layout (SIMT: nsplit
+// contiguous column shares, slot = split * n_rows + row_pos) or stream-K
+// layout (tensor core: CTA b's segment of row position p in slot b + p,
+// CTA b covering units [b W / G, (b+1) W / G) of W = n_rows * n_cols).
+struct PartLayout {
+  int nsplit = 1;
+  int skG = 0;      // > 0: stream-K with skG CTAs
+  int ncols = 0;
+};
+
 struct EpiArgs {
   int64_t n;
   int k, kp, ntiles;
@@ -66,10 +76,12 @@ struct EpiArgs {
   const float *gramJ;    // block mode: H_J^T H_J
   const float *P;        // product partials for rows in list 1
   int nsplit;
+  int skG1, ncols1;      // stream-K layout of P (skG1 > 0)
   const int *pos1;       // tile -> position in list 1 (or -1); nullptr in full mode
   int n1;                // length of list 1
   const float *Q;        // block mode: partials of S_{J,I} H_I, list 2 = J
   int nsplit2;
+  int skG2, ncols2;
   const int *pos2;
   int n2;
   float coef;            // 4 (full/rows) or 2 (block)
@@ -81,7 +93,7 @@ constexpr int kSlotStride = 4;
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_prod_simt(const ProdArgs &a, cudaStream_t s);
-cudaError_t launch_prod_tc(const ProdArgs &a, cudaStream_t s, int num_sms);
+cudaError_t launch_prod_tc(const ProdArgs &a, cudaStream_t s, int num_sms, int *G_out, int *err);
 bool tc_supported(int dtype, int kp);
 cudaError_t launch_epilogue(const EpiArgs &a, cudaStream_t s);
 // per-tile Bt copy and Gram partial of H (init / teacher forcing)
