@@ -46,7 +46,8 @@ struct symnmf_ctx {
   bool tc_layout_ok = false;
   // owned device memory
   float *H[2] = {nullptr, nullptr};
-  uint16_t *Bt[2] = {nullptr, nullptr};
+  void *Bt[2] = {nullptr, nullptr};
+  int bt_fmt = 0;          // 0: bf16 hi/lo, 1: tf32 hi/lo in float
   float *gram_part[2] = {nullptr, nullptr};
   double *gram64[2] = {nullptr, nullptr};
   float *gram32[2] = {nullptr, nullptr};
@@ -70,6 +71,10 @@ struct symnmf_ctx {
   double *norm_parts = nullptr;
   int n_norm_parts = 0;
   int *dev_err = nullptr;     // device error word (bounded-wait timeouts)
+  int *counters = nullptr;    // reduction last-arriver counters
+  int *tile_cnt = nullptr;    // per-tile stream-K arrival counters
+  double *lvl1 = nullptr;     // reduction level-1 sums
+  int ntc = 0;                // tile chunks of 32
   int *host_err = nullptr;    // pinned mirror
   // host state
   symnmf_ctrl ctrl{};
@@ -137,7 +142,8 @@ void free_all(symnmf_t h) {
                   (void *)h->P, (void *)h->Q, (void *)h->slots, (void *)h->chunk,
                   (void *)h->gramI, (void *)h->gramJ, (void *)h->dlists, (void *)h->ring,
                   (void *)h->hist, (void *)h->sel, (void *)h->dmed, (void *)h->dsum,
-                  (void *)h->norm_parts, (void *)h->dev_err})
+                  (void *)h->norm_parts, (void *)h->dev_err, (void *)h->counters, (void *)h->tile_cnt,
+                  (void *)h->lvl1})
     cudaFree(p);
   for (void *p : {(void *)h->hlists, (void *)h->hring, (void *)h->hsum, (void *)h->hmed,
                   (void *)h->host_err})
@@ -172,14 +178,37 @@ int compute_norm(symnmf_t h) {
   return SYMNMF_OK;
 }
 
+ReduceArgs reduce_args(symnmf_t h, const double *slots, const float *gram_part, long long t,
+                       int full) {
+  ReduceArgs r{};
+  r.slots = slots;
+  r.gram_part = gram_part;
+  r.ntiles = h->ntiles;
+  r.k = h->k;
+  r.n = h->n;
+  r.normS2 = h->normS2;
+  r.t = t;
+  r.full = full;
+  r.gram64_cur = h->gram64[h->cur];
+  r.gram64_next = h->gram64[1 - h->cur];
+  r.gram32_next = h->gram32[1 - h->cur];
+  r.rec = h->ring + (t >= 0 ? (t % kRing) : kRing);
+  r.lvl1 = h->lvl1;
+  r.counters = h->counters;
+  return r;
+}
+
 // Bt copy, per-tile Gram partials and the reduced Gram of H[cur]
 int refresh_derived(symnmf_t h) {
   const int c = h->cur;
-  CK(launch_prepare_tiles(h->H[c], h->n, h->k, h->kp, h->Bt[c], h->ldb, h->gram_part[c],
-                          h->stream));
-  CK(launch_reduce(nullptr, h->gram_part[c], h->ntiles, h->kp, h->k, h->n, h->normS2, 0, 0,
-                   h->chunk, h->nchunks, h->gram64[c], h->gram64[c], h->gram32[c], nullptr,
-                   h->stream));
+  CK(launch_prepare_tiles(h->H[c], h->n, h->k, h->kp, h->Bt[c], h->bt_fmt, h->ldb,
+                          h->gram_part[c], h->stream));
+  ReduceArgs r = reduce_args(h, nullptr, h->gram_part[c], -1, 0);
+  r.gram64_cur = nullptr;
+  r.gram64_next = h->gram64[c];
+  r.gram32_next = h->gram32[c];
+  r.rec = nullptr;
+  CK(launch_reduce_iter(r, h->kp, h->stream));
   return SYMNMF_OK;
 }
 
@@ -304,7 +333,7 @@ void blocks_to_tiles(symnmf_t h, const std::vector<int64_t> &blocks, int64_t blo
 }
 
 int prod(symnmf_t h, const int *row_list, int n_rows, const int *col_list, int n_cols, float *out,
-         PartLayout *lay) {
+         PartLayout *lay, const EpiArgs *fuse = nullptr) {
   ProdArgs a{};
   a.S = h->S;
   a.lds = h->lds;
@@ -316,6 +345,7 @@ int prod(symnmf_t h, const int *row_list, int n_rows, const int *col_list, int n
   a.kp = h->kp;
   a.H = h->H[h->cur];
   a.Bt = h->Bt[h->cur];
+  a.bt_fmt = h->bt_fmt;
   a.ldb = h->ldb;
   a.row_list = row_list;
   a.n_rows_list = n_rows;
@@ -341,7 +371,7 @@ int prod(symnmf_t h, const int *row_list, int n_rows, const int *col_list, int n
   if (tc) {
     a.nsplit = 1;
     lay->nsplit = 1;
-    e = launch_prod_tc(a, h->stream, h->num_sms, &lay->skG, h->dev_err);
+    e = launch_step_tc(a, fuse, h->tile_cnt, h->stream, h->num_sms, &lay->skG, h->dev_err);
   } else {
     e = launch_prod_simt(a, h->stream);
   }
@@ -389,22 +419,30 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t) {
   EpiArgs e = base_epi(h, hp);
   e.Hn = h->H[nxt];
   e.Btn = h->Bt[nxt];
+  e.bt_fmt = h->bt_fmt;
   e.gram_part = h->gram_part[nxt];
   e.slots = h->slots;
   e.gout = h->g;
   e.update = 1;
   int rc;
+  bool fused_done = false;
   if (full) {
-    PartLayout ly;
-    if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly))) return rc;
     e.mode = MODE_FULL;
     e.gram = h->gram32[cur];
     e.P = h->P;
-    e.nsplit = ly.nsplit;
-    e.skG1 = ly.skG;
-    e.ncols1 = ly.ncols;
     e.n1 = h->ntiles;
     e.store_mu = (hp->method == SYMNMF_ROW_SVRG || hp->method == SYMNMF_BLOCK_SVRG_ADAPTGROW);
+    PartLayout ly;
+    if (use_tc(h)) {
+      // one fused launch: product and per-tile epilogue
+      if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly, &e))) return rc;
+      fused_done = true;
+    } else {
+      if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly))) return rc;
+      e.nsplit = ly.nsplit;
+      e.skG1 = ly.skG;
+      e.ncols1 = ly.ncols;
+    }
   } else {
     int *hl, *dl;
     if ((rc = stage_slot(h, t, &hl, &dl))) return rc;
@@ -468,10 +506,9 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t) {
       e.n2 = (int)tJ.size();
     }
   }
-  CK(launch_epilogue(e, h->stream));
-  CK(launch_reduce(h->slots, h->gram_part[nxt], h->ntiles, h->kp, h->k, h->n, h->normS2, t,
-                   full ? 1 : 0, h->chunk, h->nchunks, h->gram64[cur], h->gram64[nxt],
-                   h->gram32[nxt], h->ring + (t % kRing), h->stream));
+  if (!fused_done) CK(launch_epilogue(e, h->stream));
+  CK(launch_reduce_iter(reduce_args(h, h->slots, h->gram_part[nxt], t, full ? 1 : 0), h->kp,
+                        h->stream));
   h->cur = nxt;
   return SYMNMF_OK;
 }
@@ -671,6 +708,7 @@ int symnmf_create_ld(const void *S, int64_t n, int64_t lds, int32_t k, int32_t d
   h->ntiles = (int)((n + kTileRows - 1) / kTileRows);
   h->ldb = (int64_t)h->ntiles * kTileRows;
   h->tc_layout_ok = ((uintptr_t)S % 16 == 0) && ((lds * (int64_t)esize(dtype)) % 16 == 0);
+  h->bt_fmt = (dtype == SYMNMF_F32) ? 1 : 0;
   reset_ctrl(&h->ctrl);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -680,7 +718,8 @@ int symnmf_create_ld(const void *S, int64_t n, int64_t lds, int32_t k, int32_t d
   h->n_norm_parts = 4 * std::max(1, h->num_sms);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = dalloc(&h->H[i], nkp);
-    if (e == cudaSuccess) e = dalloc(&h->Bt[i], (size_t)2 * h->kp * h->ldb);
+    if (e == cudaSuccess)
+      e = dalloc((uint8_t **)&h->Bt[i], (size_t)2 * h->kp * h->ldb * (h->bt_fmt ? 4 : 2));
     if (e == cudaSuccess) e = dalloc(&h->gram_part[i], (size_t)h->ntiles * h->kp * h->kp);
     if (e == cudaSuccess) e = dalloc(&h->gram64[i], (size_t)h->kp * h->kp);
     if (e == cudaSuccess) e = dalloc(&h->gram32[i], (size_t)h->kp * h->kp);
@@ -704,6 +743,10 @@ int symnmf_create_ld(const void *S, int64_t n, int64_t lds, int32_t k, int32_t d
   if (e == cudaSuccess) e = dalloc(&h->dsum, 4);
   if (e == cudaSuccess) e = dalloc(&h->norm_parts, (size_t)h->n_norm_parts);
   if (e == cudaSuccess) e = dalloc(&h->dev_err, 4);
+  h->ntc = (h->ntiles + 31) / 32;
+  if (e == cudaSuccess) e = dalloc(&h->counters, 64);
+  if (e == cudaSuccess) e = dalloc(&h->tile_cnt, (size_t)h->ntiles);
+  if (e == cudaSuccess) e = dalloc(&h->lvl1, (size_t)h->ntc * (4 + h->kp * h->kp));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_err, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hlists, sizeof(int) * kStages * 4 * h->ntiles);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hring, sizeof(DevRecord) * (kRing + 1));
@@ -793,6 +836,8 @@ int symnmf_set_H(symnmf_t h, const float *H) {
   CK(cudaMemsetAsync(h->M, 0, bytes, h->stream));
   CK(cudaMemsetAsync(h->mu, 0, bytes, h->stream));
   CK(cudaMemsetAsync(h->g, 0, bytes, h->stream));
+  CK(cudaMemsetAsync(h->counters, 0, sizeof(int) * 64, h->stream));
+  CK(cudaMemsetAsync(h->tile_cnt, 0, sizeof(int) * h->ntiles, h->stream));
   reset_ctrl(&h->ctrl);
   h->trace.clear();
   h->copied_upto = 0;
@@ -854,17 +899,18 @@ int symnmf_grad(symnmf_t h, float *G) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!G) return SYMNMF_ERR_INVALID;
-  PartLayout ly;
-  if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly))) return rc;
   EpiArgs e = base_epi(h, nullptr);
   e.mode = MODE_GRAD_ONLY;
   e.gram = h->gram32[h->cur];
   e.P = h->P;
+  e.n1 = h->ntiles;
+  e.gcaller = G;
+  PartLayout ly;
+  if (use_tc(h)) return prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly, &e);
+  if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly))) return rc;
   e.nsplit = ly.nsplit;
   e.skG1 = ly.skG;
   e.ncols1 = ly.ncols;
-  e.n1 = h->ntiles;
-  e.gcaller = G;
   CK(launch_epilogue(e, h->stream));
   return SYMNMF_OK;
 }
@@ -872,20 +918,23 @@ int symnmf_grad(symnmf_t h, float *G) {
 int symnmf_objective(symnmf_t h, double *f, double *E) {
   int rc = check_handle(h);
   if (rc) return rc;
-  PartLayout ly;
-  if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly))) return rc;
   EpiArgs e = base_epi(h, nullptr);
   e.mode = MODE_GRAD_ONLY;
   e.gram = h->gram32[h->cur];
   e.P = h->P;
-  e.nsplit = ly.nsplit;
-  e.skG1 = ly.skG;
-  e.ncols1 = ly.ncols;
   e.n1 = h->ntiles;
   e.slots = h->slots;
-  CK(launch_epilogue(e, h->stream));
-  CK(launch_reduce(h->slots, nullptr, h->ntiles, h->kp, h->k, h->n, h->normS2, -1, 1, h->chunk,
-                   h->nchunks, h->gram64[h->cur], nullptr, nullptr, h->ring + kRing, h->stream));
+  PartLayout ly;
+  if (use_tc(h)) {
+    if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly, &e))) return rc;
+  } else {
+    if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly))) return rc;
+    e.nsplit = ly.nsplit;
+    e.skG1 = ly.skG;
+    e.ncols1 = ly.ncols;
+    CK(launch_epilogue(e, h->stream));
+  }
+  CK(launch_reduce_iter(reduce_args(h, h->slots, nullptr, -1, 1), h->kp, h->stream));
   CK(cudaMemcpyAsync(h->hring + kRing, h->ring + kRing, sizeof(DevRecord),
                      cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));

@@ -1,0 +1,69 @@
+// Device helpers shared by the stand-alone epilogue and reduction kernels
+// and the fused epilogue of the tensor-core kernels: number formats of the
+// MMA copy of H, the stream-K slot arithmetic, and fixed-order summation.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "../../include/symnmf.h"
+#include "symnmf_internal.h"
+
+namespace symnmf {
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  __nv_bfloat16 b = __float2bfloat16_rn(x);
+  return *reinterpret_cast<uint16_t *>(&b);
+}
+__device__ __forceinline__ float bf16_val(uint16_t u) {
+  __nv_bfloat16 b = *reinterpret_cast<__nv_bfloat16 *>(&u);
+  return __bfloat162float(b);
+}
+// tf32 value of x >= 0 with the 13 low mantissa bits cleared
+__device__ __forceinline__ float tf32_trunc(float x) {
+  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+// x >= 0 rounded to the nearest tf32 value (ties away from zero)
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// CTA of a stream-K launch whose unit range [b W / G, (b+1) W / G) holds x
+__device__ __forceinline__ int64_t sk_cta(int64_t x, int64_t W, int64_t G) {
+  int64_t b = x * G / W;
+  while (b + 1 < G && (b + 1) * W / G <= x) ++b;
+  while (b > 0 && b * W / G > x) --b;
+  return b;
+}
+
+// Sum, in index order, `count` (<= 32) values at base[i * stride]; every
+// load is issued before the ordered additions.
+template <typename T>
+__device__ __forceinline__ double ordered_sum32(const T *base, int64_t stride, int count) {
+  double v[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = (j < count) ? (double)base[(int64_t)j * stride] : 0.0;
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) s += v[j];
+  return s;
+}
+
+// Fixed-order sum over nthr threads (et = 0..nthr-1): xor tree inside each
+// warp, then warp partials added in warp order.  scratch holds >= 33
+// doubles; bar() synchronises the participating threads.
+template <class Bar>
+__device__ __forceinline__ double group_sum(double v, int et, int nthr, Bar bar, double *scratch) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  bar();
+  if ((et & 31) == 0) scratch[et >> 5] = v;
+  bar();
+  if (et == 0) {
+    double r = 0.0;
+    for (int i = 0; i < (nthr >> 5); ++i) r += scratch[i];
+    scratch[32] = r;
+  }
+  bar();
+  return scratch[32];
+}
+
+}  // namespace symnmf

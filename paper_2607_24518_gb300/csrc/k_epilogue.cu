@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "../../include/symnmf.h"
+#include "epi_common.cuh"
 #include "symnmf_internal.h"
 
 namespace symnmf {
@@ -39,29 +40,30 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
   return sh[32];
 }
 
-__device__ __forceinline__ uint16_t bf16_bits(float x) {
-  __nv_bfloat16 b = __float2bfloat16_rn(x);
-  return *reinterpret_cast<uint16_t *>(&b);
-}
-__device__ __forceinline__ float bf16_val(uint16_t u) {
-  __nv_bfloat16 b = *reinterpret_cast<__nv_bfloat16 *>(&u);
-  return __bfloat162float(b);
-}
-
 // writes the bf16 hi/lo transposed copy and the Gram partial of the tile
 // held in smem Hn[128][KP+1]
 template <int KP>
-__device__ void tile_tail(const float (*Hn)[KP + 1], int64_t r0, uint16_t *Bt, int64_t ldb,
+__device__ void tile_tail(const float (*Hn)[KP + 1], int64_t r0, void *Bt, int bt_fmt, int64_t ldb,
                           float *gram_part, int tile) {
   const int tid = threadIdx.x;
-  if (Bt) {
+  if (Bt && bt_fmt == 0) {
+    uint16_t *B = reinterpret_cast<uint16_t *>(Bt);
     for (int e = tid; e < KP * kTileRows; e += blockDim.x) {
       const int c = e / kTileRows, r = e % kTileRows;
       const float v = Hn[r][c];
       const uint16_t hi = bf16_bits(v);
       const uint16_t lo = bf16_bits(v - bf16_val(hi));
-      Bt[(int64_t)c * ldb + r0 + r] = hi;
-      Bt[(int64_t)(KP + c) * ldb + r0 + r] = lo;
+      B[(int64_t)c * ldb + r0 + r] = hi;
+      B[(int64_t)(KP + c) * ldb + r0 + r] = lo;
+    }
+  } else if (Bt) {
+    float *B = reinterpret_cast<float *>(Bt);
+    for (int e = tid; e < KP * kTileRows; e += blockDim.x) {
+      const int c = e / kTileRows, r = e % kTileRows;
+      const float v = Hn[r][c];
+      const float hi = tf32_trunc(v);
+      B[(int64_t)c * ldb + r0 + r] = hi;
+      B[(int64_t)(KP + c) * ldb + r0 + r] = tf32_round(v - hi);
     }
   }
   if (gram_part) {
@@ -73,14 +75,6 @@ __device__ void tile_tail(const float (*Hn)[KP + 1], int64_t r0, uint16_t *Bt, i
       gram_part[(int64_t)tile * KP * KP + q] = s;
     }
   }
-}
-
-// CTA of a stream-K launch whose unit range holds unit x
-__device__ __forceinline__ int64_t sk_cta(int64_t x, int64_t W, int64_t G) {
-  int64_t b = x * G / W;
-  while (b + 1 < G && (b + 1) * W / G <= x) ++b;
-  while (b > 0 && b * W / G > x) --b;
-  return b;
 }
 
 // sum of the partials of row r, column c of list position p (fixed order)
@@ -101,8 +95,11 @@ constexpr size_t epi_smem_bytes() {
   return (size_t)(2 * kTileRows * (KP + 1) + 2 * KP * (KP + 1)) * sizeof(float);
 }
 
+constexpr int kEpiThreads = 512;
+
 template <int KP>
-__global__ void __launch_bounds__(256) epilogue_kernel(EpiArgs a) {
+__global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(EpiArgs a) {
+  constexpr int EPT = kTileRows * KP / kEpiThreads;  // elements per thread
   extern __shared__ float smem_epi[];
   float(*Hs)[KP + 1] = reinterpret_cast<float(*)[KP + 1]>(smem_epi);
   float(*Hn)[KP + 1] = reinterpret_cast<float(*)[KP + 1]>(smem_epi + kTileRows * (KP + 1));
@@ -113,13 +110,14 @@ __global__ void __launch_bounds__(256) epilogue_kernel(EpiArgs a) {
   const int tile = blockIdx.x, tid = threadIdx.x;
   const int64_t r0 = (int64_t)tile * kTileRows;
   const int rows = (int)((a.n - r0) < kTileRows ? (a.n - r0) : kTileRows);
-  for (int e = tid; e < kTileRows * KP; e += blockDim.x) {
+  const float *__restrict__ Hg = a.H;
+  for (int e = tid; e < kTileRows * KP; e += kEpiThreads) {
     const int r = e / KP, c = e % KP;
-    Hs[r][c] = (r < rows) ? a.H[(r0 + r) * KP + c] : 0.f;
+    Hs[r][c] = (r < rows) ? Hg[(r0 + r) * KP + c] : 0.f;
   }
   const bool block = (a.mode == MODE_BLOCK);
   const float *g1src = block ? a.gramJ : a.gram;
-  for (int e = tid; e < KP * KP; e += blockDim.x) {
+  for (int e = tid; e < KP * KP; e += kEpiThreads) {
     G1[e / KP][e % KP] = g1src[e];
     if (block) G2[e / KP][e % KP] = a.gramI[e];
   }
@@ -141,11 +139,34 @@ __global__ void __launch_bounds__(256) epilogue_kernel(EpiArgs a) {
     b20 = sk_cta((int64_t)p2 * a.ncols2, W, a.skG2);
     b21 = sk_cta((int64_t)p2 * a.ncols2 + a.ncols2 - 1, W, a.skG2);
   }
+
+  // phase 1: issue every global load of this thread's elements
+  float pv[EPT], qv[EPT], av[EPT], mv[EPT], uv[EPT];
+  const bool rms = (a.method == SYMNMF_RMSPROP);
+#pragma unroll
+  for (int i = 0; i < EPT; ++i) {
+    const int e = tid + i * kEpiThreads;
+    const int r = e / KP, c = e % KP;
+    const bool valid = (r < rows) && (c < a.k);
+    const int64_t gi = (r0 + r) * KP + c;
+    pv[i] = (valid && p1 >= 0)
+                ? part_sum<KP>(a.P, a.nsplit, a.skG1, a.ncols1, a.n1, p1, r, c, b10, b11)
+                : 0.f;
+    qv[i] = (valid && p2 >= 0)
+                ? part_sum<KP>(a.Q, a.nsplit2, a.skG2, a.ncols2, a.n2, p2, r, c, b20, b21)
+                : 0.f;
+    uv[i] = (valid && p1 < 0 && p2 < 0) ? a.mu[gi] : 0.f;
+    av[i] = (valid && a.update) ? a.A[gi] : 0.f;
+    mv[i] = (valid && a.update && rms) ? a.M[gi] : 0.f;
+  }
   __syncthreads();
 
+  // phase 2: gradient, update, projection
   float tr = 0.f, kkt2 = 0.f, sumA = 0.f;
   int nonfin = 0;
-  for (int e = tid; e < kTileRows * KP; e += blockDim.x) {
+#pragma unroll
+  for (int i = 0; i < EPT; ++i) {
+    const int e = tid + i * kEpiThreads;
     const int r = e / KP, c = e % KP;
     float hn = 0.f;
     if (r < rows && c < a.k) {
@@ -155,24 +176,20 @@ __global__ void __launch_bounds__(256) epilogue_kernel(EpiArgs a) {
       if (p1 >= 0 || p2 >= 0) {
         g = 0.f;
         if (p1 >= 0) {
-          const float p =
-              part_sum<KP>(a.P, a.nsplit, a.skG1, a.ncols1, a.n1, p1, r, c, b10, b11);
           float hg = 0.f;
 #pragma unroll
           for (int d = 0; d < KP; ++d) hg = fmaf(Hs[r][d], G1[d][c], hg);
-          g = a.coef * (hg - p);
-          tr = fmaf(h, p, tr);
+          g = a.coef * (hg - pv[i]);
+          tr = fmaf(h, pv[i], tr);
         }
         if (p2 >= 0) {
-          const float q =
-              part_sum<KP>(a.Q, a.nsplit2, a.skG2, a.ncols2, a.n2, p2, r, c, b20, b21);
           float hg = 0.f;
 #pragma unroll
           for (int d = 0; d < KP; ++d) hg = fmaf(Hs[r][d], G2[d][c], hg);
-          g += a.coef * (hg - q);
+          g += a.coef * (hg - qv[i]);
         }
       } else {
-        g = a.mu[gi];
+        g = uv[i];
       }
       const float pg = (h > 0.f) ? g : fminf(0.f, g);
       kkt2 = fmaf(pg, pg, kkt2);
@@ -182,15 +199,15 @@ __global__ void __launch_bounds__(256) epilogue_kernel(EpiArgs a) {
       if (a.store_mu) a.mu[gi] = g;
       if (a.update) {
         float x;
-        if (a.method == SYMNMF_RMSPROP) {
-          const float v = a.alpha * a.A[gi] + (1.f - a.alpha) * (g * g);
+        if (rms) {
+          const float v = a.alpha * av[i] + (1.f - a.alpha) * (g * g);
           a.A[gi] = v;
-          const float m = a.mom * a.M[gi] + a.eta * g / (sqrtf(v) + a.eps);
+          const float m = a.mom * mv[i] + a.eta * g / (sqrtf(v) + a.eps);
           a.M[gi] = m;
           x = h - m;
           sumA += v;
         } else {
-          const float acc = a.A[gi] + g * g;
+          const float acc = av[i] + g * g;
           a.A[gi] = acc;
           x = h - a.eta * g / (sqrtf(acc) + a.eps);
           sumA += acc;
@@ -204,7 +221,7 @@ __global__ void __launch_bounds__(256) epilogue_kernel(EpiArgs a) {
     Hn[r][c] = hn;
   }
   __syncthreads();
-  if (a.update) tile_tail<KP>(Hn, r0, a.Btn, a.ldb, a.gram_part, tile);
+  if (a.update) tile_tail<KP>(Hn, r0, a.Btn, a.bt_fmt, a.ldb, a.gram_part, tile);
   const double s_tr = block_sum((double)tr, red);
   const double s_kkt = block_sum((double)kkt2, red);
   const double s_a = block_sum((double)sumA, red);
@@ -216,11 +233,13 @@ __global__ void __launch_bounds__(256) epilogue_kernel(EpiArgs a) {
     sl[2] = s_a;
     sl[3] = s_nf;
   }
+
+
 }
 
 template <int KP>
-__global__ void __launch_bounds__(256) prepare_kernel(const float *H, int64_t n, uint16_t *Bt,
-                                                      int64_t ldb, float *gram_part) {
+__global__ void __launch_bounds__(256) prepare_kernel(const float *H, int64_t n, void *Bt,
+                                                      int bt_fmt, int64_t ldb, float *gram_part) {
   __shared__ float Hn[kTileRows][KP + 1];
   const int tile = blockIdx.x;
   const int64_t r0 = (int64_t)tile * kTileRows;
@@ -230,69 +249,74 @@ __global__ void __launch_bounds__(256) prepare_kernel(const float *H, int64_t n,
     Hn[r][c] = (r < rows) ? H[(r0 + r) * KP + c] : 0.f;
   }
   __syncthreads();
-  tile_tail<KP>(Hn, r0, Bt, ldb, gram_part, tile);
+  tile_tail<KP>(Hn, r0, Bt, bt_fmt, ldb, gram_part, tile);
 }
 
-// stage 1: chunk c sums tiles [c*per, (c+1)*per) in order (FP64)
-__global__ void __launch_bounds__(256) reduce_stage1(const double *slots, const float *gram_part,
-                                                     int ntiles, int kp, int per,
-                                                     double *chunk_buf) {
-  const int c = blockIdx.x;
-  const int t0 = c * per, t1 = min(ntiles, t0 + per);
-  const int stride = 4 + kp * kp;
-  double *out = chunk_buf + (int64_t)c * stride;
-  const int tid = threadIdx.x;
-  if (slots && tid < 4) {
-    double s = 0.0;
-    for (int t = t0; t < t1; ++t) s += slots[(int64_t)t * kSlotStride + tid];
-    out[tid] = s;
-  }
-  if (gram_part) {
-    for (int e = tid; e < kp * kp; e += blockDim.x) {
-      double s = 0.0;
-      for (int t = t0; t < t1; ++t) s += (double)gram_part[(int64_t)t * kp * kp + e];
-      out[4 + e] = s;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(256) reduce_stage2(const double *chunk_buf, int nchunks, int kp,
-                                                     int k, int64_t n, double normS2, long long t,
-                                                     int full, int have_slots, int have_gram,
-                                                     const double *gram64_cur, double *gram64_next,
-                                                     float *gram32_next, DevRecord *rec) {
+// Fixed-order FP64 reduction of an iteration's per-tile results (the 4
+// scalar slots and the kp x kp Gram partial of every tile).  Grid (entry
+// blocks of 128 values, chunks of 32 tiles): level 1 sums a chunk's tiles in
+// tile order; the last CTA of an entry block to arrive sums the chunks in
+// chunk order, so the result does not depend on timing.  Entry block 0 also
+// forms the iteration record f = ||S||^2 - 2 tr + ||Gram_t||^2 (Eq. 2).
+template <int KP>
+__global__ void __launch_bounds__(128) reduce_iter_kernel(ReduceArgs a) {
   __shared__ double red[40];
   __shared__ double sc[4];
-  const int stride = 4 + kp * kp;
-  const int tid = threadIdx.x;
-  if (have_slots && tid < 4) {
-    double s = 0.0;
-    for (int c = 0; c < nchunks; ++c) s += chunk_buf[(int64_t)c * stride + tid];
-    sc[tid] = s;
+  __shared__ int last;
+  const int stride = 4 + KP * KP;
+  const int eb = blockIdx.x, tc = blockIdx.y, nTC = gridDim.y;
+  const int e = eb * 128 + threadIdx.x;
+  const int t0 = tc * 32;
+  const int cnt = (a.ntiles - t0) < 32 ? (a.ntiles - t0) : 32;
+  const bool gram = (a.gram_part != nullptr);
+  if (e < stride) {
+    double v = 0.0;
+    if (e < 4) {
+      if (a.slots) v = ordered_sum32(a.slots + (int64_t)t0 * kSlotStride + e, kSlotStride, cnt);
+    } else if (gram) {
+      v = ordered_sum32(a.gram_part + (int64_t)t0 * KP * KP + (e - 4), KP * KP, cnt);
+    }
+    a.lvl1[(int64_t)tc * stride + e] = v;
   }
-  if (have_gram) {
-    for (int e = tid; e < kp * kp; e += blockDim.x) {
-      double s = 0.0;
-      for (int c = 0; c < nchunks; ++c) s += chunk_buf[(int64_t)c * stride + 4 + e];
-      gram64_next[e] = s;
-      gram32_next[e] = (float)s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const int old = atomicAdd(&a.counters[eb], 1);
+    last = (old == nTC - 1);
+    if (last) a.counters[eb] = 0;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  if (e < stride) {
+    for (int g0 = 0; g0 < nTC; g0 += 32) {
+      const int c2 = (nTC - g0) < 32 ? (nTC - g0) : 32;
+      s += ordered_sum32(a.lvl1 + (int64_t)g0 * stride + e, stride, c2);
+    }
+    if (e >= 4 && gram) {
+      a.gram64_next[e - 4] = s;
+      a.gram32_next[e - 4] = (float)s;
     }
   }
+  if (eb != 0) return;
+  if (threadIdx.x < 4) sc[threadIdx.x] = s;
   double g2 = 0.0;
-  for (int e = tid; e < kp * kp; e += blockDim.x) g2 += gram64_cur[e] * gram64_cur[e];
+  if (a.gram64_cur)
+    for (int i = threadIdx.x; i < KP * KP; i += blockDim.x) g2 += a.gram64_cur[i] * a.gram64_cur[i];
   g2 = block_sum(g2, red);
-  if (tid == 0 && have_slots && rec) {
-    DevRecord r;
-    r.t = t;
-    r.tr = sc[0];
-    r.gram2 = g2;
-    r.f = normS2 - 2.0 * sc[0] + g2;
-    r.E = r.f / normS2;
-    r.kkt = sqrt(sc[1]) / ((double)n * (double)k);
-    r.sumA = sc[2];
-    r.nonfinite = (int)sc[3];
-    r.full = full;
-    *rec = r;
+  if (threadIdx.x == 0 && a.rec && a.slots) {
+    DevRecord rc;
+    rc.t = a.t;
+    rc.tr = sc[0];
+    rc.gram2 = g2;
+    rc.f = a.normS2 - 2.0 * sc[0] + g2;
+    rc.E = rc.f / a.normS2;
+    rc.kkt = sqrt(sc[1]) / ((double)a.n * (double)a.k);
+    rc.sumA = sc[2];
+    rc.nonfinite = (int)sc[3];
+    rc.full = a.full;
+    *a.rec = rc;
   }
 }
 
@@ -457,28 +481,23 @@ cudaError_t launch_epilogue(const EpiArgs &a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(epilogue_kernel<KPV>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    epilogue_kernel<KPV><<<a.ntiles, 256, bytes, s>>>(a);
+    epilogue_kernel<KPV><<<a.ntiles, kEpiThreads, bytes, s>>>(a);
   });
   return cudaGetLastError();
 }
 
-cudaError_t launch_prepare_tiles(const float *H, int64_t n, int k, int kp, uint16_t *Bt,
+cudaError_t launch_prepare_tiles(const float *H, int64_t n, int k, int kp, void *Bt, int bt_fmt,
                                  int64_t ldb, float *gram_part, cudaStream_t s) {
   (void)k;
   const int ntiles = (int)((n + kTileRows - 1) / kTileRows);
-  KP_SWITCH(kp, prepare_kernel<KPV><<<ntiles, 256, 0, s>>>(H, n, Bt, ldb, gram_part));
+  KP_SWITCH(kp, prepare_kernel<KPV><<<ntiles, 256, 0, s>>>(H, n, Bt, bt_fmt, ldb, gram_part));
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const double *slots, const float *gram_part, int ntiles, int kp, int k,
-                          int64_t n, double normS2, long long t, int full, double *chunk_buf,
-                          int nchunks, const double *gram64_cur, double *gram64_next,
-                          float *gram32_next, DevRecord *rec, cudaStream_t s) {
-  const int per = (ntiles + nchunks - 1) / nchunks;
-  const int nc = (ntiles + per - 1) / per;
-  reduce_stage1<<<nc, 256, 0, s>>>(slots, gram_part, ntiles, kp, per, chunk_buf);
-  reduce_stage2<<<1, 256, 0, s>>>(chunk_buf, nc, kp, k, n, normS2, t, full, slots != nullptr,
-                                  gram_part != nullptr, gram64_cur, gram64_next, gram32_next, rec);
+cudaError_t launch_reduce_iter(const ReduceArgs &a, int kp, cudaStream_t s) {
+  const int stride = 4 + (a.gram_part ? kp * kp : 0);
+  dim3 grid((stride + 127) / 128, (a.ntiles + 31) / 32);
+  KP_SWITCH(kp, reduce_iter_kernel<KPV><<<grid, 128, 0, s>>>(a));
   return cudaGetLastError();
 }
 

@@ -1,43 +1,62 @@
-// Tensor-core product P = S[rows, cols] * H[cols] for BF16-stored S on
-// sm_103a (the S H term of the gradient, Sec. 2.1; the dominant cost of
-// every iteration, Sec. 4.3).
+// Tensor-core solver step on sm_103a: the streamed product S H (the S H term
+// of the gradient, Sec. 2.1, the dominant cost of every iteration, Sec. 4.3)
+// with the iteration's epilogue fused into the same kernel.
 //
-// Design (one CTA per SM, persistent, warp-specialised):
-//   warp 0     TMA producer: streams 128 x 128 tiles of S (two 128-byte
-//              swizzle atoms) and the matching 128-column slice of the
-//              bf16 hi/lo copy of H^T into a ring of shared-memory stages
-//   warp 1     MMA issuer: one thread issues tcgen05.mma kind::f16
-//              (M = 128, N = 2 kp: the hi and lo halves of H side by side,
-//              K = 16 per instruction) into a double-buffered TMEM
-//              accumulator and frees stages with tcgen05.commit
-//   warps 2-5  epilogue: tcgen05.ld the 128 x N accumulator, add the hi and
-//              lo halves (so H enters with ~16 significant bits), write the
-//              FP32 partial of its (row tile, column range) segment
-// Work is the row-major list of (row tile, column tile) units, split into
-// equal contiguous ranges, one per CTA (stream-K), so every SM streams the
-// same number of S bytes whatever n is.  A CTA's range covers whole row
-// tiles plus at most one partial tile at each end; partial segment of CTA
-// b for row tile p goes to slot b + p (unique, see stream_k_slot), and the
-// epilogue kernel adds a tile's slots in CTA order, so the result is
-// deterministic.
+// One persistent CTA per SM, warp-specialised:
+//   warp 0      TMA producer: streams 128-row tiles of S (128-byte swizzled
+//               atoms) and the matching slice of the hi/lo MMA copy of H^T
+//               into a ring of shared-memory stages
+//   warp 1      MMA issuer: one thread issues tcgen05.mma into a double-
+//               buffered 128 x 2kp TMEM accumulator (columns [0,kp) multiply
+//               H_hi, [kp,2kp) multiply H_lo) and frees stages with
+//               tcgen05.commit
+//   warps 2-5   epilogue, one thread per tile row: reads the accumulator
+//               (tcgen05.ld), P = acc_hi + acc_lo, and for a finished tile
+//               runs the whole per-row update: g = 4 (H Gram_t - P), the
+//               AdaGrad / RMSprop step with the max(0, .) projection into the
+//               other H buffer, the hi/lo MMA copy of the new rows, and the
+//               tile partials tr = sum H * P, ||grad_proj||^2, sum(G), NaN
+//               count and the Gram partial H'^T H'
+//   warps 6-9   (FP32 storage only) converters, see below
+// Storage types:
+//   BF16  kind::f16, A = S straight from shared memory, B = [H_hi | H_lo]
+//         in bf16 (H enters with about 16 significant bits)
+//   FP32  error-compensated TF32 (after Ootomo & Yokota, IJHPCA 2022): the
+//         converter warps split each staged S row into S_hi (13 low mantissa
+//         bits cleared, exact in tf32) and S_lo = round_tf32(S - S_hi) and
+//         store both in tensor memory, where the MMA reads its A operand
+//         (shared memory is read once per S byte); with B = [H_hi | H_lo]
+//         in tf32 the two MMAs per k-slice accumulate
+//         (S_hi + S_lo)(H_hi + H_lo), leaving only the rounding of the lo
+//         parts (relative 2^-22, unbiased)
+// Work: the row-major list of (row tile, 128-column tile) units is split
+// into equal contiguous ranges, one per CTA (stream-K), so every SM streams
+// the same number of S bytes.  A tile whose units span several CTAs is
+// finished by the last of them to arrive (per-tile counter): the others
+// leave their FP32 partial in slot (cta + tile); the finisher adds the
+// slots in CTA order, so results do not depend on timing.  Finished tiles
+// feed the fixed-order FP64 cross-tile reduction (epi_common.cuh), whose
+// last CTA writes the Gram of H_{t+1} and the iteration record.
+// Launches over row / column lists (sampled iterations) only write the
+// partial slots; the stand-alone epilogue kernel consumes them.
 //
-// Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
-// CTA records an error code, stops all roles, drains its own copies and
-// MMAs with bounded waits, frees TMEM and returns.
+// Every mbarrier wait is bounded (2 s of %globaltimer): on expiry the CTA
+// records an error code, stops all roles, drains its own copies and MMAs
+// with bounded waits, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
 
+#include "epi_common.cuh"
 #include "symnmf_internal.h"
+#include "tc_ptx.cuh"
 
 namespace symnmf {
 namespace {
 
-constexpr int kThreads = 192;
-constexpr uint64_t kWaitNs = 2000000000ull;
-constexpr uint32_t kAtomBytes = 128 * 128;   // 128 rows x 128 bytes
+using namespace tc;
 
 struct TcArgs {
   int64_t W;             // units = n_rows_list * n_cols_list
@@ -45,163 +64,391 @@ struct TcArgs {
   int n_cols;
   const int *row_list;
   const int *col_list;
-  float *out;
+  float *out;            // partial slots
   int *err;
-  int stages;
+  int fused;             // run the per-tile epilogue in the kernel
+  int *tile_cnt;         // per-tile arrival counters (fused)
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+template <int DT, int KP>
+struct Cfg {
+  static constexpr bool F32 = (DT == 0);
+  static constexpr int N = 2 * KP;
+  static constexpr int ATOM_COLS = F32 ? 32 : 64;       // elements per 128-byte row
+  static constexpr int APS = (KP == 64) ? 1 : 2;         // swizzle atoms per stage
+  static constexpr int SPU = 128 / (APS * ATOM_COLS);    // stages per 128-column unit
+  static constexpr int KSL = 4 * APS;                    // MMA k-slices per stage
+  static constexpr uint32_t A_BYTES = APS * kAtomBytes;
+  static constexpr uint32_t B_ATOM = N * 128;
+  static constexpr uint32_t B_BYTES = APS * B_ATOM;
+  static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+  // stages per accumulator chain: the tensor core's FP32 accumulation is
+  // kept to at most 16 chained MMAs, the rest is summed in FP32 registers
+  static constexpr int FOLD = F32 ? 1 : SPU;
+  static constexpr uint32_t EPI_FLOATS = 128 * (KP + 1) + KP * KP;
+  static constexpr uint32_t EPI_BYTES = EPI_FLOATS * 4 + 512;
+  static constexpr uint32_t BAR_BYTES = 512;
+  static constexpr uint32_t BUDGET = 232448u - 1024u - BAR_BYTES - EPI_BYTES;
+  static constexpr int STAGES = (BUDGET / STAGE) < 8u ? (int)(BUDGET / STAGE) : 8;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + BAR_BYTES + EPI_BYTES;
+  static constexpr int THREADS = F32 ? 320 : 192;
+  static constexpr uint32_t ABUF = F32 ? 64u * APS : 0u;  // TMEM columns per A buffer
+  static constexpr uint32_t ACC0 = 2 * ABUF;
+  static constexpr uint32_t TMEM_NEED = ACC0 + 2 * N;
+  static constexpr uint32_t TMEM_COLS = TMEM_NEED <= 32 ? 32 : TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
+  static_assert(STAGES >= 2, "shared memory ring too small");
+};
+
+// ------------------------------------------------------------------ epilogue
+// Register-block shape of the per-thread share of the kp x kp Gram partial
+template <int KP>
+struct GramBlk {
+  static constexpr int BR = KP == 64 ? 8 : KP == 32 ? 4 : KP == 16 ? 2 : 1;
+  static constexpr int BC = KP == 64 ? 4 : KP == 32 ? 2 : 1;
+  static constexpr int NBLK = (KP / BR) * (KP / BC);  // <= 128
+};
+
+// Per-tile update for the thread's row (row = tile row, et = index among the
+// 128 epilogue threads); p holds the row of S H for H_t, summed in FP32 in
+// a fixed order.  Everything the iteration produces for this tile is
+// written here; the cross-tile sums are left to the reduction kernel.
+template <int DT, int KP>
+__device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&p)[KP], float *Hs,
+                                              const float *Gs, double *scratch, int et, int row) {
+  const int64_t r0 = (int64_t)tp * 128;
+  const int rows = (int)((e.n - r0) < 128 ? (e.n - r0) : 128);
+  const bool vrow = row < rows;
+  float *hrow = Hs + row * (KP + 1);
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(e.H + (r0 + row) * KP);
+#pragma unroll
+    for (int c4 = 0; c4 < KP / 4; ++c4) {
+      const float4 v = vrow ? src[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      hrow[4 * c4 + 0] = v.x;
+      hrow[4 * c4 + 1] = v.y;
+      hrow[4 * c4 + 2] = v.z;
+      hrow[4 * c4 + 3] = v.w;
+    }
+  }
+  // (H Gram_t) row, then g = coef ((H Gram_t) - S H) in place of p (Sec. 2.1)
+  float hg[KP];
+#pragma unroll
+  for (int c = 0; c < KP; ++c) hg[c] = 0.f;
+#pragma unroll 2
+  for (int d = 0; d < KP; ++d) {
+    const float hv = hrow[d];
+    const float4 *gr = reinterpret_cast<const float4 *>(Gs + d * KP);
+#pragma unroll
+    for (int c4 = 0; c4 < KP / 4; ++c4) {
+      const float4 gv = gr[c4];
+      hg[4 * c4 + 0] = fmaf(hv, gv.x, hg[4 * c4 + 0]);
+      hg[4 * c4 + 1] = fmaf(hv, gv.y, hg[4 * c4 + 1]);
+      hg[4 * c4 + 2] = fmaf(hv, gv.z, hg[4 * c4 + 2]);
+      hg[4 * c4 + 3] = fmaf(hv, gv.w, hg[4 * c4 + 3]);
+    }
+  }
+  float tr = 0.f, kkt2 = 0.f, sumA = 0.f, nonfin = 0.f;
+#pragma unroll
+  for (int c = 0; c < KP; ++c) {
+    const float h = hrow[c];
+    float g = 0.f;
+    if (c < e.k) {
+      g = e.coef * (hg[c] - p[c]);
+      tr = fmaf(h, p[c], tr);
+      const float pg = (h > 0.f) ? g : fminf(0.f, g);
+      kkt2 = fmaf(pg, pg, kkt2);
+      if (!isfinite(g)) nonfin += 1.f;
+    }
+    p[c] = g;
+  }
+  if (!vrow) tr = kkt2 = nonfin = 0.f;
+  // update and projection, 8 columns at a time
+  const bool rms = (e.method == SYMNMF_RMSPROP);
+  const int64_t base = (r0 + row) * KP;
+#pragma unroll
+  for (int cc = 0; cc < KP; cc += 8) {
+    float av[8], mv[8], hn[8];
+    if (vrow && e.update) {
+      const float4 u = reinterpret_cast<const float4 *>(e.A + base + cc)[0];
+      const float4 v = reinterpret_cast<const float4 *>(e.A + base + cc)[1];
+      av[0] = u.x; av[1] = u.y; av[2] = u.z; av[3] = u.w;
+      av[4] = v.x; av[5] = v.y; av[6] = v.z; av[7] = v.w;
+      if (rms) {
+        const float4 s4 = reinterpret_cast<const float4 *>(e.M + base + cc)[0];
+        const float4 w4 = reinterpret_cast<const float4 *>(e.M + base + cc)[1];
+        mv[0] = s4.x; mv[1] = s4.y; mv[2] = s4.z; mv[3] = s4.w;
+        mv[4] = w4.x; mv[5] = w4.y; mv[6] = w4.z; mv[7] = w4.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mv[j] = 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) av[j] = mv[j] = 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = cc + j;
+      const float h = hrow[c];
+      const float g = p[c];
+      hn[j] = h;
+      if (e.update) {
+        if (c < e.k && vrow) {
+          float x;
+          if (rms) {
+            const float v = e.alpha * av[j] + (1.f - e.alpha) * (g * g);
+            av[j] = v;
+            const float m = e.mom * mv[j] + e.eta * g / (sqrtf(v) + e.eps);
+            mv[j] = m;
+            x = h - m;
+            sumA += v;
+          } else {
+            const float acc = av[j] + g * g;
+            av[j] = acc;
+            x = h - e.eta * g / (sqrtf(acc) + e.eps);
+            sumA += acc;
+          }
+          hn[j] = (x > 0.f) ? x : 0.f;
+        } else {
+          hn[j] = 0.f;
+        }
+      }
+    }
+    if (vrow) {
+      if (e.gout) {
+        reinterpret_cast<float4 *>(e.gout + base + cc)[0] = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
+        reinterpret_cast<float4 *>(e.gout + base + cc)[1] = make_float4(p[cc + 4], p[cc + 5], p[cc + 6], p[cc + 7]);
+      }
+      if (e.store_mu) {
+        reinterpret_cast<float4 *>(e.mu + base + cc)[0] = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
+        reinterpret_cast<float4 *>(e.mu + base + cc)[1] = make_float4(p[cc + 4], p[cc + 5], p[cc + 6], p[cc + 7]);
+      }
+      if (e.gcaller) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (cc + j < e.k) e.gcaller[(r0 + row) * e.k + cc + j] = p[cc + j];
+      }
+      if (e.update) {
+        reinterpret_cast<float4 *>(e.A + base + cc)[0] = make_float4(av[0], av[1], av[2], av[3]);
+        reinterpret_cast<float4 *>(e.A + base + cc)[1] = make_float4(av[4], av[5], av[6], av[7]);
+        if (rms) {
+          reinterpret_cast<float4 *>(e.M + base + cc)[0] = make_float4(mv[0], mv[1], mv[2], mv[3]);
+          reinterpret_cast<float4 *>(e.M + base + cc)[1] = make_float4(mv[4], mv[5], mv[6], mv[7]);
+        }
+        reinterpret_cast<float4 *>(e.Hn + base + cc)[0] = make_float4(hn[0], hn[1], hn[2], hn[3]);
+        reinterpret_cast<float4 *>(e.Hn + base + cc)[1] = make_float4(hn[4], hn[5], hn[6], hn[7]);
+      }
+    }
+    if (e.update) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) hrow[cc + j] = hn[j];
+      if (e.Btn) {
+        if (e.bt_fmt == 0) {
+          uint16_t *B = reinterpret_cast<uint16_t *>(e.Btn);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const uint16_t hi = bf16_bits(hn[j]);
+            B[(int64_t)(cc + j) * e.ldb + r0 + row] = hi;
+            B[(int64_t)(KP + cc + j) * e.ldb + r0 + row] = bf16_bits(hn[j] - bf16_val(hi));
+          }
+        } else {
+          float *B = reinterpret_cast<float *>(e.Btn);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float hi = tf32_trunc(hn[j]);
+            B[(int64_t)(cc + j) * e.ldb + r0 + row] = hi;
+            B[(int64_t)(KP + cc + j) * e.ldb + r0 + row] = tf32_round(hn[j] - hi);
+          }
+        }
+      }
+    }
+  }
+  epi_bar();  // Hs holds the tile of H_{t+1}
+  if (e.update && e.gram_part) {
+    using GB = GramBlk<KP>;
+    if (et < GB::NBLK) {
+      const int cb = et / (KP / GB::BC), db = et % (KP / GB::BC);
+      const int c0 = cb * GB::BR, d0 = db * GB::BC;
+      float acc[GB::BR][GB::BC];
+#pragma unroll
+      for (int i = 0; i < GB::BR; ++i)
+#pragma unroll
+        for (int j = 0; j < GB::BC; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+      for (int r = 0; r < 128; ++r) {
+        const float *hr = Hs + r * (KP + 1);
+        float x[GB::BR], y[GB::BC];
+#pragma unroll
+        for (int i = 0; i < GB::BR; ++i) x[i] = hr[c0 + i];
+#pragma unroll
+        for (int j = 0; j < GB::BC; ++j) y[j] = hr[d0 + j];
+#pragma unroll
+        for (int i = 0; i < GB::BR; ++i)
+#pragma unroll
+          for (int j = 0; j < GB::BC; ++j) acc[i][j] = fmaf(x[i], y[j], acc[i][j]);
+      }
+      float *gp = e.gram_part + (int64_t)tp * KP * KP;
+#pragma unroll
+      for (int i = 0; i < GB::BR; ++i)
+#pragma unroll
+        for (int j = 0; j < GB::BC; ++j) gp[(c0 + i) * KP + d0 + j] = acc[i][j];
+    }
+  }
+  // tile scalars: warp xor trees, then warps added in order
+  double v4[4] = {(double)tr, (double)kkt2, (double)sumA, (double)nonfin};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], o);
+  if ((et & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) scratch[(et >> 5) * 4 + i] = v4[i];
+  epi_bar();
+  if (et < 4 && e.slots) {
+    const double sv = scratch[et] + scratch[4 + et] + scratch[8 + et] + scratch[12 + et];
+    e.slots[(int64_t)tp * kSlotStride + et] = sv;
+  }
+  epi_bar();
 }
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait; false on timeout or when another role has aborted
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          uint64_t limit_ns = kWaitNs) {
-  if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = gtimer();
-  while (true) {
-    if (mbar_try(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (gtimer() - t0 > limit_ns) return false;
+
+template <int DT, int KP>
+__device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_base, float *Hs,
+                              float *Gs, double *scratch, int *sflag, uint64_t *tfull,
+                              uint64_t *tempty, volatile int *abort_flag, int64_t L0, int64_t L1,
+                              int b) {
+  using C = Cfg<DT, KP>;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3;
+  const int row = q * 32 + lane;
+  const int et = (warp - 2) * 32 + lane;
+  if (a.fused)
+    for (int i = et; i < KP * KP; i += 128) Gs[i] = e.gram[i];
+  epi_bar();
+  int acc = 0;
+  uint32_t tph[2] = {0u, 0u};
+  bool ok = true;
+  int64_t L = L0;
+  while (L < L1 && ok) {
+    const int tp = (int)(L / a.n_cols);
+    const int64_t tile_end = (int64_t)(tp + 1) * a.n_cols;
+    const int64_t seg_end = L1 < tile_end ? L1 : tile_end;
+    // fold the segment's accumulator chunks into FP32 registers
+    float p[KP];
+#pragma unroll
+    for (int c = 0; c < KP; ++c) p[c] = 0.f;
+    const int64_t nfold = (seg_end - L) * (C::SPU / C::FOLD);
+    for (int64_t f = 0; f < nfold; ++f) {
+      if (!warp_wait(&tfull[acc], tph[acc], abort_flag)) {
+        if (lane == 0) {
+          set_err(a.err, 5);
+          *abort_flag = 1;
+        }
+        ok = false;
+        break;
+      }
+      fence_after();
+      const uint32_t tb =
+          tmem_base + ((uint32_t)(q * 32) << 16) + C::ACC0 + (uint32_t)(acc * C::N);
+#pragma unroll
+      for (int cc = 0; cc < KP; cc += 8) {
+        uint32_t x[16];
+        tmem_ld_pair(tb + cc, tb + KP + cc, x);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) p[cc + j] += __uint_as_float(x[j]) + __uint_as_float(x[8 + j]);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+      tph[acc] ^= 1;
+      acc ^= 1;
+    }
+    if (!ok) break;
+    bool do_epi = false;
+    int64_t b0 = b, b1 = b;
+    if (a.fused) {
+      b0 = sk_cta((int64_t)tp * a.n_cols, a.W, a.G);
+      b1 = sk_cta((int64_t)tp * a.n_cols + a.n_cols - 1, a.W, a.G);
+      do_epi = (b0 == b1);
+    }
+    if (!do_epi) {
+      float *dst = a.out + ((int64_t)(b + tp) * 128 + row) * KP;
+#pragma unroll
+      for (int cc = 0; cc < KP; cc += 4)
+        reinterpret_cast<float4 *>(dst + cc)[0] = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
+      if (a.fused) {
+        __threadfence();
+        epi_bar();
+        if (et == 0) {
+          const int old = atomicAdd(&a.tile_cnt[tp], 1);
+          const int last = (old == (int)(b1 - b0));
+          if (last) a.tile_cnt[tp] = 0;
+          *reinterpret_cast<volatile int *>(sflag) = last;
+        }
+        epi_bar();
+        do_epi = *reinterpret_cast<volatile int *>(sflag) != 0;
+        if (do_epi) {
+          // partials of the tile's CTAs, added in CTA order
+          __threadfence();
+#pragma unroll
+          for (int c = 0; c < KP; ++c) p[c] = 0.f;
+          for (int64_t bb = b0; bb <= b1; ++bb) {
+            const float4 *src =
+                reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP);
+#pragma unroll
+            for (int c4 = 0; c4 < KP / 4; ++c4) {
+              const float4 v = src[c4];
+              p[4 * c4 + 0] += v.x;
+              p[4 * c4 + 1] += v.y;
+              p[4 * c4 + 2] += v.z;
+              p[4 * c4 + 3] += v.w;
+            }
+          }
+        }
+      }
+    }
+    if (do_epi) tile_epilogue<DT, KP>(e, tp, p, Hs, Gs, scratch, et, row);
+    L = seg_end;
   }
 }
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
-                                            int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
-      "%3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t *holder, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                   smem_u32(holder)),
-               "r"(ncols));
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
-}
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-// 8 columns of hi and 8 of lo for this thread's TMEM lane, then wait
-__device__ __forceinline__ void tmem_ld_pair(uint32_t ta, uint32_t tb, uint32_t (&x)[16]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]),
-                 "=r"(x[6]), "=r"(x[7])
-               : "r"(ta));
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(x[8]), "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]), "=r"(x[13]),
-                 "=r"(x[14]), "=r"(x[15])
-               : "r"(tb));
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(x[5]),
-                 "+r"(x[6]), "+r"(x[7]), "+r"(x[8]), "+r"(x[9]), "+r"(x[10]), "+r"(x[11]),
-                 "+r"(x[12]), "+r"(x[13]), "+r"(x[14]), "+r"(x[15])
-               :
-               : "memory");
-}
 
-// shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
-// 8-row groups 1024 bytes apart
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-// instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-template <int KP>
-struct Cfg {
-  static constexpr int N = 2 * KP;
-  static constexpr uint32_t A_BYTES = 2 * kAtomBytes;      // 128 rows x 128 bf16
-  static constexpr uint32_t B_BYTES = 2 * N * 128;         // N rows x 128 bf16
-  static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
-  static constexpr uint32_t TMEM_COLS = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
-  static constexpr int STAGES = (int)std::min<uint32_t>(8u, (200u * 1024u) / STAGE);
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 + 256;
-};
-
-__device__ __forceinline__ void set_err(int *err, int code) {
-  if (err) atomicCAS(err, 0, code);
-}
-
-template <int KP>
-__global__ void __launch_bounds__(kThreads, 1)
-    prod_tc_bf16_kernel(const __grid_constant__ CUtensorMap mapS,
-                        const __grid_constant__ CUtensorMap mapB, TcArgs a) {
-  using C = Cfg<KP>;
+// -------------------------------------------------------------------- kernel
+template <int DT, int KP>
+__global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
+    step_tc_kernel(const __grid_constant__ CUtensorMap mapS,
+                   const __grid_constant__ CUtensorMap mapB, const TcArgs a, const EpiArgs e) {
+  using C = Cfg<DT, KP>;
   constexpr int N = C::N;
   constexpr int STAGES = C::STAGES;
+  constexpr bool F32 = C::F32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * C::STAGE);
   uint64_t *empty = full + STAGES;
-  uint64_t *tfull = empty + STAGES;
+  uint64_t *afull = empty + STAGES;
+  uint64_t *aempty = afull + 2;
+  uint64_t *tfull = aempty + 2;
   uint64_t *tempty = tfull + 2;
   uint64_t *drain = tempty + 2;
   uint32_t *holder = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(holder + 1);
   int *consumed = const_cast<int *>(abort_flag) + 1;
+  int *sflag = consumed + 1;
+  float *Hs = reinterpret_cast<float *>(smem + STAGES * C::STAGE + C::BAR_BYTES);
+  float *Gs = reinterpret_cast<float *>(
+      (reinterpret_cast<uintptr_t>(Hs + 128 * (KP + 1)) + 15) & ~uintptr_t(15));
+  double *scratch = reinterpret_cast<double *>(
+      (reinterpret_cast<uintptr_t>(Gs + KP * KP) + 15) & ~uintptr_t(15));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], F32 ? 5 : 1);  // (4 converter warps +) the MMA commit
     }
     for (int i = 0; i < 2; ++i) {
+      mbar_init(&afull[i], 4);
+      mbar_init(&aempty[i], 1);
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], 4);
     }
@@ -218,6 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int b = blockIdx.x;
   const int64_t L0 = (int64_t)b * a.W / a.G;
   const int64_t L1 = (int64_t)(b + 1) * a.W / a.G;
+  const int64_t c0 = L0 * C::SPU, c1 = L1 * C::SPU;  // stage-sized chunks
   int issued = 0;
 
   if (warp == 0) {
@@ -226,7 +474,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
       int stage = 0;
       uint32_t phase = 0;
-      for (int64_t L = L0; L < L1; ++L) {
+      for (int64_t c = c0; c < c1; ++c) {
+        const int64_t L = c / C::SPU;
+        const int kc = (int)(c % C::SPU);
         const int tp = (int)(L / a.n_cols), ci = (int)(L % a.n_cols);
         const int rt = a.row_list ? a.row_list[tp] : tp;
         const int ct = a.col_list ? a.col_list[ci] : ci;
@@ -237,11 +487,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         uint8_t *sa = smem + stage * C::STAGE;
         uint8_t *sb = sa + C::A_BYTES;
+        const int x0 = ct * 128 + kc * (C::APS * C::ATOM_COLS);
         mbar_expect_tx(&full[stage], C::STAGE);
-        tma_load_2d(sa, &mapS, &full[stage], ct * 128, rt * 128);
-        tma_load_2d(sa + kAtomBytes, &mapS, &full[stage], ct * 128 + 64, rt * 128);
-        tma_load_2d(sb, &mapB, &full[stage], ct * 128, 0);
-        tma_load_2d(sb + N * 128, &mapB, &full[stage], ct * 128 + 64, 0);
+#pragma unroll
+        for (int at = 0; at < C::APS; ++at) {
+          tma_load_2d(sa + at * kAtomBytes, &mapS, &full[stage], x0 + at * C::ATOM_COLS, rt * 128);
+          tma_load_2d(sb + at * C::B_ATOM, &mapB, &full[stage], x0 + at * C::ATOM_COLS, 0);
+        }
         ++issued;
         if (++stage == STAGES) {
           stage = 0;
@@ -254,22 +506,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       int acc = 0;
-      uint32_t tphase[2] = {0u, 0u};
-      constexpr uint32_t idesc = idesc_bf16(128, N);
+      uint32_t tph[2] = {0u, 0u};
+      uint32_t aph[2] = {0u, 0u};
+      constexpr uint32_t idesc = F32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
       int done = 0;
-      for (int64_t L = L0; L < L1; ++L) {
+      for (int64_t c = c0; c < c1; ++c) {
+        const int64_t L = c / C::SPU;
+        const int kc = (int)(c % C::SPU);
         const int ci = (int)(L % a.n_cols);
-        const bool seg_start = (L == L0) || (ci == 0);
-        const bool seg_end = (L == L1 - 1) || (ci == a.n_cols - 1);
-        if (seg_start) {
-          if (!mbar_wait(&tempty[acc], tphase[acc] ^ 1, abort_flag)) {
-            set_err(a.err, 2);
-            *abort_flag = 1;
-            break;
-          }
-          fence_after();
+        (void)L;
+        (void)kc;
+        (void)ci;
+        const bool seg_start = (c % C::FOLD) == 0;
+        const bool seg_end = (c % C::FOLD) == C::FOLD - 1;
+        const int ab = (int)((c - c0) & 1);
+        if (seg_start && !mbar_wait(&tempty[acc], tph[acc] ^ 1, abort_flag)) {
+          set_err(a.err, 2);
+          *abort_flag = 1;
+          break;
         }
-        if (!mbar_wait(&full[stage], phase, abort_flag)) {
+        if ((F32 && !mbar_wait(&afull[ab], aph[ab], abort_flag)) ||
+            !mbar_wait(&full[stage], phase, abort_flag)) {
           set_err(a.err, 3);
           *abort_flag = 1;
           break;
@@ -277,18 +534,33 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_after();
         const uint32_t sa = smem_u32(smem + stage * C::STAGE);
         const uint32_t sb = sa + C::A_BYTES;
-        const uint32_t d = tmem_base + (uint32_t)(acc * N);
+        const uint32_t d = tmem_base + C::ACC0 + (uint32_t)(acc * N);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const uint32_t aoff = (uint32_t)(j >> 2) * kAtomBytes + (uint32_t)(j & 3) * 32u;
-          const uint32_t boff = (uint32_t)(j >> 2) * (uint32_t)(N * 128) + (uint32_t)(j & 3) * 32u;
-          mma_bf16(d, sdesc(sa + aoff), sdesc(sb + boff), idesc, (seg_start && j == 0) ? 0u : 1u);
+        for (int j = 0; j < C::KSL; ++j) {
+          const uint32_t within = (uint32_t)(j & 3) * 32u;
+          const uint64_t bd = sdesc(sb + (uint32_t)(j >> 2) * C::B_ATOM + within);
+          const uint32_t first = (seg_start && j == 0) ? 0u : 1u;
+          if constexpr (F32) {
+            // S_hi [H_hi | H_lo] and S_lo H_hi (S_lo [H_hi | H_lo] when kp = 8,
+            // the narrowest MMA being N = 16)
+            constexpr uint32_t idesc_lo = idesc_tf32(128, KP >= 16 ? KP : N);
+            const uint32_t ahi = tmem_base + (uint32_t)ab * C::ABUF + (uint32_t)j * 8u;
+            mma_tf32_ta(d, ahi, bd, idesc, first);
+            mma_tf32_ta(d, ahi + 32u * C::APS, bd, idesc_lo, 1u);
+          } else {
+            const uint64_t ad = sdesc(sa + (uint32_t)(j >> 2) * kAtomBytes + within);
+            mma_bf16(d, ad, bd, idesc, first);
+          }
         }
         mma_commit(&empty[stage]);
+        if (F32) {
+          mma_commit(&aempty[ab]);
+          aph[ab] ^= 1;
+        }
         ++done;
         if (seg_end) {
           mma_commit(&tfull[acc]);
-          tphase[acc] ^= 1;
+          tph[acc] ^= 1;
           acc ^= 1;
         }
         if (++stage == STAGES) {
@@ -297,57 +569,66 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       *consumed = done;
-      // wait until every MMA issued by this thread has completed
       mma_commit(drain);
       if (!mbar_wait(drain, 0, abort_flag, 100000000ull) && !*abort_flag) set_err(a.err, 4);
     }
-  } else {
-    const int q = warp & 3;
-    const int row = q * 32 + lane;
-    int acc = 0;
-    uint32_t tphase[2] = {0u, 0u};
-    int64_t L = L0;
-    while (L < L1) {
-      const int tp = (int)(L / a.n_cols);
-      const int64_t tile_end = (int64_t)(tp + 1) * a.n_cols;
-      const int64_t seg_end = L1 < tile_end ? L1 : tile_end;
-      // one lane waits, the warp follows together (tcgen05.ld is .sync.aligned)
-      int ok = 1;
-      if (lane == 0) ok = mbar_wait(&tfull[acc], tphase[acc], abort_flag) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) {
-        if (lane == 0) {
-          set_err(a.err, 5);
-          *abort_flag = 1;
+  } else if (warp >= 6) {
+    if constexpr (F32) {
+      // converters: one thread per row of the tile
+      const int q = warp & 3;
+      const int row = q * 32 + lane;
+      const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t eph[2] = {0u, 0u};
+      for (int64_t c = c0; c < c1; ++c) {
+        const int ab = (int)((c - c0) & 1);
+        if (!warp_wait(&full[stage], phase, abort_flag) ||
+            !warp_wait(&aempty[ab], eph[ab] ^ 1, abort_flag)) {
+          if (lane == 0) {
+            set_err(a.err, 15);
+            *abort_flag = 1;
+          }
+          break;
         }
-        break;
-      }
-      fence_after();
-      float *dst = a.out + ((int64_t)(b + tp) * 128 + row) * KP;
-      const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * N);
+        fence_after();
+        const uint8_t *sa = smem + stage * C::STAGE;
 #pragma unroll
-      for (int c0 = 0; c0 < KP; c0 += 8) {
-        uint32_t x[16];
-        tmem_ld_pair(lane_base + c0, lane_base + KP + c0, x);
-        float4 o0, o1;
-        o0.x = __uint_as_float(x[0]) + __uint_as_float(x[8]);
-        o0.y = __uint_as_float(x[1]) + __uint_as_float(x[9]);
-        o0.z = __uint_as_float(x[2]) + __uint_as_float(x[10]);
-        o0.w = __uint_as_float(x[3]) + __uint_as_float(x[11]);
-        o1.x = __uint_as_float(x[4]) + __uint_as_float(x[12]);
-        o1.y = __uint_as_float(x[5]) + __uint_as_float(x[13]);
-        o1.z = __uint_as_float(x[6]) + __uint_as_float(x[14]);
-        o1.w = __uint_as_float(x[7]) + __uint_as_float(x[15]);
-        reinterpret_cast<float4 *>(dst + c0)[0] = o0;
-        reinterpret_cast<float4 *>(dst + c0)[1] = o1;
+        for (int at = 0; at < C::APS; ++at) {
+          const uint8_t *rowp = sa + at * kAtomBytes + row * 128;
+          uint32_t hi[32], lo[32];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 v = *reinterpret_cast<const float4 *>(rowp + ((j ^ (row & 7)) << 4));
+            const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float h = tf32_trunc(x[u]);
+              hi[4 * j + u] = __float_as_uint(h);
+              lo[4 * j + u] = __float_as_uint(tf32_round(x[u] - h));
+            }
+          }
+          const uint32_t base = tmem_base + lane_off + (uint32_t)ab * C::ABUF + (uint32_t)at * 32u;
+          tmem_st32(base, hi);
+          tmem_st32(base + 32u * C::APS, lo);
+        }
+        tmem_wait_st();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&empty[stage]);
+          mbar_arrive(&afull[ab]);
+        }
+        eph[ab] ^= 1;
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[acc]);
-      tphase[acc] ^= 1;
-      acc ^= 1;
-      L = seg_end;
     }
+  } else {
+    epilogue_role<DT, KP>(a, e, tmem_base, Hs, Gs, scratch, sflag, tfull, tempty, abort_flag, L0,
+                          L1, b);
   }
   __syncthreads();
   if (warp == 0 && lane == 0 && *abort_flag) {
@@ -370,6 +651,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ------------------------------------------------------------------- host
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -396,52 +678,66 @@ bool make_map_2d(CUtensorMap *m, const void *base, CUtensorMapDataType dt, uint6
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int KP>
-cudaError_t launch_kp(const ProdArgs &p, cudaStream_t s, int G, TcArgs ta) {
-  using C = Cfg<KP>;
+template <int DT, int KP>
+cudaError_t launch_cfg(const ProdArgs &p, const EpiArgs &e, cudaStream_t s, const TcArgs &ta) {
+  using C = Cfg<DT, KP>;
+  const CUtensorMapDataType t =
+      C::F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const uint64_t es = C::F32 ? 4 : 2;
   CUtensorMap mS, mB;
-  if (!make_map_2d(&mS, p.S, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (uint64_t)p.n, (uint64_t)p.n,
-                   (uint64_t)p.lds * 2, 64, 128))
+  if (!make_map_2d(&mS, p.S, t, (uint64_t)p.n, (uint64_t)p.n, (uint64_t)p.lds * es, C::ATOM_COLS,
+                   128))
     return cudaErrorInvalidValue;
-  if (!make_map_2d(&mB, p.Bt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (uint64_t)p.ldb, (uint64_t)(2 * KP),
-                   (uint64_t)p.ldb * 2, 64, 2 * KP))
+  if (!make_map_2d(&mB, p.Bt, t, (uint64_t)p.ldb, (uint64_t)(2 * KP), (uint64_t)p.ldb * es,
+                   C::ATOM_COLS, 2 * KP))
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(prod_tc_bf16_kernel<KP>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-  if (e != cudaSuccess) return e;
-  ta.stages = C::STAGES;
-  prod_tc_bf16_kernel<KP><<<G, kThreads, C::SMEM, s>>>(mS, mB, ta);
+  cudaError_t err = cudaFuncSetAttribute(step_tc_kernel<DT, KP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  if (err != cudaSuccess) return err;
+  step_tc_kernel<DT, KP><<<ta.G, C::THREADS, C::SMEM, s>>>(mS, mB, ta, e);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 bool tc_supported(int dtype, int kp) {
-  return dtype == 1 && (kp == 8 || kp == 16 || kp == 32 || kp == 64) && encode_fn() != nullptr;
+  return (dtype == 0 || dtype == 1) && (kp == 8 || kp == 16 || kp == 32 || kp == 64) &&
+         encode_fn() != nullptr;
 }
 
-int stream_k_ctas(int64_t units, int num_sms) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>(units, num_sms));
-}
-
-cudaError_t launch_prod_tc(const ProdArgs &a, cudaStream_t s, int num_sms, int *G_out, int *err) {
+cudaError_t launch_step_tc(const ProdArgs &a, const EpiArgs *epi, int *tile_cnt, cudaStream_t s,
+                           int num_sms, int *G_out, int *err) {
   if (a.n_rows_list <= 0 || a.n_cols_list <= 0) return cudaSuccess;
   TcArgs ta{};
   ta.W = (int64_t)a.n_rows_list * a.n_cols_list;
-  ta.G = stream_k_ctas(ta.W, num_sms);
+  ta.G = (int)std::max<int64_t>(1, std::min<int64_t>(ta.W, num_sms));
   ta.n_cols = a.n_cols_list;
   ta.row_list = a.row_list;
   ta.col_list = a.col_list;
   ta.out = a.out;
   ta.err = err;
+  ta.fused = (epi != nullptr) ? 1 : 0;
+  ta.tile_cnt = tile_cnt;
   *G_out = ta.G;
-  switch (a.kp) {
-    case 8: return launch_kp<8>(a, s, ta.G, ta);
-    case 16: return launch_kp<16>(a, s, ta.G, ta);
-    case 32: return launch_kp<32>(a, s, ta.G, ta);
-    case 64: return launch_kp<64>(a, s, ta.G, ta);
-    default: return cudaErrorInvalidValue;
+  EpiArgs e{};
+  if (epi) e = *epi;
+  const int want_fmt = (a.dtype == 0) ? 1 : 0;
+  if (a.bt_fmt != want_fmt) return cudaErrorInvalidValue;
+#define SYMNMF_TC_CASE(DTV)                           \
+  switch (a.kp) {                                     \
+    case 8: return launch_cfg<DTV, 8>(a, e, s, ta);   \
+    case 16: return launch_cfg<DTV, 16>(a, e, s, ta); \
+    case 32: return launch_cfg<DTV, 32>(a, e, s, ta); \
+    case 64: return launch_cfg<DTV, 64>(a, e, s, ta); \
+    default: return cudaErrorInvalidValue;            \
   }
+  if (a.dtype == 0) {
+    SYMNMF_TC_CASE(0)
+  } else if (a.dtype == 1) {
+    SYMNMF_TC_CASE(1)
+  }
+#undef SYMNMF_TC_CASE
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace symnmf

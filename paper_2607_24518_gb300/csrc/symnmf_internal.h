@@ -3,9 +3,12 @@
 //   * row tiles are 128 rows; ntiles = ceil(n / 128)
 //   * n x k state arrays are stored n x kp (kp = 8, 16, 32 or 64 >= k), the
 //     columns k..kp-1 held at exactly 0, so the padded columns never move
-//   * the MMA copy of H is stored transposed, [2*kp][ldb] bfloat16 with
-//     rows 0..kp-1 = hi(H^T) and kp..2kp-1 = lo(H^T) = bf16(H - hi), ldb =
-//     ntiles * 128 (columns past n are 0)
+//   * the MMA copy of H is stored transposed, [2*kp][ldb] with rows 0..kp-1
+//     = hi(H^T) and kp..2kp-1 = lo(H^T), ldb = ntiles * 128 (columns past n
+//     are 0), in one of two formats (bt_fmt):
+//       0: bfloat16, hi = bf16(H), lo = bf16(H - hi)      (BF16 / FP8 S)
+//       1: float holding tf32 values, hi = H with the 13 low mantissa bits
+//          cleared, lo = (H - hi) likewise truncated       (FP32 S)
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -36,7 +39,8 @@ struct ProdArgs {
   int64_t n;
   int k, kp;
   const float *H;        // FP32 master, n x kp (SIMT path)
-  const uint16_t *Bt;    // bf16 hi/lo transposed copy (tensor-core path)
+  const void *Bt;        // hi/lo transposed copy (tensor-core path)
+  int bt_fmt;
   int64_t ldb;
   const int *row_list;   // row tile indices (nullptr: all tiles in order)
   int n_rows_list;
@@ -66,7 +70,8 @@ struct EpiArgs {
   float eta, eps, alpha, mom;
   const float *H;        // H_t (n x kp)
   float *Hn;             // H_{t+1}
-  uint16_t *Btn;         // MMA copy of H_{t+1}
+  void *Btn;             // MMA copy of H_{t+1}
+  int bt_fmt;
   int64_t ldb;
   float *A, *M, *mu;     // state (n x kp)
   float *gout;           // g (n x kp) or nullptr
@@ -89,23 +94,40 @@ struct EpiArgs {
   float *gram_part;      // per tile kp x kp partial of H_{t+1}^T H_{t+1} (nullptr: skip)
 };
 
+// Cross-tile reduction of one iteration (launch_reduce_iter)
+struct ReduceArgs {
+  const double *slots;       // per tile [tr, kkt2, sumA, nonfinite] or nullptr
+  const float *gram_part;    // per tile Gram partials or nullptr
+  int ntiles;
+  int k;
+  int64_t n;
+  double normS2;
+  long long t;
+  int full;
+  const double *gram64_cur;  // Gram of H_t (for ||H_t^T H_t||^2) or nullptr
+  double *gram64_next;
+  float *gram32_next;
+  DevRecord *rec;            // record destination or nullptr
+  double *lvl1;              // ceil(ntiles/32) x (4 + kp^2) scratch
+  int *counters;             // >= ceil((4 + kp^2)/128) counters, zero between launches
+};
+
 constexpr int kSlotStride = 4;
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_prod_simt(const ProdArgs &a, cudaStream_t s);
-cudaError_t launch_prod_tc(const ProdArgs &a, cudaStream_t s, int num_sms, int *G_out, int *err);
+// tensor-core product; with epi != nullptr (full row and column lists only)
+// the kernel also runs the per-tile epilogue and the cross-tile reduction
+cudaError_t launch_step_tc(const ProdArgs &a, const EpiArgs *epi, int *tile_cnt, cudaStream_t s,
+                           int num_sms, int *G_out, int *err);
 bool tc_supported(int dtype, int kp);
 cudaError_t launch_epilogue(const EpiArgs &a, cudaStream_t s);
 // per-tile Bt copy and Gram partial of H (init / teacher forcing)
-cudaError_t launch_prepare_tiles(const float *H, int64_t n, int k, int kp, uint16_t *Bt,
+cudaError_t launch_prepare_tiles(const float *H, int64_t n, int k, int kp, void *Bt, int bt_fmt,
                                  int64_t ldb, float *gram_part, cudaStream_t s);
-// two-level fixed-order reduction of per-tile slots and Gram partials; writes
-// the record of iteration t (ring slot t % kRing), Gram64/Gram32 of the next
-// iterate, and reads Gram64 of the current iterate for ||Gram_t||^2.
-cudaError_t launch_reduce(const double *slots, const float *gram_part, int ntiles, int kp, int k,
-                          int64_t n, double normS2, long long t, int full, double *chunk_buf,
-                          int nchunks, const double *gram64_cur, double *gram64_next,
-                          float *gram32_next, DevRecord *ring, cudaStream_t s);
+// fixed-order FP64 reduction of the per-tile slots and Gram partials of an
+// iteration: Gram of the next iterate (FP64 and FP32) and the record
+cudaError_t launch_reduce_iter(const ReduceArgs &a, int kp, cudaStream_t s);
 // Gram of a subset of tiles (lists of tile indices) -> FP32 kp x kp, two lists
 cudaError_t launch_gram_subset(const float *gram_part, int kp, const int *list1, int n1,
                                const int *list2, int n2, float *out1, float *out2,
