@@ -712,7 +712,7 @@ int symnmf_create_ld(const void *S, int64_t n, int64_t lds, int32_t k, int32_t d
   reset_ctrl(&h->ctrl);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-  const int64_t nkp = n * h->kp;
+  const int64_t nkp = (int64_t)h->ntiles * kTileRows * h->kp;  // tile column-major
   h->pq_cap_tiles = h->ntiles + 3 * (int64_t)std::max(1, h->num_sms);
   h->nchunks = std::max(1, std::min(h->ntiles, 64));
   h->n_norm_parts = 4 * std::max(1, h->num_sms);
@@ -830,7 +830,7 @@ int symnmf_set_H(symnmf_t h, const float *H) {
   h->err.clear();
   h->cur = 0;
   CK(launch_pack(H, h->H[0], h->n, h->k, h->kp, h->stream));
-  const size_t bytes = sizeof(float) * h->n * h->kp;
+  const size_t bytes = sizeof(float) * (size_t)h->ntiles * kTileRows * h->kp;
   CK(cudaMemsetAsync(h->H[1], 0, bytes, h->stream));
   CK(cudaMemsetAsync(h->A, 0, bytes, h->stream));
   CK(cudaMemsetAsync(h->M, 0, bytes, h->stream));

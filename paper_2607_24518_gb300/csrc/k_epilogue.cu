@@ -372,12 +372,14 @@ __global__ void sum_array_kernel(const double *x, int m, int stride, int off, do
   }
 }
 
+// caller row-major n x k -> n x kp over all tile rows (pads zeroed)
 __global__ void pack_kernel(const float *src, float *dst, int64_t n, int k, int kp) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n * kp) return;
+  const int64_t tiles = (n + kTileRows - 1) / kTileRows;
+  if (e >= tiles * kTileRows * kp) return;
   const int64_t r = e / kp;
   const int c = (int)(e % kp);
-  dst[e] = (c < k) ? src[r * k + c] : 0.f;
+  dst[e] = (c < k && r < n) ? src[r * k + c] : 0.f;
 }
 
 __global__ void unpack_kernel(const float *src, float *dst, int64_t n, int k, int kp) {
@@ -522,7 +524,7 @@ cudaError_t launch_norm_s2(const void *S, int64_t n, int64_t lds, int dtype, con
 }
 
 cudaError_t launch_pack(const float *src, float *dst, int64_t n, int k, int kp, cudaStream_t s) {
-  const int64_t tot = n * kp;
+  const int64_t tot = (n + kTileRows - 1) / kTileRows * kTileRows * kp;
   pack_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, dst, n, k, kp);
   return cudaGetLastError();
 }

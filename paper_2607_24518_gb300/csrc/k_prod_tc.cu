@@ -91,10 +91,11 @@ struct Cfg {
   static constexpr uint32_t BUDGET = 232448u - 1024u - BAR_BYTES - EPI_BYTES;
   static constexpr int STAGES = (BUDGET / STAGE) < 8u ? (int)(BUDGET / STAGE) : 8;
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + BAR_BYTES + EPI_BYTES;
-  static constexpr int THREADS = F32 ? 320 : 192;
+  static constexpr int THREADS = 320;
   static constexpr uint32_t ABUF = F32 ? 64u * APS : 0u;  // TMEM columns per A buffer
   static constexpr uint32_t ACC0 = 2 * ABUF;
-  static constexpr uint32_t TMEM_NEED = ACC0 + 2 * N;
+  static constexpr uint32_t PB0 = ACC0 + 2 * N;           // double-buffered P rows
+  static constexpr uint32_t TMEM_NEED = PB0 + 2 * KP;
   static constexpr uint32_t TMEM_COLS = TMEM_NEED <= 32 ? 32 : TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
   static_assert(STAGES >= 2, "shared memory ring too small");
 };
@@ -115,12 +116,30 @@ struct GramBlk {
 template <int DT, int KP>
 __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&p)[KP], float *Hs,
                                               const float *Gs, double *scratch, int et, int row) {
+  constexpr int HW = KP <= 16 ? KP : 16;  // columns whose state is held at once
   const int64_t r0 = (int64_t)tp * 128;
   const int rows = (int)((e.n - r0) < 128 ? (e.n - r0) : 128);
   const bool vrow = row < rows;
+  const bool rms = (e.method == SYMNMF_RMSPROP);
+  const int64_t base = (r0 + row) * KP;
   float *hrow = Hs + row * (KP + 1);
+  // state of the first HW columns, issued before the H Gram pass hides it
+  float av[HW], mv[HW];
+  auto load_state = [&](int c0) {
+#pragma unroll
+    for (int c4 = 0; c4 < HW / 4; ++c4) {
+      float4 u = make_float4(0.f, 0.f, 0.f, 0.f), w = u;
+      if (vrow && e.update) {
+        u = reinterpret_cast<const float4 *>(e.A + base + c0)[c4];
+        if (rms) w = reinterpret_cast<const float4 *>(e.M + base + c0)[c4];
+      }
+      av[4 * c4 + 0] = u.x; av[4 * c4 + 1] = u.y; av[4 * c4 + 2] = u.z; av[4 * c4 + 3] = u.w;
+      mv[4 * c4 + 0] = w.x; mv[4 * c4 + 1] = w.y; mv[4 * c4 + 2] = w.z; mv[4 * c4 + 3] = w.w;
+    }
+  };
+  load_state(0);
   {
-    const float4 *src = reinterpret_cast<const float4 *>(e.H + (r0 + row) * KP);
+    const float4 *src = reinterpret_cast<const float4 *>(e.H + base);
 #pragma unroll
     for (int c4 = 0; c4 < KP / 4; ++c4) {
       const float4 v = vrow ? src[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -130,10 +149,14 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
       hrow[4 * c4 + 3] = v.w;
     }
   }
-  // (H Gram_t) row, then g = coef ((H Gram_t) - S H) in place of p (Sec. 2.1)
-  float hg[KP];
+  // tr(H^T S H) share of the row, then g = coef ((H Gram_t) - S H) formed
+  // in place of p, H Gram_t right to left (Sec. 2.1)
+  float tr = 0.f, kkt2 = 0.f, sumA = 0.f, nonfin = 0.f;
 #pragma unroll
-  for (int c = 0; c < KP; ++c) hg[c] = 0.f;
+  for (int c = 0; c < KP; ++c) {
+    if (c < e.k) tr = fmaf(hrow[c], p[c], tr);
+    p[c] = -p[c];
+  }
 #pragma unroll 2
   for (int d = 0; d < KP; ++d) {
     const float hv = hrow[d];
@@ -141,123 +164,112 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
 #pragma unroll
     for (int c4 = 0; c4 < KP / 4; ++c4) {
       const float4 gv = gr[c4];
-      hg[4 * c4 + 0] = fmaf(hv, gv.x, hg[4 * c4 + 0]);
-      hg[4 * c4 + 1] = fmaf(hv, gv.y, hg[4 * c4 + 1]);
-      hg[4 * c4 + 2] = fmaf(hv, gv.z, hg[4 * c4 + 2]);
-      hg[4 * c4 + 3] = fmaf(hv, gv.w, hg[4 * c4 + 3]);
+      p[4 * c4 + 0] = fmaf(hv, gv.x, p[4 * c4 + 0]);
+      p[4 * c4 + 1] = fmaf(hv, gv.y, p[4 * c4 + 1]);
+      p[4 * c4 + 2] = fmaf(hv, gv.z, p[4 * c4 + 2]);
+      p[4 * c4 + 3] = fmaf(hv, gv.w, p[4 * c4 + 3]);
     }
   }
-  float tr = 0.f, kkt2 = 0.f, sumA = 0.f, nonfin = 0.f;
 #pragma unroll
   for (int c = 0; c < KP; ++c) {
-    const float h = hrow[c];
     float g = 0.f;
     if (c < e.k) {
-      g = e.coef * (hg[c] - p[c]);
-      tr = fmaf(h, p[c], tr);
-      const float pg = (h > 0.f) ? g : fminf(0.f, g);
+      g = e.coef * p[c];
+      const float pg = (hrow[c] > 0.f) ? g : fminf(0.f, g);
       kkt2 = fmaf(pg, pg, kkt2);
       if (!isfinite(g)) nonfin += 1.f;
     }
     p[c] = g;
   }
   if (!vrow) tr = kkt2 = nonfin = 0.f;
-  // update and projection, 8 columns at a time
-  const bool rms = (e.method == SYMNMF_RMSPROP);
-  const int64_t base = (r0 + row) * KP;
+  // update and projection, HW columns at a time
 #pragma unroll
-  for (int cc = 0; cc < KP; cc += 8) {
-    float av[8], mv[8], hn[8];
-    if (vrow && e.update) {
-      const float4 u = reinterpret_cast<const float4 *>(e.A + base + cc)[0];
-      const float4 v = reinterpret_cast<const float4 *>(e.A + base + cc)[1];
-      av[0] = u.x; av[1] = u.y; av[2] = u.z; av[3] = u.w;
-      av[4] = v.x; av[5] = v.y; av[6] = v.z; av[7] = v.w;
-      if (rms) {
-        const float4 s4 = reinterpret_cast<const float4 *>(e.M + base + cc)[0];
-        const float4 w4 = reinterpret_cast<const float4 *>(e.M + base + cc)[1];
-        mv[0] = s4.x; mv[1] = s4.y; mv[2] = s4.z; mv[3] = s4.w;
-        mv[4] = w4.x; mv[5] = w4.y; mv[6] = w4.z; mv[7] = w4.w;
-      } else {
+  for (int hc = 0; hc < KP; hc += HW) {
+    if (hc > 0) load_state(hc);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) mv[j] = 0.f;
-      }
-    } else {
+    for (int cc = hc; cc < hc + HW; cc += 8) {
+      float hn[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) av[j] = mv[j] = 0.f;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int c = cc + j;
-      const float h = hrow[c];
-      const float g = p[c];
-      hn[j] = h;
-      if (e.update) {
-        if (c < e.k && vrow) {
-          float x;
-          if (rms) {
-            const float v = e.alpha * av[j] + (1.f - e.alpha) * (g * g);
-            av[j] = v;
-            const float m = e.mom * mv[j] + e.eta * g / (sqrtf(v) + e.eps);
-            mv[j] = m;
-            x = h - m;
-            sumA += v;
+      for (int j = 0; j < 8; ++j) {
+        const int c = cc + j, s = cc - hc + j;
+        const float h = hrow[c];
+        const float g = p[c];
+        hn[j] = h;
+        if (e.update) {
+          if (c < e.k && vrow) {
+            float x;
+            if (rms) {
+              const float v = e.alpha * av[s] + (1.f - e.alpha) * (g * g);
+              av[s] = v;
+              const float m = e.mom * mv[s] + e.eta * g / (sqrtf(v) + e.eps);
+              mv[s] = m;
+              x = h - m;
+              sumA += v;
+            } else {
+              const float acc = av[s] + g * g;
+              av[s] = acc;
+              x = h - e.eta * g / (sqrtf(acc) + e.eps);
+              sumA += acc;
+            }
+            hn[j] = (x > 0.f) ? x : 0.f;
           } else {
-            const float acc = av[j] + g * g;
-            av[j] = acc;
-            x = h - e.eta * g / (sqrtf(acc) + e.eps);
-            sumA += acc;
+            hn[j] = 0.f;
           }
-          hn[j] = (x > 0.f) ? x : 0.f;
-        } else {
-          hn[j] = 0.f;
         }
       }
-    }
-    if (vrow) {
-      if (e.gout) {
-        reinterpret_cast<float4 *>(e.gout + base + cc)[0] = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
-        reinterpret_cast<float4 *>(e.gout + base + cc)[1] = make_float4(p[cc + 4], p[cc + 5], p[cc + 6], p[cc + 7]);
-      }
-      if (e.store_mu) {
-        reinterpret_cast<float4 *>(e.mu + base + cc)[0] = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
-        reinterpret_cast<float4 *>(e.mu + base + cc)[1] = make_float4(p[cc + 4], p[cc + 5], p[cc + 6], p[cc + 7]);
-      }
-      if (e.gcaller) {
+      const int s0 = cc - hc;
+      if (vrow) {
+        float4 *g4 = reinterpret_cast<float4 *>(e.gout + base + cc);
+        float4 *m4 = reinterpret_cast<float4 *>(e.mu + base + cc);
+        const float4 p0 = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
+        const float4 p1 = make_float4(p[cc + 4], p[cc + 5], p[cc + 6], p[cc + 7]);
+        if (e.gout) {
+          g4[0] = p0;
+          g4[1] = p1;
+        }
+        if (e.store_mu) {
+          m4[0] = p0;
+          m4[1] = p1;
+        }
+        if (e.gcaller) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (cc + j < e.k) e.gcaller[(r0 + row) * e.k + cc + j] = p[cc + j];
+          for (int j = 0; j < 8; ++j)
+            if (cc + j < e.k) e.gcaller[(r0 + row) * e.k + cc + j] = p[cc + j];
+        }
+        if (e.update) {
+          float4 *a4 = reinterpret_cast<float4 *>(e.A + base + cc);
+          a4[0] = make_float4(av[s0], av[s0 + 1], av[s0 + 2], av[s0 + 3]);
+          a4[1] = make_float4(av[s0 + 4], av[s0 + 5], av[s0 + 6], av[s0 + 7]);
+          if (rms) {
+            float4 *v4 = reinterpret_cast<float4 *>(e.M + base + cc);
+            v4[0] = make_float4(mv[s0], mv[s0 + 1], mv[s0 + 2], mv[s0 + 3]);
+            v4[1] = make_float4(mv[s0 + 4], mv[s0 + 5], mv[s0 + 6], mv[s0 + 7]);
+          }
+          float4 *h4 = reinterpret_cast<float4 *>(e.Hn + base + cc);
+          h4[0] = make_float4(hn[0], hn[1], hn[2], hn[3]);
+          h4[1] = make_float4(hn[4], hn[5], hn[6], hn[7]);
+        }
       }
       if (e.update) {
-        reinterpret_cast<float4 *>(e.A + base + cc)[0] = make_float4(av[0], av[1], av[2], av[3]);
-        reinterpret_cast<float4 *>(e.A + base + cc)[1] = make_float4(av[4], av[5], av[6], av[7]);
-        if (rms) {
-          reinterpret_cast<float4 *>(e.M + base + cc)[0] = make_float4(mv[0], mv[1], mv[2], mv[3]);
-          reinterpret_cast<float4 *>(e.M + base + cc)[1] = make_float4(mv[4], mv[5], mv[6], mv[7]);
-        }
-        reinterpret_cast<float4 *>(e.Hn + base + cc)[0] = make_float4(hn[0], hn[1], hn[2], hn[3]);
-        reinterpret_cast<float4 *>(e.Hn + base + cc)[1] = make_float4(hn[4], hn[5], hn[6], hn[7]);
-      }
-    }
-    if (e.update) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) hrow[cc + j] = hn[j];
-      if (e.Btn) {
-        if (e.bt_fmt == 0) {
-          uint16_t *B = reinterpret_cast<uint16_t *>(e.Btn);
+        for (int j = 0; j < 8; ++j) hrow[cc + j] = hn[j];
+        if (e.Btn) {
+          if (e.bt_fmt == 0) {
+            uint16_t *B = reinterpret_cast<uint16_t *>(e.Btn);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const uint16_t hi = bf16_bits(hn[j]);
-            B[(int64_t)(cc + j) * e.ldb + r0 + row] = hi;
-            B[(int64_t)(KP + cc + j) * e.ldb + r0 + row] = bf16_bits(hn[j] - bf16_val(hi));
-          }
-        } else {
-          float *B = reinterpret_cast<float *>(e.Btn);
+            for (int j = 0; j < 8; ++j) {
+              const uint16_t hi = bf16_bits(hn[j]);
+              B[(int64_t)(cc + j) * e.ldb + r0 + row] = hi;
+              B[(int64_t)(KP + cc + j) * e.ldb + r0 + row] = bf16_bits(hn[j] - bf16_val(hi));
+            }
+          } else {
+            float *B = reinterpret_cast<float *>(e.Btn);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float hi = tf32_trunc(hn[j]);
-            B[(int64_t)(cc + j) * e.ldb + r0 + row] = hi;
-            B[(int64_t)(KP + cc + j) * e.ldb + r0 + row] = tf32_round(hn[j] - hi);
+            for (int j = 0; j < 8; ++j) {
+              const float hi = tf32_trunc(hn[j]);
+              B[(int64_t)(cc + j) * e.ldb + r0 + row] = hi;
+              B[(int64_t)(KP + cc + j) * e.ldb + r0 + row] = tf32_round(hn[j] - hi);
+            }
           }
         }
       }
@@ -311,83 +323,121 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
   epi_bar();
 }
 
+// Shared-memory handshake between the folder and epilogue warps: the folders
+// hand over one finished P row block per tile segment through the TMEM P
+// buffer pb (double-buffered); pflag[pb] says whether this CTA finishes the
+// tile (otherwise another CTA does, from the partial slots).
+struct Hand {
+  uint64_t *pfull, *pempty;
+  volatile int *pflag;
+};
+
+// Epilogue warps 2-5: one thread per tile row.
 template <int DT, int KP>
 __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_base, float *Hs,
-                              float *Gs, double *scratch, int *sflag, uint64_t *tfull,
-                              uint64_t *tempty, volatile int *abort_flag, int64_t L0, int64_t L1,
-                              int b) {
+                              float *Gs, double *scratch, const Hand &hd,
+                              volatile int *abort_flag, int64_t L0, int64_t L1) {
   using C = Cfg<DT, KP>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3;
   const int row = q * 32 + lane;
   const int et = (warp - 2) * 32 + lane;
-  if (a.fused)
-    for (int i = et; i < KP * KP; i += 128) Gs[i] = e.gram[i];
+  if (!a.fused) return;
+  for (int i = et; i < KP * KP; i += 128) Gs[i] = e.gram[i];
   epi_bar();
-  int acc = 0;
-  uint32_t tph[2] = {0u, 0u};
-  bool ok = true;
-  int64_t L = L0;
-  while (L < L1 && ok) {
+  int pb = 0;
+  uint32_t pph[2] = {0u, 0u};
+  for (int64_t L = L0; L < L1;) {
     const int tp = (int)(L / a.n_cols);
     const int64_t tile_end = (int64_t)(tp + 1) * a.n_cols;
-    const int64_t seg_end = L1 < tile_end ? L1 : tile_end;
-    // fold the segment's accumulator chunks into FP32 registers
-    float p[KP];
-#pragma unroll
-    for (int c = 0; c < KP; ++c) p[c] = 0.f;
-    const int64_t nfold = (seg_end - L) * (C::SPU / C::FOLD);
-    for (int64_t f = 0; f < nfold; ++f) {
-      if (!warp_wait(&tfull[acc], tph[acc], abort_flag)) {
-        if (lane == 0) {
-          set_err(a.err, 5);
-          *abort_flag = 1;
-        }
-        ok = false;
-        break;
+    L = L1 < tile_end ? L1 : tile_end;
+    if (!warp_wait(&hd.pfull[pb], pph[pb], abort_flag)) {
+      if (lane == 0) {
+        set_err(a.err, 6);
+        *abort_flag = 1;
       }
-      fence_after();
-      const uint32_t tb =
-          tmem_base + ((uint32_t)(q * 32) << 16) + C::ACC0 + (uint32_t)(acc * C::N);
+      return;
+    }
+    fence_after();
+    const int epi = hd.pflag[pb];
+    float p[KP];
+    if (epi) {
+      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + C::PB0 + (uint32_t)(pb * KP);
 #pragma unroll
       for (int cc = 0; cc < KP; cc += 8) {
-        uint32_t x[16];
-        tmem_ld_pair(tb + cc, tb + KP + cc, x);
+        uint32_t x[8];
+        tmem_ld8(tb + cc, x);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) p[cc + j] += __uint_as_float(x[j]) + __uint_as_float(x[8 + j]);
+        for (int j = 0; j < 8; ++j) p[cc + j] = __uint_as_float(x[j]);
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[acc]);
-      tph[acc] ^= 1;
-      acc ^= 1;
     }
-    if (!ok) break;
-    bool do_epi = false;
+    fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&hd.pempty[pb]);
+    pph[pb] ^= 1;
+    pb ^= 1;
+    if (epi) tile_epilogue<DT, KP>(e, tp, p, Hs, Gs, scratch, et, row);
+  }
+}
+
+// Folder warps 6-9: fold each accumulator chain (<= 16 MMAs) into FP32
+// registers, one thread per tile row, and hand the tile segment's P over.
+// With FP32 storage the same warps first convert each staged S row into
+// its tf32 hi / lo parts in TMEM (the MMA's A operand).
+template <int DT, int KP>
+__device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, uint64_t *full,
+                            uint64_t *empty, uint64_t *afull, uint64_t *aempty, uint64_t *tfull,
+                            uint64_t *tempty, const Hand &hd, int *sflag,
+                            volatile int *abort_flag, int64_t L0, int64_t L1, int b) {
+  using C = Cfg<DT, KP>;
+  constexpr int STAGES = C::STAGES;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3;
+  const int row = q * 32 + lane;
+  const int ft = (warp - 6) * 32 + lane;
+  const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+  const int64_t c0 = L0 * C::SPU, c1 = L1 * C::SPU;
+  float p[KP];
+#pragma unroll
+  for (int c = 0; c < KP; ++c) p[c] = 0.f;
+  int acc = 0, pb = 0;
+  uint32_t tph[2] = {0u, 0u}, pph[2] = {0u, 0u};
+  bool ok = true;
+
+  auto fail = [&](int code) {
+    if (lane == 0) {
+      set_err(a.err, code);
+      *abort_flag = 1;
+    }
+    ok = false;
+  };
+  // hand the finished segment of tile tp over (or leave a partial)
+  auto finish_segment = [&](int tp) {
     int64_t b0 = b, b1 = b;
+    int epi = 0;
     if (a.fused) {
       b0 = sk_cta((int64_t)tp * a.n_cols, a.W, a.G);
       b1 = sk_cta((int64_t)tp * a.n_cols + a.n_cols - 1, a.W, a.G);
-      do_epi = (b0 == b1);
+      epi = (b0 == b1);
     }
-    if (!do_epi) {
+    if (!epi) {
       float *dst = a.out + ((int64_t)(b + tp) * 128 + row) * KP;
 #pragma unroll
       for (int cc = 0; cc < KP; cc += 4)
         reinterpret_cast<float4 *>(dst + cc)[0] = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
       if (a.fused) {
         __threadfence();
-        epi_bar();
-        if (et == 0) {
+        fold_bar();
+        if (ft == 0) {
           const int old = atomicAdd(&a.tile_cnt[tp], 1);
           const int last = (old == (int)(b1 - b0));
           if (last) a.tile_cnt[tp] = 0;
           *reinterpret_cast<volatile int *>(sflag) = last;
         }
-        epi_bar();
-        do_epi = *reinterpret_cast<volatile int *>(sflag) != 0;
-        if (do_epi) {
-          // partials of the tile's CTAs, added in CTA order
+        fold_bar();
+        epi = *reinterpret_cast<volatile int *>(sflag);
+        if (epi) {
+          // the tile's partials, added in CTA order
           __threadfence();
 #pragma unroll
           for (int c = 0; c < KP; ++c) p[c] = 0.f;
@@ -406,8 +456,109 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
         }
       }
     }
-    if (do_epi) tile_epilogue<DT, KP>(e, tp, p, Hs, Gs, scratch, et, row);
-    L = seg_end;
+    if (a.fused) {
+      if (!warp_wait(&hd.pempty[pb], pph[pb] ^ 1, abort_flag)) {
+        fail(7);
+        return;
+      }
+      fence_after();
+      if (epi) {
+        const uint32_t tb = tmem_base + lane_off + C::PB0 + (uint32_t)(pb * KP);
+#pragma unroll
+        for (int cc = 0; cc < KP; cc += 8) {
+          float v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = p[cc + j];
+          tmem_st8(tb + cc, v);
+        }
+        tmem_wait_st();
+      }
+      if (ft == 0) hd.pflag[pb] = epi;
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&hd.pfull[pb]);
+      pph[pb] ^= 1;
+      pb ^= 1;
+    }
+#pragma unroll
+    for (int c = 0; c < KP; ++c) p[c] = 0.f;
+  };
+  // fold accumulator chain f (stage-sized chunks [f FOLD, (f+1) FOLD))
+  auto fold = [&](int64_t f) {
+    if (!warp_wait(&tfull[acc], tph[acc], abort_flag)) {
+      fail(5);
+      return;
+    }
+    fence_after();
+    const uint32_t tb = tmem_base + lane_off + C::ACC0 + (uint32_t)(acc * C::N);
+#pragma unroll
+    for (int cc = 0; cc < KP; cc += 8) {
+      uint32_t x[16];
+      tmem_ld_pair(tb + cc, tb + KP + cc, x);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) p[cc + j] += __uint_as_float(x[j]) + __uint_as_float(x[8 + j]);
+    }
+    fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&tempty[acc]);
+    tph[acc] ^= 1;
+    acc ^= 1;
+    const int64_t cend = (f + 1) * C::FOLD;
+    if (cend % C::SPU == 0) {
+      const int64_t u = cend / C::SPU - 1;  // unit just completed
+      if (u + 1 == L1 || (u + 1) % a.n_cols == 0) finish_segment((int)(u / a.n_cols));
+    }
+  };
+
+  if constexpr (C::F32) {
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t eph[2] = {0u, 0u};
+    for (int64_t c = c0; c < c1 && ok; ++c) {
+      const int ab = (int)((c - c0) & 1);
+      if (!warp_wait(&full[stage], phase, abort_flag) ||
+          !warp_wait(&aempty[ab], eph[ab] ^ 1, abort_flag)) {
+        fail(15);
+        break;
+      }
+      fence_after();
+      const uint8_t *sa = smem + stage * C::STAGE;
+#pragma unroll
+      for (int at = 0; at < C::APS; ++at) {
+        const uint8_t *rowp = sa + at * kAtomBytes + row * 128;
+        uint32_t hi[32], lo[32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 v = *reinterpret_cast<const float4 *>(rowp + ((j ^ (row & 7)) << 4));
+          const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float h = tf32_trunc(x[u]);
+            hi[4 * j + u] = __float_as_uint(h);
+            lo[4 * j + u] = __float_as_uint(tf32_round(x[u] - h));
+          }
+        }
+        const uint32_t base = tmem_base + lane_off + (uint32_t)ab * C::ABUF + (uint32_t)at * 32u;
+        tmem_st32(base, hi);
+        tmem_st32(base + 32u * C::APS, lo);
+      }
+      tmem_wait_st();
+      fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&empty[stage]);
+        mbar_arrive(&afull[ab]);
+      }
+      eph[ab] ^= 1;
+      if (++stage == STAGES) {
+        stage = 0;
+        phase ^= 1;
+      }
+      if (c > c0) fold(c - 1);  // FOLD == 1: one chain per stage
+    }
+    if (ok && c1 > c0) fold(c1 - 1);
+  } else {
+    for (int64_t f = c0 / C::FOLD; f < c1 / C::FOLD && ok; ++f) fold(f);
   }
 }
 
@@ -429,11 +580,14 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
   uint64_t *aempty = afull + 2;
   uint64_t *tfull = aempty + 2;
   uint64_t *tempty = tfull + 2;
-  uint64_t *drain = tempty + 2;
+  uint64_t *pfull = tempty + 2;
+  uint64_t *pempty = pfull + 2;
+  uint64_t *drain = pempty + 2;
   uint32_t *holder = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(holder + 1);
   int *consumed = const_cast<int *>(abort_flag) + 1;
   int *sflag = consumed + 1;
+  volatile int *pflag = sflag + 1;  // two entries
   float *Hs = reinterpret_cast<float *>(smem + STAGES * C::STAGE + C::BAR_BYTES);
   float *Gs = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(Hs + 128 * (KP + 1)) + 15) & ~uintptr_t(15));
@@ -451,6 +605,8 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
       mbar_init(&aempty[i], 1);
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], 4);
+      mbar_init(&pfull[i], 4);
+      mbar_init(&pempty[i], 4);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -573,62 +729,12 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
       if (!mbar_wait(drain, 0, abort_flag, 100000000ull) && !*abort_flag) set_err(a.err, 4);
     }
   } else if (warp >= 6) {
-    if constexpr (F32) {
-      // converters: one thread per row of the tile
-      const int q = warp & 3;
-      const int row = q * 32 + lane;
-      const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-      int stage = 0;
-      uint32_t phase = 0;
-      uint32_t eph[2] = {0u, 0u};
-      for (int64_t c = c0; c < c1; ++c) {
-        const int ab = (int)((c - c0) & 1);
-        if (!warp_wait(&full[stage], phase, abort_flag) ||
-            !warp_wait(&aempty[ab], eph[ab] ^ 1, abort_flag)) {
-          if (lane == 0) {
-            set_err(a.err, 15);
-            *abort_flag = 1;
-          }
-          break;
-        }
-        fence_after();
-        const uint8_t *sa = smem + stage * C::STAGE;
-#pragma unroll
-        for (int at = 0; at < C::APS; ++at) {
-          const uint8_t *rowp = sa + at * kAtomBytes + row * 128;
-          uint32_t hi[32], lo[32];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float4 v = *reinterpret_cast<const float4 *>(rowp + ((j ^ (row & 7)) << 4));
-            const float x[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float h = tf32_trunc(x[u]);
-              hi[4 * j + u] = __float_as_uint(h);
-              lo[4 * j + u] = __float_as_uint(tf32_round(x[u] - h));
-            }
-          }
-          const uint32_t base = tmem_base + lane_off + (uint32_t)ab * C::ABUF + (uint32_t)at * 32u;
-          tmem_st32(base, hi);
-          tmem_st32(base + 32u * C::APS, lo);
-        }
-        tmem_wait_st();
-        fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&empty[stage]);
-          mbar_arrive(&afull[ab]);
-        }
-        eph[ab] ^= 1;
-        if (++stage == STAGES) {
-          stage = 0;
-          phase ^= 1;
-        }
-      }
-    }
+    const Hand hd{pfull, pempty, pflag};
+    folder_role<DT, KP>(a, tmem_base, smem, full, empty, afull, aempty, tfull, tempty, hd, sflag,
+                        abort_flag, L0, L1, b);
   } else {
-    epilogue_role<DT, KP>(a, e, tmem_base, Hs, Gs, scratch, sflag, tfull, tempty, abort_flag, L0,
-                          L1, b);
+    const Hand hd{pfull, pempty, pflag};
+    epilogue_role<DT, KP>(a, e, tmem_base, Hs, Gs, scratch, hd, abort_flag, L0, L1);
   }
   __syncthreads();
   if (warp == 0 && lane == 0 && *abort_flag) {

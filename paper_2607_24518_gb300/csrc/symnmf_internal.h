@@ -1,8 +1,10 @@
 // Internal declarations shared by the host runtime (capi.cu) and the kernels.
 // Layout conventions (all owned buffers):
 //   * row tiles are 128 rows; ntiles = ceil(n / 128)
-//   * n x k state arrays are stored n x kp (kp = 8, 16, 32 or 64 >= k), the
-//     columns k..kp-1 held at exactly 0, so the padded columns never move
+//   * n x k state arrays (H, G / v, m, mu, g) are stored row-major with kp
+//     (8, 16, 32 or 64 >= k) columns and ntiles * 128 rows; columns k..kp-1
+//     and rows past n are held at exactly 0, so the padding never moves
+//   * product partial slots are 128 x kp row-major blocks
 //   * the MMA copy of H is stored transposed, [2*kp][ldb] with rows 0..kp-1
 //     = hi(H^T) and kp..2kp-1 = lo(H^T), ldb = ntiles * 128 (columns past n
 //     are 0), in one of two formats (bt_fmt):
@@ -16,6 +18,7 @@
 namespace symnmf {
 
 constexpr int kTileRows = 128;
+
 constexpr int kRing = 1024;  // device record ring (iterations)
 
 enum Mode : int { MODE_FULL = 0, MODE_ROWS = 1, MODE_BLOCK = 2, MODE_GRAD_ONLY = 3 };
@@ -28,8 +31,7 @@ struct DevRecord {
 };
 
 // S x H product over a list of 128-row tiles and a list of 128-column tiles.
-// out[(split * n_rows_list + row_pos) * 128 * kp + r * kp + c] holds the
-// partial sum of split `split` (a contiguous share of the column list).
+// Partial slot s holds 128 x kp values at out[(s * 128 + r) * kp + c].
 struct ProdArgs {
   const void *S;
   int64_t lds;           // row pitch of S in elements
@@ -38,7 +40,7 @@ struct ProdArgs {
   int64_t ld_scales;
   int64_t n;
   int k, kp;
-  const float *H;        // FP32 master, n x kp (SIMT path)
+  const float *H;        // FP32 master, row-major n x kp (SIMT path)
   const void *Bt;        // hi/lo transposed copy (tensor-core path)
   int bt_fmt;
   int64_t ldb;

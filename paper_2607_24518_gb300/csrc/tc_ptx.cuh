@@ -164,8 +164,30 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
 __device__ __forceinline__ void set_err(int *err, int code) {
   if (err) atomicCAS(err, 0, code);
 }
-// named barrier among the 128 epilogue threads (warps 2-5)
+// named barriers: 1 among the 128 epilogue threads (warps 2-5), 2 among
+// the 128 folder threads (warps 6-9)
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void fold_bar() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+// 8 consecutive columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_st8(uint32_t ta, const float (&v)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, uint32_t (&x)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]),
+                 "=r"(x[6]), "=r"(x[7])
+               : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3]), "+r"(x[4]), "+r"(x[5]),
+                 "+r"(x[6]), "+r"(x[7])
+               :
+               : "memory");
+}
 
 }  // namespace tc
 }  // namespace symnmf
