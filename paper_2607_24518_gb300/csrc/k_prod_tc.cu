@@ -10,25 +10,28 @@
 //               buffered 128 x 2kp TMEM accumulator (columns [0,kp) multiply
 //               H_hi, [kp,2kp) multiply H_lo) and frees stages with
 //               tcgen05.commit
-//   warps 2-5   epilogue, one thread per tile row: reads the accumulator
+//   warps 2-9   epilogue, two threads per tile row (half the columns each):
 //               (tcgen05.ld), P = acc_hi + acc_lo, and for a finished tile
 //               runs the whole per-row update: g = 4 (H Gram_t - P), the
 //               AdaGrad / RMSprop step with the max(0, .) projection into the
 //               other H buffer, the hi/lo MMA copy of the new rows, and the
 //               tile partials tr = sum H * P, ||grad_proj||^2, sum(G), NaN
 //               count and the Gram partial H'^T H'
-//   warps 6-9   (FP32 storage only) converters, see below
+//   warps 10-13 folders: fold each accumulator chain into FP32 registers and
+//               hand a finished tile segment's P over; with FP32 storage
+//               they also convert the staged S rows, see below
 // Storage types:
 //   BF16  kind::f16, A = S straight from shared memory, B = [H_hi | H_lo]
 //         in bf16 (H enters with about 16 significant bits)
-//   FP32  error-compensated TF32 (after Ootomo & Yokota, IJHPCA 2022): the
-//         converter warps split each staged S row into S_hi (13 low mantissa
-//         bits cleared, exact in tf32) and S_lo = round_tf32(S - S_hi) and
-//         store both in tensor memory, where the MMA reads its A operand
-//         (shared memory is read once per S byte); with B = [H_hi | H_lo]
-//         in tf32 the two MMAs per k-slice accumulate
-//         (S_hi + S_lo)(H_hi + H_lo), leaving only the rounding of the lo
-//         parts (relative 2^-22, unbiased)
+//   FP32  error-compensated TF32 (after Ootomo & Yokota, IJHPCA 2022):
+//         kind::tf32 reads the staged FP32 S tile straight from shared
+//         memory and uses its 19 high bits, i.e. S_hi = S with the 13 low
+//         mantissa bits cleared; the converter warps form
+//         S_lo = round_tf32(S - S_hi) and store it in tensor memory, where a
+//         second MMA reads it as its A operand.  With B = [H_hi | H_lo] in
+//         tf32 the k-slice accumulates S_hi [H_hi | H_lo] into one
+//         accumulator and S_lo H_hi into a second one, leaving only
+//         S_lo H_lo (relative 2^-22) and the rounding of the lo parts
 // Work: the row-major list of (row tile, 128-column tile) units is split
 // into equal contiguous ranges, one per CTA (stream-K), so every SM streams
 // the same number of S bytes.  A tile whose units span several CTAs is
@@ -75,7 +78,7 @@ struct Cfg {
   static constexpr bool F32 = (DT == 0);
   static constexpr int N = 2 * KP;
   static constexpr int ATOM_COLS = F32 ? 32 : 64;       // elements per 128-byte row
-  static constexpr int APS = (KP == 64) ? 1 : 2;         // swizzle atoms per stage
+  static constexpr int APS = (KP == 64) ? 1 : 2;          // swizzle atoms per stage
   static constexpr int SPU = 128 / (APS * ATOM_COLS);    // stages per 128-column unit
   static constexpr int KSL = 4 * APS;                    // MMA k-slices per stage
   static constexpr uint32_t A_BYTES = APS * kAtomBytes;
@@ -83,7 +86,8 @@ struct Cfg {
   static constexpr uint32_t B_BYTES = APS * B_ATOM;
   static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
   // stages per accumulator chain: the tensor core's FP32 accumulation is
-  // kept to at most 16 chained MMAs, the rest is summed in FP32 registers
+  // kept to at most 8 chained MMAs per accumulator, the rest is summed in
+  // FP32 registers
   static constexpr int FOLD = F32 ? 1 : SPU;
   static constexpr uint32_t EPI_FLOATS = 128 * (KP + 1) + KP * KP;
   static constexpr uint32_t EPI_BYTES = EPI_FLOATS * 4 + 512;
@@ -91,10 +95,15 @@ struct Cfg {
   static constexpr uint32_t BUDGET = 232448u - 1024u - BAR_BYTES - EPI_BYTES;
   static constexpr int STAGES = (BUDGET / STAGE) < 8u ? (int)(BUDGET / STAGE) : 8;
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + BAR_BYTES + EPI_BYTES;
-  static constexpr int THREADS = 320;
-  static constexpr uint32_t ABUF = F32 ? 64u * APS : 0u;  // TMEM columns per A buffer
-  static constexpr uint32_t ACC0 = 2 * ABUF;
-  static constexpr uint32_t PB0 = ACC0 + 2 * N;           // double-buffered P rows
+  static constexpr int THREADS = 448;  // 14 warps: TMA, MMA, 8 epilogue, 4 folder
+  // FP32: TMEM columns of one S_lo buffer, number of S_lo buffers, width
+  // of the separate S_lo H accumulator (0: shared with the main one)
+  static constexpr uint32_t ABUF = F32 ? 32u * APS : 0u;
+  static constexpr int NABUF = F32 ? 2 : 1;
+  static constexpr int NL = (F32 && KP <= 32) ? (KP >= 16 ? KP : N) : 0;
+  static constexpr uint32_t ACC0 = F32 ? NABUF * ABUF : 0u;
+  static constexpr uint32_t ACCW = N + NL;                // columns per accumulator buffer
+  static constexpr uint32_t PB0 = ACC0 + 2 * ACCW;        // double-buffered P rows
   static constexpr uint32_t TMEM_NEED = PB0 + 2 * KP;
   static constexpr uint32_t TMEM_COLS = TMEM_NEED <= 32 ? 32 : TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
   static_assert(STAGES >= 2, "shared memory ring too small");
@@ -104,26 +113,37 @@ struct Cfg {
 // Register-block shape of the per-thread share of the kp x kp Gram partial
 template <int KP>
 struct GramBlk {
-  static constexpr int BR = KP == 64 ? 8 : KP == 32 ? 4 : KP == 16 ? 2 : 1;
+  static constexpr int BR = KP == 64 ? 4 : KP == 32 ? 2 : 1;
   static constexpr int BC = KP == 64 ? 4 : KP == 32 ? 2 : 1;
-  static constexpr int NBLK = (KP / BR) * (KP / BC);  // <= 128
+  static constexpr int NBLK = (KP / BR) * (KP / BC);  // <= 256
 };
 
 // Per-tile update for the thread's row (row = tile row, et = index among the
 // 128 epilogue threads); p holds the row of S H for H_t, summed in FP32 in
 // a fixed order.  Everything the iteration produces for this tile is
 // written here; the cross-tile sums are left to the reduction kernel.
+// columns owned by each of the two epilogue threads of a row (kp = 8: the
+// first thread owns all of them, the second only joins the barriers)
+template <int KP>
+struct Own {
+  static constexpr int KH = KP >= 16 ? KP / 2 : KP;
+  static constexpr int HW = KH <= 16 ? KH : 16;  // columns whose state is held at once
+};
+
 template <int DT, int KP>
-__device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&p)[KP], float *Hs,
-                                              const float *Gs, double *scratch, int et, int row) {
-  constexpr int HW = KP <= 16 ? KP : 16;  // columns whose state is held at once
+__device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&p)[Own<KP>::KH],
+                                              float *Hs, const float *Gs, double *scratch, int et,
+                                              int row, int half) {
+  constexpr int KH = Own<KP>::KH;
+  constexpr int HW = Own<KP>::HW;
+  const bool works = (KP >= 16) || half == 0;
+  const int cb = (KP >= 16) ? half * KH : 0;  // first owned column
   const int64_t r0 = (int64_t)tp * 128;
   const int rows = (int)((e.n - r0) < 128 ? (e.n - r0) : 128);
-  const bool vrow = row < rows;
+  const bool vrow = works && row < rows;
   const bool rms = (e.method == SYMNMF_RMSPROP);
-  const int64_t base = (r0 + row) * KP;
+  const int64_t base = (r0 + row) * KP + cb;
   float *hrow = Hs + row * (KP + 1);
-  // state of the first HW columns, issued before the H Gram pass hides it
   float av[HW], mv[HW];
   auto load_state = [&](int c0) {
 #pragma unroll
@@ -138,31 +158,33 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
     }
   };
   load_state(0);
-  {
+  if (works) {
+    const bool in = row < rows;
     const float4 *src = reinterpret_cast<const float4 *>(e.H + base);
 #pragma unroll
-    for (int c4 = 0; c4 < KP / 4; ++c4) {
-      const float4 v = vrow ? src[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
-      hrow[4 * c4 + 0] = v.x;
-      hrow[4 * c4 + 1] = v.y;
-      hrow[4 * c4 + 2] = v.z;
-      hrow[4 * c4 + 3] = v.w;
+    for (int c4 = 0; c4 < KH / 4; ++c4) {
+      const float4 v = in ? src[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      hrow[cb + 4 * c4 + 0] = v.x;
+      hrow[cb + 4 * c4 + 1] = v.y;
+      hrow[cb + 4 * c4 + 2] = v.z;
+      hrow[cb + 4 * c4 + 3] = v.w;
     }
   }
+  epi_bar();  // both halves of each H_t row are in Hs
   // tr(H^T S H) share of the row, then g = coef ((H Gram_t) - S H) formed
   // in place of p, H Gram_t right to left (Sec. 2.1)
   float tr = 0.f, kkt2 = 0.f, sumA = 0.f, nonfin = 0.f;
 #pragma unroll
-  for (int c = 0; c < KP; ++c) {
-    if (c < e.k) tr = fmaf(hrow[c], p[c], tr);
-    p[c] = -p[c];
+  for (int j = 0; j < KH; ++j) {
+    if (cb + j < e.k) tr = fmaf(hrow[cb + j], p[j], tr);
+    p[j] = -p[j];
   }
 #pragma unroll 2
   for (int d = 0; d < KP; ++d) {
     const float hv = hrow[d];
-    const float4 *gr = reinterpret_cast<const float4 *>(Gs + d * KP);
+    const float4 *gr = reinterpret_cast<const float4 *>(Gs + d * KP + cb);
 #pragma unroll
-    for (int c4 = 0; c4 < KP / 4; ++c4) {
+    for (int c4 = 0; c4 < KH / 4; ++c4) {
       const float4 gv = gr[c4];
       p[4 * c4 + 0] = fmaf(hv, gv.x, p[4 * c4 + 0]);
       p[4 * c4 + 1] = fmaf(hv, gv.y, p[4 * c4 + 1]);
@@ -171,29 +193,30 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
     }
   }
 #pragma unroll
-  for (int c = 0; c < KP; ++c) {
+  for (int j = 0; j < KH; ++j) {
     float g = 0.f;
-    if (c < e.k) {
-      g = e.coef * p[c];
-      const float pg = (hrow[c] > 0.f) ? g : fminf(0.f, g);
+    if (cb + j < e.k) {
+      g = e.coef * p[j];
+      const float pg = (hrow[cb + j] > 0.f) ? g : fminf(0.f, g);
       kkt2 = fmaf(pg, pg, kkt2);
       if (!isfinite(g)) nonfin += 1.f;
     }
-    p[c] = g;
+    p[j] = g;
   }
   if (!vrow) tr = kkt2 = nonfin = 0.f;
+  epi_bar();  // every thread has read H_t from Hs
   // update and projection, HW columns at a time
 #pragma unroll
-  for (int hc = 0; hc < KP; hc += HW) {
+  for (int hc = 0; hc < KH; hc += HW) {
     if (hc > 0) load_state(hc);
 #pragma unroll
     for (int cc = hc; cc < hc + HW; cc += 8) {
       float hn[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const int c = cc + j, s = cc - hc + j;
+        const int c = cb + cc + j, s = cc - hc + j;
         const float h = hrow[c];
-        const float g = p[c];
+        const float g = p[cc + j];
         hn[j] = h;
         if (e.update) {
           if (c < e.k && vrow) {
@@ -219,22 +242,22 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
       }
       const int s0 = cc - hc;
       if (vrow) {
-        float4 *g4 = reinterpret_cast<float4 *>(e.gout + base + cc);
-        float4 *m4 = reinterpret_cast<float4 *>(e.mu + base + cc);
         const float4 p0 = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
         const float4 p1 = make_float4(p[cc + 4], p[cc + 5], p[cc + 6], p[cc + 7]);
         if (e.gout) {
+          float4 *g4 = reinterpret_cast<float4 *>(e.gout + base + cc);
           g4[0] = p0;
           g4[1] = p1;
         }
         if (e.store_mu) {
+          float4 *m4 = reinterpret_cast<float4 *>(e.mu + base + cc);
           m4[0] = p0;
           m4[1] = p1;
         }
         if (e.gcaller) {
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            if (cc + j < e.k) e.gcaller[(r0 + row) * e.k + cc + j] = p[cc + j];
+            if (cb + cc + j < e.k) e.gcaller[(r0 + row) * e.k + cb + cc + j] = p[cc + j];
         }
         if (e.update) {
           float4 *a4 = reinterpret_cast<float4 *>(e.A + base + cc);
@@ -250,25 +273,25 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
           h4[1] = make_float4(hn[4], hn[5], hn[6], hn[7]);
         }
       }
-      if (e.update) {
+      if (e.update && works) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) hrow[cc + j] = hn[j];
+        for (int j = 0; j < 8; ++j) hrow[cb + cc + j] = hn[j];
         if (e.Btn) {
           if (e.bt_fmt == 0) {
             uint16_t *B = reinterpret_cast<uint16_t *>(e.Btn);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const uint16_t hi = bf16_bits(hn[j]);
-              B[(int64_t)(cc + j) * e.ldb + r0 + row] = hi;
-              B[(int64_t)(KP + cc + j) * e.ldb + r0 + row] = bf16_bits(hn[j] - bf16_val(hi));
+              B[(int64_t)(cb + cc + j) * e.ldb + r0 + row] = hi;
+              B[(int64_t)(KP + cb + cc + j) * e.ldb + r0 + row] = bf16_bits(hn[j] - bf16_val(hi));
             }
           } else {
             float *B = reinterpret_cast<float *>(e.Btn);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const float hi = tf32_trunc(hn[j]);
-              B[(int64_t)(cc + j) * e.ldb + r0 + row] = hi;
-              B[(int64_t)(KP + cc + j) * e.ldb + r0 + row] = tf32_round(hn[j] - hi);
+              B[(int64_t)(cb + cc + j) * e.ldb + r0 + row] = hi;
+              B[(int64_t)(KP + cb + cc + j) * e.ldb + r0 + row] = tf32_round(hn[j] - hi);
             }
           }
         }
@@ -317,7 +340,9 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
     for (int i = 0; i < 4; ++i) scratch[(et >> 5) * 4 + i] = v4[i];
   epi_bar();
   if (et < 4 && e.slots) {
-    const double sv = scratch[et] + scratch[4 + et] + scratch[8 + et] + scratch[12 + et];
+    double sv = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sv += scratch[4 * w + et];
     e.slots[(int64_t)tp * kSlotStride + et] = sv;
   }
   epi_bar();
@@ -341,9 +366,10 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3;
   const int row = q * 32 + lane;
-  const int et = (warp - 2) * 32 + lane;
+  const int et = (warp - 2) * 32 + lane;  // 0..255
+  const int half = (warp - 2) >> 2;       // column half owned
   if (!a.fused) return;
-  for (int i = et; i < KP * KP; i += 128) Gs[i] = e.gram[i];
+  for (int i = et; i < KP * KP; i += 256) Gs[i] = e.gram[i];
   epi_bar();
   int pb = 0;
   uint32_t pph[2] = {0u, 0u};
@@ -351,7 +377,7 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     const int tp = (int)(L / a.n_cols);
     const int64_t tile_end = (int64_t)(tp + 1) * a.n_cols;
     L = L1 < tile_end ? L1 : tile_end;
-    if (!warp_wait(&hd.pfull[pb], pph[pb], abort_flag)) {
+    if (!warp_wait_idle(&hd.pfull[pb], pph[pb], abort_flag)) {
       if (lane == 0) {
         set_err(a.err, 6);
         *abort_flag = 1;
@@ -360,11 +386,13 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     }
     fence_after();
     const int epi = hd.pflag[pb];
-    float p[KP];
+    constexpr int KH = Own<KP>::KH;
+    float p[KH];
     if (epi) {
-      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + C::PB0 + (uint32_t)(pb * KP);
+      const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + C::PB0 +
+                          (uint32_t)(pb * KP + ((KP >= 16) ? half * KH : 0));
 #pragma unroll
-      for (int cc = 0; cc < KP; cc += 8) {
+      for (int cc = 0; cc < KH; cc += 8) {
         uint32_t x[8];
         tmem_ld8(tb + cc, x);
 #pragma unroll
@@ -376,7 +404,7 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     if (lane == 0) mbar_arrive(&hd.pempty[pb]);
     pph[pb] ^= 1;
     pb ^= 1;
-    if (epi) tile_epilogue<DT, KP>(e, tp, p, Hs, Gs, scratch, et, row);
+    if (epi) tile_epilogue<DT, KP>(e, tp, p, Hs, Gs, scratch, et, row, half);
   }
 }
 
@@ -394,7 +422,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3;
   const int row = q * 32 + lane;
-  const int ft = (warp - 6) * 32 + lane;
+  const int ft = (warp - 10) * 32 + lane;
   const uint32_t lane_off = (uint32_t)(q * 32) << 16;
   const int64_t c0 = L0 * C::SPU, c1 = L1 * C::SPU;
   float p[KP];
@@ -457,7 +485,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       }
     }
     if (a.fused) {
-      if (!warp_wait(&hd.pempty[pb], pph[pb] ^ 1, abort_flag)) {
+      if (!warp_wait_idle(&hd.pempty[pb], pph[pb] ^ 1, abort_flag)) {
         fail(7);
         return;
       }
@@ -490,13 +518,27 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       return;
     }
     fence_after();
-    const uint32_t tb = tmem_base + lane_off + C::ACC0 + (uint32_t)(acc * C::N);
+    const uint32_t tb = tmem_base + lane_off + C::ACC0 + (uint32_t)acc * C::ACCW;
 #pragma unroll
     for (int cc = 0; cc < KP; cc += 8) {
       uint32_t x[16];
       tmem_ld_pair(tb + cc, tb + KP + cc, x);
+      float v[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) p[cc + j] += __uint_as_float(x[j]) + __uint_as_float(x[8 + j]);
+      for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(x[j]) + __uint_as_float(x[8 + j]);
+      if constexpr (C::NL == KP) {  // S_lo H_hi
+        uint32_t y[8];
+        tmem_ld8(tb + C::N + cc, y);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] += __uint_as_float(y[j]);
+      } else if constexpr (C::NL == C::N) {  // S_lo [H_hi | H_lo]
+        uint32_t y[16];
+        tmem_ld_pair(tb + C::N + cc, tb + C::N + KP + cc, y);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] += __uint_as_float(y[j]) + __uint_as_float(y[8 + j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) p[cc + j] += v[j];
     }
     fence_before();
     __syncwarp();
@@ -513,9 +555,9 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
   if constexpr (C::F32) {
     int stage = 0;
     uint32_t phase = 0;
-    uint32_t eph[2] = {0u, 0u};
+    uint32_t eph[4] = {0u, 0u, 0u, 0u};
     for (int64_t c = c0; c < c1 && ok; ++c) {
-      const int ab = (int)((c - c0) & 1);
+      const int ab = (int)((c - c0) % C::NABUF);
       if (!warp_wait(&full[stage], phase, abort_flag) ||
           !warp_wait(&aempty[ab], eph[ab] ^ 1, abort_flag)) {
         fail(15);
@@ -526,21 +568,22 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
 #pragma unroll
       for (int at = 0; at < C::APS; ++at) {
         const uint8_t *rowp = sa + at * kAtomBytes + row * 128;
-        uint32_t hi[32], lo[32];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float4 v = *reinterpret_cast<const float4 *>(rowp + ((j ^ (row & 7)) << 4));
-          const float x[4] = {v.x, v.y, v.z, v.w};
+        for (int hh = 0; hh < 2; ++hh) {  // 16 columns at a time
+          uint32_t lo[16];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float h = tf32_trunc(x[u]);
-            hi[4 * j + u] = __float_as_uint(h);
-            lo[4 * j + u] = __float_as_uint(tf32_round(x[u] - h));
+          for (int j = 0; j < 4; ++j) {
+            const int ch = 4 * hh + j;  // 16-byte chunk of the 128-byte row
+            const float4 v = *reinterpret_cast<const float4 *>(rowp + ((ch ^ (row & 7)) << 4));
+            const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              lo[4 * j + u] = __float_as_uint(tf32_round(x[u] - tf32_trunc(x[u])));
           }
+          tmem_st16(tmem_base + lane_off + (uint32_t)ab * C::ABUF + (uint32_t)at * 32u +
+                        (uint32_t)hh * 16u,
+                    lo);
         }
-        const uint32_t base = tmem_base + lane_off + (uint32_t)ab * C::ABUF + (uint32_t)at * 32u;
-        tmem_st32(base, hi);
-        tmem_st32(base + 32u * C::APS, lo);
       }
       tmem_wait_st();
       fence_before();
@@ -577,8 +620,8 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * C::STAGE);
   uint64_t *empty = full + STAGES;
   uint64_t *afull = empty + STAGES;
-  uint64_t *aempty = afull + 2;
-  uint64_t *tfull = aempty + 2;
+  uint64_t *aempty = afull + 4;
+  uint64_t *tfull = aempty + 4;
   uint64_t *tempty = tfull + 2;
   uint64_t *pfull = tempty + 2;
   uint64_t *pempty = pfull + 2;
@@ -600,13 +643,15 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], F32 ? 5 : 1);  // (4 converter warps +) the MMA commit
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
       mbar_init(&afull[i], 4);
       mbar_init(&aempty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], 4);
       mbar_init(&pfull[i], 4);
-      mbar_init(&pempty[i], 4);
+      mbar_init(&pempty[i], 8);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -663,7 +708,7 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
       uint32_t phase = 0;
       int acc = 0;
       uint32_t tph[2] = {0u, 0u};
-      uint32_t aph[2] = {0u, 0u};
+      uint32_t aph[4] = {0u, 0u, 0u, 0u};
       constexpr uint32_t idesc = F32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
       int done = 0;
       for (int64_t c = c0; c < c1; ++c) {
@@ -675,14 +720,13 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
         (void)ci;
         const bool seg_start = (c % C::FOLD) == 0;
         const bool seg_end = (c % C::FOLD) == C::FOLD - 1;
-        const int ab = (int)((c - c0) & 1);
+        const int ab = (int)((c - c0) % C::NABUF);
         if (seg_start && !mbar_wait(&tempty[acc], tph[acc] ^ 1, abort_flag)) {
           set_err(a.err, 2);
           *abort_flag = 1;
           break;
         }
-        if ((F32 && !mbar_wait(&afull[ab], aph[ab], abort_flag)) ||
-            !mbar_wait(&full[stage], phase, abort_flag)) {
+        if (!mbar_wait(&full[stage], phase, abort_flag)) {
           set_err(a.err, 3);
           *abort_flag = 1;
           break;
@@ -690,22 +734,43 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
         fence_after();
         const uint32_t sa = smem_u32(smem + stage * C::STAGE);
         const uint32_t sb = sa + C::A_BYTES;
-        const uint32_t d = tmem_base + C::ACC0 + (uint32_t)(acc * N);
+        const uint32_t d = tmem_base + C::ACC0 + (uint32_t)acc * C::ACCW;
+        if constexpr (F32) {
+          // S_hi [H_hi | H_lo] straight from the staged tile, then, once the
+          // converters have stored S_lo, S_lo H_hi from TMEM (S_lo [H_hi |
+          // H_lo] when kp = 8, the narrowest MMA being N = 16)
+          constexpr uint32_t idesc_lo = idesc_tf32(128, KP >= 16 ? KP : N);
 #pragma unroll
-        for (int j = 0; j < C::KSL; ++j) {
-          const uint32_t within = (uint32_t)(j & 3) * 32u;
-          const uint64_t bd = sdesc(sb + (uint32_t)(j >> 2) * C::B_ATOM + within);
-          const uint32_t first = (seg_start && j == 0) ? 0u : 1u;
-          if constexpr (F32) {
-            // S_hi [H_hi | H_lo] and S_lo H_hi (S_lo [H_hi | H_lo] when kp = 8,
-            // the narrowest MMA being N = 16)
-            constexpr uint32_t idesc_lo = idesc_tf32(128, KP >= 16 ? KP : N);
-            const uint32_t ahi = tmem_base + (uint32_t)ab * C::ABUF + (uint32_t)j * 8u;
-            mma_tf32_ta(d, ahi, bd, idesc, first);
-            mma_tf32_ta(d, ahi + 32u * C::APS, bd, idesc_lo, 1u);
-          } else {
+          for (int j = 0; j < C::KSL; ++j) {
+            const uint32_t within = (uint32_t)(j & 3) * 32u;
+            const uint64_t bd = sdesc(sb + (uint32_t)(j >> 2) * C::B_ATOM + within);
             const uint64_t ad = sdesc(sa + (uint32_t)(j >> 2) * kAtomBytes + within);
-            mma_bf16(d, ad, bd, idesc, first);
+            mma_tf32_ss(d, ad, bd, idesc, (seg_start && j == 0) ? 0u : 1u);
+          }
+          if (!mbar_wait(&afull[ab], aph[ab], abort_flag)) {
+            set_err(a.err, 3);
+            *abort_flag = 1;
+            break;
+          }
+          fence_after();
+#pragma unroll
+          for (int j = 0; j < C::KSL; ++j) {
+            const uint32_t within = (uint32_t)(j & 3) * 32u;
+            const uint64_t bd = sdesc(sb + (uint32_t)(j >> 2) * C::B_ATOM + within);
+            const uint32_t alo = tmem_base + (uint32_t)ab * C::ABUF + (uint32_t)j * 8u;
+            if constexpr (C::NL > 0) {
+              mma_tf32_ta(d + N, alo, bd, idesc_lo, (seg_start && j == 0) ? 0u : 1u);
+            } else {
+              mma_tf32_ta(d + (KP >= 16 ? KP : 0), alo, bd, idesc_lo, 1u);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < C::KSL; ++j) {
+            const uint32_t within = (uint32_t)(j & 3) * 32u;
+            const uint64_t bd = sdesc(sb + (uint32_t)(j >> 2) * C::B_ATOM + within);
+            const uint64_t ad = sdesc(sa + (uint32_t)(j >> 2) * kAtomBytes + within);
+            mma_bf16(d, ad, bd, idesc, (seg_start && j == 0) ? 0u : 1u);
           }
         }
         mma_commit(&empty[stage]);
@@ -728,7 +793,7 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
       mma_commit(drain);
       if (!mbar_wait(drain, 0, abort_flag, 100000000ull) && !*abort_flag) set_err(a.err, 4);
     }
-  } else if (warp >= 6) {
+  } else if (warp >= 10) {
     const Hand hd{pfull, pempty, pflag};
     folder_role<DT, KP>(a, tmem_base, smem, full, empty, afull, aempty, tfull, tempty, hd, sflag,
                         abort_flag, L0, L1, b);

@@ -43,6 +43,29 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait that lets the hardware suspend the thread for up to ns
+// nanoseconds (it resumes early when the phase completes)
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for warps that idle for long stretches (suspends between
+// polls instead of spinning, leaving issue slots to the streaming warps)
+__device__ __forceinline__ bool mbar_wait_idle(uint64_t *bar, uint32_t parity,
+                                               volatile int *abort_flag) {
+  const uint64_t t0 = gtimer();
+  while (true) {
+    if (mbar_try_sleep(bar, parity, 20000u)) return true;
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > kWaitNs) return false;
+  }
+}
 // bounded wait; false on timeout or when another role has aborted
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                           uint64_t limit_ns = kWaitNs) {
@@ -130,6 +153,14 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
+// kind::tf32 MMA with both operands in shared memory
+__device__ __forceinline__ void mma_tf32_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
 // kind::tf32 MMA with the A operand in tensor memory
 __device__ __forceinline__ void mma_tf32_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc,
                                             uint32_t accumulate) {
@@ -150,6 +181,16 @@ __device__ __forceinline__ void tmem_st32(uint32_t ta, const uint32_t (&v)[32]) 
       "r"(v[29]), "r"(v[30]), "r"(v[31])
       : "memory");
 }
+// 16 consecutive columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16};" ::"r"(ta),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15])
+      : "memory");
+}
 __device__ __forceinline__ void tmem_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -159,14 +200,20 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
   if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
+__device__ __forceinline__ bool warp_wait_idle(uint64_t *bar, uint32_t parity,
+                                               volatile int *abort_flag) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait_idle(bar, parity, abort_flag) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
 
 
 __device__ __forceinline__ void set_err(int *err, int code) {
   if (err) atomicCAS(err, 0, code);
 }
-// named barriers: 1 among the 128 epilogue threads (warps 2-5), 2 among
-// the 128 folder threads (warps 6-9)
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// named barriers: 1 among the 256 epilogue threads (warps 2-9), 2 among
+// the 128 folder threads (warps 10-13)
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void fold_bar() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
 // 8 consecutive columns of this thread's TMEM lane
 __device__ __forceinline__ void tmem_st8(uint32_t ta, const float (&v)[8]) {
