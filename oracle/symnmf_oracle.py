@@ -431,6 +431,56 @@ class Solver:
 
 
 # --------------------------------------------------------------------------
+# FP8 E4M3 storage of S (OCP 8-bit floating point, E4M3: bias 7, 3 mantissa
+# bits, largest finite 448, subnormal step 2^-9)
+# --------------------------------------------------------------------------
+E4M3_MAX = 448.0
+
+
+def e4m3_round(x):
+    """Round |x| <= 448 to the nearest E4M3 value, ties to even mantissa."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    m, E = np.frexp(a)                      # a = m 2^E, m in [0.5, 1)
+    e = np.maximum(E - 1, -6)               # binade exponent, subnormals share 2^-6
+    step = np.ldexp(1.0, e - 3)             # 3 mantissa bits
+    q = np.round(a / step) * step           # numpy rounds half to even
+    q = np.minimum(q, E4M3_MAX)
+    return np.where(a == 0, 0.0, np.sign(x) * q)
+
+
+def tile_scale(amax):
+    """Power-of-two scale 2^ceil(log2(amax / 448)) of a tile (1 for amax = 0)."""
+    if amax <= 0:
+        return 1.0
+    m, E = math.frexp(amax / E4M3_MAX)
+    e = E - 1 if m == 0.5 else E
+    return math.ldexp(1.0, e)
+
+
+def quantize_fp8(S, tile=128):
+    """Per-tile power-of-two scaled E4M3 storage: returns (q, scales) with
+    S ~ scales[i // tile, j // tile] * q[i, j]."""
+    S = np.asarray(S, dtype=np.float64)
+    n = S.shape[0]
+    nt = -(-n // tile)
+    q = np.zeros_like(S)
+    scales = np.ones((nt, nt))
+    for a in range(nt):
+        for b in range(nt):
+            blk = S[a * tile:(a + 1) * tile, b * tile:(b + 1) * tile]
+            sc = tile_scale(float(np.max(np.abs(blk))) if blk.size else 0.0)
+            scales[a, b] = sc
+            q[a * tile:(a + 1) * tile, b * tile:(b + 1) * tile] = e4m3_round(blk / sc)
+    return q, scales
+
+
+def dequantize_fp8(q, scales, tile=128):
+    n = q.shape[0]
+    return q * np.kron(scales, np.ones((tile, tile)))[:n, :n]
+
+
+# --------------------------------------------------------------------------
 # comparison helpers: column matching and error metrics
 # --------------------------------------------------------------------------
 

@@ -437,3 +437,50 @@ def test_lower_median():
     assert O.lower_median([4.0, 1.0, 3.0, 2.0]) == 2.0
     x = np.random.default_rng(0).random(1001)
     assert O.lower_median(x) == float(np.median(x))
+
+
+# ------------------------------------------------------------ FP8 storage
+def test_e4m3_round_matches_torch_float8():
+    """The E4M3 rounding against torch's float8_e4m3fn conversion (a library
+    routine) on values spread over every binade and the subnormals."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(0, 448, 20000), 2.0 ** rng.uniform(-12, 8.8, 20000),
+                        np.arange(0, 449, 0.0625)])
+    x = x[x <= 448.0]
+    ours = O.e4m3_round(x)
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.float8_e4m3fn).double().numpy()
+    x32 = torch.tensor(x, dtype=torch.float32).double().numpy()
+    ours32 = O.e4m3_round(x32)
+    assert np.array_equal(ours32, ref)
+
+
+def test_e4m3_grid_facts():
+    """Format facts: 448 is the largest value, 2^-9 the smallest subnormal,
+    ties go to the even mantissa."""
+    assert O.e4m3_round(448.0) == 448.0
+    assert O.e4m3_round(2.0 ** -9) == 2.0 ** -9
+    assert O.e4m3_round(2.0 ** -10) == 0.0          # tie between 0 and 2^-9 -> even (0)
+    assert O.e4m3_round(1.0625) == 1.0              # tie -> even mantissa
+    assert O.e4m3_round(1.1875) == 1.25
+    grid = np.concatenate([[0.0], 2.0 ** np.linspace(-10, np.log2(448.0), 400001)])
+    assert len(np.unique(O.e4m3_round(grid))) == 127   # 2^7 codes minus NaN, incl. 0
+
+
+def test_tile_scale_power_of_two_bound():
+    for amax in [1e-7, 0.3, 1.0, 448.0 / 1024, 448.0 / 1024 * 1.0000001, 7.0]:
+        sc = O.tile_scale(amax)
+        assert math.log2(sc) == round(math.log2(sc))
+        assert amax / sc <= 448.0 and amax / sc > 224.0
+    assert O.tile_scale(0.0) == 1.0
+
+
+def test_quantize_dequantize_error_bound():
+    """Relative error of each quantised entry is at most 2^-4 (3 mantissa
+    bits, round to nearest) in the normal range of its tile."""
+    inst = gen.tpdm_groups(n=300, groups=6, T=1200, q=0.05, seed=4)
+    q, sc = O.quantize_fp8(inst.S)
+    D = O.dequantize_fp8(q, sc)
+    big = inst.S > 1e-2
+    assert np.all(np.abs(D[big] - inst.S[big]) <= 2.0 ** -4 * inst.S[big])
+    assert np.all(np.abs(q) <= 448.0)
