@@ -155,6 +155,27 @@ int symnmf_set_stream(symnmf_t h, void *stream);
  * ld_scales) with S_ij = scales[i/128][j/128] * q_ij.  Borrowed like S.
  * Recomputes ||S||^2 from the dequantised values. */
 int symnmf_set_tile_scales(symnmf_t h, const float *scales, int64_t ld_scales);
+/* FP8 E4M3 storage of a matrix (all of S, or a band of its rows) with one
+ * power-of-two scale per 128 x 128 tile.  Storage format of this library
+ * (the paper runs FP32; Sec. 2.1 only needs S H and ||S||_F^2 from S).
+ * For each tile: scale = the smallest power of two with
+ * max|tile| / scale <= 448 (1 for an all-zero tile) and
+ * q_ij = e4m3(S_ij / scale), rounded to nearest even (|S_ij| / scale <= 448,
+ * so nothing saturates; S_ij / scale is exact).  Inputs (device): src,
+ * rows x cols values of src_dtype (SYMNMF_F32 or SYMNMF_BF16) with row
+ * pitch ld_src elements.  Outputs (device, caller-owned): q, rows x cols
+ * bytes with row pitch ldq; scales, ceil(rows/128) x ceil(cols/128) FP32
+ * with row pitch ld_scales; tile_sumsq (may be NULL), the FP64 sum of
+ * squares of each unquantised tile in the layout of scales (for
+ * symnmf_set_norm).  Tiles start at the band's first row and column, so a
+ * band of a larger S must start at a multiple of 128 rows.  Asynchronous on
+ * stream (cudaStream_t as void*, NULL = legacy default stream).  INVALID for
+ * null q/src/scales, rows or cols < 1, a pitch below its width or another
+ * src_dtype; UNSUPPORTED for more than 65535 row tiles in one call; CUDA
+ * for a launch failure. */
+int symnmf_quantize_fp8(const void *src, int32_t src_dtype, int64_t rows, int64_t cols,
+                        int64_t ld_src, uint8_t *q, int64_t ldq, float *scales, int64_t ld_scales,
+                        double *tile_sumsq, void *stream);
 /* Override / read ||S||_F^2 used by the objective (e.g. the norm of the
  * unquantised matrix when S is stored in BF16 or FP8). */
 int symnmf_set_norm(symnmf_t h, double normS2);

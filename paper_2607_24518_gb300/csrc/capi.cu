@@ -47,7 +47,7 @@ struct symnmf_ctx {
   // owned device memory
   float *H[2] = {nullptr, nullptr};
   void *Bt[2] = {nullptr, nullptr};
-  int bt_fmt = 0;          // 0: bf16 hi/lo, 1: tf32 hi/lo in float
+  int bt_fmt = 0;          // 0: bf16 hi/lo, 1: tf32 hi/lo in float, 2: e4m3 pieces
   float *gram_part[2] = {nullptr, nullptr};
   double *gram64[2] = {nullptr, nullptr};
   float *gram32[2] = {nullptr, nullptr};
@@ -708,7 +708,7 @@ int symnmf_create_ld(const void *S, int64_t n, int64_t lds, int32_t k, int32_t d
   h->ntiles = (int)((n + kTileRows - 1) / kTileRows);
   h->ldb = (int64_t)h->ntiles * kTileRows;
   h->tc_layout_ok = ((uintptr_t)S % 16 == 0) && ((lds * (int64_t)esize(dtype)) % 16 == 0);
-  h->bt_fmt = (dtype == SYMNMF_F32) ? 1 : 0;
+  h->bt_fmt = (dtype == SYMNMF_F32) ? 1 : (dtype == SYMNMF_FP8E4M3) ? 2 : 0;
   reset_ctrl(&h->ctrl);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -719,7 +719,7 @@ int symnmf_create_ld(const void *S, int64_t n, int64_t lds, int32_t k, int32_t d
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = dalloc(&h->H[i], nkp);
     if (e == cudaSuccess)
-      e = dalloc((uint8_t **)&h->Bt[i], (size_t)2 * h->kp * h->ldb * (h->bt_fmt ? 4 : 2));
+      e = dalloc((uint8_t **)&h->Bt[i], bt_bytes(h->bt_fmt, h->kp, h->ldb));
     if (e == cudaSuccess) e = dalloc(&h->gram_part[i], (size_t)h->ntiles * h->kp * h->kp);
     if (e == cudaSuccess) e = dalloc(&h->gram64[i], (size_t)h->kp * h->kp);
     if (e == cudaSuccess) e = dalloc(&h->gram32[i], (size_t)h->kp * h->kp);
@@ -796,6 +796,19 @@ int symnmf_set_tile_scales(symnmf_t h, const float *scales, int64_t ld_scales) {
   h->scales = scales;
   h->ld_scales = ld_scales;
   return compute_norm(h);
+}
+
+int symnmf_quantize_fp8(const void *src, int32_t src_dtype, int64_t rows, int64_t cols,
+                        int64_t ld_src, uint8_t *q, int64_t ldq, float *scales, int64_t ld_scales,
+                        double *tile_sumsq, void *stream) {
+  if (!src || !q || !scales || rows < 1 || cols < 1 || ld_src < cols || ldq < cols ||
+      ld_scales < (cols + kTileRows - 1) / kTileRows)
+    return SYMNMF_ERR_INVALID;
+  if (src_dtype != SYMNMF_F32 && src_dtype != SYMNMF_BF16) return SYMNMF_ERR_INVALID;
+  if ((rows + kTileRows - 1) / kTileRows > 65535) return SYMNMF_ERR_UNSUPPORTED;
+  const cudaError_t e = launch_quantize_fp8(src, src_dtype, rows, cols, ld_src, q, ldq, scales,
+                                            ld_scales, tile_sumsq, (cudaStream_t)stream);
+  return e == cudaSuccess ? SYMNMF_OK : SYMNMF_ERR_CUDA;
 }
 
 int symnmf_set_norm(symnmf_t h, double normS2) {

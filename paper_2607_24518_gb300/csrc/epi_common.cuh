@@ -3,6 +3,8 @@
 // MMA copy of H, the stream-K slot arithmetic, and fixed-order summation.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_fp16.h>
 
 #include "../../include/symnmf.h"
 #include "symnmf_internal.h"
@@ -24,6 +26,32 @@ __device__ __forceinline__ float tf32_trunc(float x) {
 // x >= 0 rounded to the nearest tf32 value (ties away from zero)
 __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// OCP E4M3 code of x, round to nearest even, saturating at +-448
+__device__ __forceinline__ uint8_t e4m3_bits(float x) {
+  return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float e4m3_val(uint8_t u) {
+  return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)u, __NV_E4M3)));
+}
+// smallest power of two d with amax / d <= 448 (1 for amax = 0 or not
+// finite).  With amax = m 2^E, m in [0.5, 1): amax / 448 = (m / 1.75)
+// 2^(E-8), so d = 2^(E-9) when m <= 0.875 and 2^(E-8) otherwise; frexpf
+// is exact, so the decision is exact.
+__device__ __forceinline__ float e4m3_tile_scale(float amax) {
+  if (!(amax > 0.f) || !isfinite(amax)) return 1.f;
+  int E;
+  const float m = frexpf(amax, &E);
+  int e = E - 9 + (m > 0.875f ? 1 : 0);
+  if (e < -100) e = -100;
+  return ldexpf(1.f, e);
+}
+// two-piece E4M3 form of h at tile factor d: h ~ d (hi + lo / 16)
+__device__ __forceinline__ void e4m3_pieces(float h, float inv_d, uint8_t &hi, uint8_t &lo) {
+  const float x = h * inv_d;
+  hi = e4m3_bits(x);
+  lo = e4m3_bits(16.f * (x - e4m3_val(hi)));
 }
 
 // CTA of a stream-K launch whose unit range [b W / G, (b+1) W / G) holds x

@@ -40,8 +40,8 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
   return sh[32];
 }
 
-// writes the bf16 hi/lo transposed copy and the Gram partial of the tile
-// held in smem Hn[128][KP+1]
+// writes the transposed MMA copy (format bt_fmt) and the Gram partial of
+// the tile held in smem Hn[128][KP+1]; every thread of the block calls it
 template <int KP>
 __device__ void tile_tail(const float (*Hn)[KP + 1], int64_t r0, void *Bt, int bt_fmt, int64_t ldb,
                           float *gram_part, int tile) {
@@ -56,6 +56,28 @@ __device__ void tile_tail(const float (*Hn)[KP + 1], int64_t r0, void *Bt, int b
       B[(int64_t)c * ldb + r0 + r] = hi;
       B[(int64_t)(KP + c) * ldb + r0 + r] = lo;
     }
+  } else if (Bt && bt_fmt == 2) {
+    // tile factor d from the tile's largest entry (H >= 0), then the pieces
+    __shared__ float wmax[32];
+    float m = 0.f;
+    for (int e = tid; e < KP * kTileRows; e += blockDim.x) m = fmaxf(m, Hn[e % kTileRows][e / kTileRows]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) wmax[tid >> 5] = m;
+    __syncthreads();
+    float amax = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) amax = fmaxf(amax, wmax[w]);
+    const float d = e4m3_tile_scale(amax), inv = 1.f / d;
+    uint8_t *B = reinterpret_cast<uint8_t *>(Bt);
+    for (int e = tid; e < KP * kTileRows; e += blockDim.x) {
+      const int c = e / kTileRows, r = e % kTileRows;
+      uint8_t hi, lo;
+      e4m3_pieces(Hn[r][c], inv, hi, lo);
+      B[(int64_t)c * ldb + r0 + r] = hi;
+      B[(int64_t)(KP + c) * ldb + r0 + r] = lo;
+    }
+    if (tid == 0) bt_deq(Bt, KP, ldb)[tile] = d;
+    __syncthreads();
   } else if (Bt) {
     float *B = reinterpret_cast<float *>(Bt);
     for (int e = tid; e < KP * kTileRows; e += blockDim.x) {

@@ -71,14 +71,18 @@ struct TcArgs {
   int *err;
   int fused;             // run the per-tile epilogue in the kernel
   int *tile_cnt;         // per-tile arrival counters (fused)
+  const float *sS;       // FP8: tile scales of S (row pitch ld_sS)
+  int64_t ld_sS;
+  const float *deq;      // FP8: tile factors d of the MMA copy of H
 };
 
 template <int DT, int KP>
 struct Cfg {
   static constexpr bool F32 = (DT == 0);
+  static constexpr bool F8 = (DT == 2);
   static constexpr int N = 2 * KP;
-  static constexpr int ATOM_COLS = F32 ? 32 : 64;       // elements per 128-byte row
-  static constexpr int APS = (KP == 64) ? 1 : 2;          // swizzle atoms per stage
+  static constexpr int ATOM_COLS = F32 ? 32 : F8 ? 128 : 64;  // elements per 128-byte row
+  static constexpr int APS = (KP == 64 || F8) ? 1 : 2;    // swizzle atoms per stage
   static constexpr int SPU = 128 / (APS * ATOM_COLS);    // stages per 128-column unit
   static constexpr int KSL = 4 * APS;                    // MMA k-slices per stage
   static constexpr uint32_t A_BYTES = APS * kAtomBytes;
@@ -173,7 +177,7 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
   epi_bar();  // both halves of each H_t row are in Hs
   // tr(H^T S H) share of the row, then g = coef ((H Gram_t) - S H) formed
   // in place of p, H Gram_t right to left (Sec. 2.1)
-  float tr = 0.f, kkt2 = 0.f, sumA = 0.f, nonfin = 0.f;
+  float tr = 0.f, kkt2 = 0.f, sumA = 0.f, nonfin = 0.f, hmax = 0.f;
 #pragma unroll
   for (int j = 0; j < KH; ++j) {
     if (cb + j < e.k) tr = fmaf(hrow[cb + j], p[j], tr);
@@ -276,7 +280,10 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
       if (e.update && works) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) hrow[cb + cc + j] = hn[j];
-        if (e.Btn) {
+        if constexpr (DT == 2) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) hmax = fmaxf(hmax, hn[j]);
+        } else if (e.Btn) {
           if (e.bt_fmt == 0) {
             uint16_t *B = reinterpret_cast<uint16_t *>(e.Btn);
 #pragma unroll
@@ -335,6 +342,11 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], o);
+  if constexpr (DT == 2) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+    if ((et & 31) == 0) scratch[32 + (et >> 5)] = (double)hmax;
+  }
   if ((et & 31) == 0)
 #pragma unroll
     for (int i = 0; i < 4; ++i) scratch[(et >> 5) * 4 + i] = v4[i];
@@ -344,6 +356,26 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
 #pragma unroll
     for (int w = 0; w < 8; ++w) sv += scratch[4 * w + et];
     e.slots[(int64_t)tp * kSlotStride + et] = sv;
+  }
+  if constexpr (DT == 2) {
+    // E4M3 pieces of the tile of H_{t+1} at the tile's power-of-two factor
+    if (e.update && e.Btn) {
+      float amax = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) amax = fmaxf(amax, (float)scratch[32 + w]);
+      const float d = e4m3_tile_scale(amax), inv = 1.f / d;
+      if (works) {
+        uint8_t *B = reinterpret_cast<uint8_t *>(e.Btn);
+#pragma unroll 4
+        for (int j = 0; j < KH; ++j) {
+          uint8_t hi, lo;
+          e4m3_pieces(hrow[cb + j], inv, hi, lo);
+          B[(int64_t)(cb + j) * e.ldb + r0 + row] = hi;
+          B[(int64_t)(KP + cb + j) * e.ldb + r0 + row] = lo;
+        }
+      }
+      if (et == 0) bt_deq(e.Btn, KP, e.ldb)[tp] = d;
+    }
   }
   epi_bar();
 }
@@ -513,6 +545,15 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
   };
   // fold accumulator chain f (stage-sized chunks [f FOLD, (f+1) FOLD))
   auto fold = [&](int64_t f) {
+    float sc = 1.f;
+    if constexpr (C::F8) {
+      // one unit per chain: its S tile scale over the H tile factor
+      const int64_t u = f;
+      const int tp = (int)(u / a.n_cols), ci = (int)(u % a.n_cols);
+      const int rt = a.row_list ? a.row_list[tp] : tp;
+      const int ct = a.col_list ? a.col_list[ci] : ci;
+      sc = a.sS[(int64_t)rt * a.ld_sS + ct] * a.deq[ct];
+    }
     if (!warp_wait(&tfull[acc], tph[acc], abort_flag)) {
       fail(5);
       return;
@@ -524,8 +565,14 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       uint32_t x[16];
       tmem_ld_pair(tb + cc, tb + KP + cc, x);
       float v[8];
+      if constexpr (C::F8) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(x[j]) + __uint_as_float(x[8 + j]);
+        for (int j = 0; j < 8; ++j)
+          v[j] = fmaf(__uint_as_float(x[8 + j]), 0.0625f, __uint_as_float(x[j])) * sc;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(x[j]) + __uint_as_float(x[8 + j]);
+      }
       if constexpr (C::NL == KP) {  // S_lo H_hi
         uint32_t y[8];
         tmem_ld8(tb + C::N + cc, y);
@@ -709,7 +756,8 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
       int acc = 0;
       uint32_t tph[2] = {0u, 0u};
       uint32_t aph[4] = {0u, 0u, 0u, 0u};
-      constexpr uint32_t idesc = F32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
+      constexpr uint32_t idesc =
+          F32 ? idesc_tf32(128, N) : C::F8 ? idesc_e4m3(128, N) : idesc_bf16(128, N);
       int done = 0;
       for (int64_t c = c0; c < c1; ++c) {
         const int64_t L = c / C::SPU;
@@ -770,7 +818,10 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
             const uint32_t within = (uint32_t)(j & 3) * 32u;
             const uint64_t bd = sdesc(sb + (uint32_t)(j >> 2) * C::B_ATOM + within);
             const uint64_t ad = sdesc(sa + (uint32_t)(j >> 2) * kAtomBytes + within);
-            mma_bf16(d, ad, bd, idesc, (seg_start && j == 0) ? 0u : 1u);
+            if constexpr (C::F8)
+              mma_e4m3(d, ad, bd, idesc, (seg_start && j == 0) ? 0u : 1u);
+            else
+              mma_bf16(d, ad, bd, idesc, (seg_start && j == 0) ? 0u : 1u);
           }
         }
         mma_commit(&empty[stage]);
@@ -852,9 +903,10 @@ bool make_map_2d(CUtensorMap *m, const void *base, CUtensorMapDataType dt, uint6
 template <int DT, int KP>
 cudaError_t launch_cfg(const ProdArgs &p, const EpiArgs &e, cudaStream_t s, const TcArgs &ta) {
   using C = Cfg<DT, KP>;
-  const CUtensorMapDataType t =
-      C::F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const uint64_t es = C::F32 ? 4 : 2;
+  const CUtensorMapDataType t = C::F32  ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                : C::F8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const uint64_t es = C::F32 ? 4 : C::F8 ? 1 : 2;
   CUtensorMap mS, mB;
   if (!make_map_2d(&mS, p.S, t, (uint64_t)p.n, (uint64_t)p.n, (uint64_t)p.lds * es, C::ATOM_COLS,
                    128))
@@ -872,7 +924,7 @@ cudaError_t launch_cfg(const ProdArgs &p, const EpiArgs &e, cudaStream_t s, cons
 }  // namespace
 
 bool tc_supported(int dtype, int kp) {
-  return (dtype == 0 || dtype == 1) && (kp == 8 || kp == 16 || kp == 32 || kp == 64) &&
+  return (dtype == 0 || dtype == 1 || dtype == 2) && (kp == 8 || kp == 16 || kp == 32 || kp == 64) &&
          encode_fn() != nullptr;
 }
 
@@ -889,11 +941,17 @@ cudaError_t launch_step_tc(const ProdArgs &a, const EpiArgs *epi, int *tile_cnt,
   ta.err = err;
   ta.fused = (epi != nullptr) ? 1 : 0;
   ta.tile_cnt = tile_cnt;
+  ta.sS = a.scales;
+  ta.ld_sS = a.ld_scales;
   *G_out = ta.G;
   EpiArgs e{};
   if (epi) e = *epi;
-  const int want_fmt = (a.dtype == 0) ? 1 : 0;
+  const int want_fmt = (a.dtype == 0) ? 1 : (a.dtype == 2) ? 2 : 0;
   if (a.bt_fmt != want_fmt) return cudaErrorInvalidValue;
+  if (a.dtype == 2) {
+    if (!a.scales) return cudaErrorInvalidValue;
+    ta.deq = bt_deq(const_cast<void *>(a.Bt), a.kp, a.ldb);
+  }
 #define SYMNMF_TC_CASE(DTV)                           \
   switch (a.kp) {                                     \
     case 8: return launch_cfg<DTV, 8>(a, e, s, ta);   \
@@ -906,6 +964,8 @@ cudaError_t launch_step_tc(const ProdArgs &a, const EpiArgs *epi, int *tile_cnt,
     SYMNMF_TC_CASE(0)
   } else if (a.dtype == 1) {
     SYMNMF_TC_CASE(1)
+  } else if (a.dtype == 2) {
+    SYMNMF_TC_CASE(2)
   }
 #undef SYMNMF_TC_CASE
   return cudaErrorInvalidValue;

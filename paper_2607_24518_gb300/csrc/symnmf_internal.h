@@ -11,6 +11,10 @@
 //       0: bfloat16, hi = bf16(H), lo = bf16(H - hi)      (BF16 / FP8 S)
 //       1: float holding tf32 values, hi = H with the 13 low mantissa bits
 //          cleared, lo = (H - hi) likewise truncated       (FP32 S)
+//       2: e4m3 bytes, hi = e4m3(H / d), lo = e4m3(16 (H / d - hi)), with d a
+//          power of two per 128-row tile of H (the smallest with
+//          max|H_tile| / d <= 448); the 2 kp rows are followed by the
+//          ntiles FP32 values d                               (FP8 S)
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -18,6 +22,17 @@
 namespace symnmf {
 
 constexpr int kTileRows = 128;
+
+// bytes of one MMA copy of H in format fmt, and the tile factors d of format 2
+inline size_t bt_bytes(int fmt, int kp, int64_t ldb) {
+  const size_t es = fmt == 1 ? 4 : fmt == 2 ? 1 : 2;
+  size_t b = (size_t)2 * kp * ldb * es;
+  if (fmt == 2) b += (size_t)(ldb / kTileRows) * sizeof(float);
+  return b;
+}
+__host__ __device__ inline float *bt_deq(void *Bt, int kp, int64_t ldb) {
+  return reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(Bt) + (size_t)2 * kp * ldb);
+}
 
 constexpr int kRing = 1024;  // device record ring (iterations)
 
@@ -147,6 +162,10 @@ cudaError_t launch_median_g2(const float *g, int64_t n, int k, int kp, unsigned 
 // Piecewise reset: A = c * max(g^2, med); per-tile sum(A) into slots[.][2]
 cudaError_t launch_reset(float *A, const float *g, const float *med, float c, int64_t n, int k,
                          int kp, double *slots, cudaStream_t s);
+// per-tile power-of-two scaled E4M3 codes of a rows x cols FP32 / BF16 matrix
+cudaError_t launch_quantize_fp8(const void *src, int src_dtype, int64_t rows, int64_t cols,
+                                int64_t ld_src, uint8_t *q, int64_t ldq, float *scales,
+                                int64_t ld_scales, double *tile_sumsq, cudaStream_t s);
 cudaError_t launch_sum_slot(const double *slots, int ntiles, int which, double *out,
                             cudaStream_t s);
 

@@ -72,6 +72,7 @@ def _load():
         "symnmf_set_stream": [vp, vp],
         "symnmf_set_tile_scales": [vp, vp, i64],
         "symnmf_set_norm": [vp, dbl],
+        "symnmf_quantize_fp8": [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, vp],
         "symnmf_get_norm": [vp, P(dbl)],
         "symnmf_set_impl": [vp, i32],
         "symnmf_get_impl": [vp, P(i32)],
@@ -113,7 +114,7 @@ def _load():
 LIB = _load()
 DECLARED = [
     "symnmf_create", "symnmf_create_ld", "symnmf_destroy", "symnmf_set_stream",
-    "symnmf_set_tile_scales", "symnmf_set_norm", "symnmf_get_norm", "symnmf_set_impl",
+    "symnmf_set_tile_scales", "symnmf_quantize_fp8", "symnmf_set_norm", "symnmf_get_norm", "symnmf_set_impl",
     "symnmf_get_impl", "symnmf_set_H", "symnmf_get_H", "symnmf_get_buffer", "symnmf_set_buffer",
     "symnmf_get_ctrl", "symnmf_set_ctrl", "symnmf_grad", "symnmf_objective",
     "symnmf_hparams_default", "symnmf_step", "symnmf_batch_step", "symnmf_get_trace",
@@ -171,6 +172,14 @@ def symnmf_set_stream(h, stream):
 
 def symnmf_set_tile_scales(h, scales, ld_scales):
     return _check(LIB.symnmf_set_tile_scales(h, _ptr(scales), ld_scales), h)
+
+
+def symnmf_quantize_fp8(src, src_dtype, rows, cols, ld_src, q, ldq, scales, ld_scales,
+                        tile_sumsq=None, stream=None):
+    """Per-tile power-of-two scaled E4M3 codes of src (device tensors)."""
+    s = getattr(stream, "cuda_stream", stream)
+    return _check(LIB.symnmf_quantize_fp8(_ptr(src), src_dtype, rows, cols, ld_src, _ptr(q), ldq,
+                                          _ptr(scales), ld_scales, _ptr(tile_sumsq), s))
 
 
 def symnmf_set_norm(h, normS2):
