@@ -244,6 +244,51 @@ int symnmf_state_bytes(symnmf_t h, size_t *bytes);
 int symnmf_get_state(symnmf_t h, void *buf, size_t bytes);
 int symnmf_set_state(symnmf_t h, const void *buf, size_t bytes);
 
+/* ------------------------------------------- objective without allocation */
+
+/* Size of the fixed device scratch of symnmf_objective_noalloc (8 MiB). */
+#define SYMNMF_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* f (device, one double) = normS2 - 2 tr(H^T S H) + ||H^T H||_F^2 (Eq. 2)
+ * for a caller's S and H, with no handle and no device allocation.  The
+ * paper has no counterpart; this library adds it for callers that cannot
+ * allocate at the moment they need an objective: a monitor thread that
+ * must not stall a running solve (cudaMalloc and cudaFree can synchronise
+ * the device), a process whose device memory is fully reserved by another
+ * allocator, or an application that promised its host a fixed device
+ * footprint.  Its scratch is one array of SYMNMF_NOALLOC_SCRATCH_BYTES in
+ * device memory, created with the library's module on each device, so a
+ * call only launches kernels (three).
+ * Arguments: S (device, n x n, row pitch lds >= n elements, storage dtype;
+ * FP8 also takes the tile scales of symnmf_set_tile_scales, else scales
+ * may be NULL), H (device, FP32, n x k with row pitch k, 1 <= k <= 64),
+ * normS2 = ||S||_F^2 (for example from symnmf_get_norm), f (device, one
+ * double, written).  Nothing is kept after the call's kernels finish.
+ * Arithmetic: S H by FP32 FMA; tr and the Gram summed across 128-row tiles
+ * in FP64 in a fixed order, so the same inputs give the same bits.
+ * Limit: the call needs ceil(n/128) * (64 + 4 kp^2) bytes of scratch (kp =
+ * k rounded up to 8, 16, 32 or 64; plus under 256 bytes of alignment), at
+ * most SYMNMF_NOALLOC_SCRATCH_BYTES: n <= 3,355,392 for kp = 8, 986,880 for
+ * kp = 16, 258,048 for kp = 32, 65,280 for kp = 64.  A larger call returns
+ * SYMNMF_ERR_UNSUPPORTED and launches nothing.
+ * Zero state: no part of the scratch has to start at zero; every slot the
+ * last kernel reads is written earlier in the same call.
+ * Set-up: the first call on each device looks up that device's scratch
+ * address (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture begins.
+ * Concurrency: all calls on one device share the one scratch, so calls
+ * whose kernels can overlap in time (different streams, or host threads
+ * without an order between them) race and give wrong values; order them,
+ * for example on one stream.  Asynchronous on stream (cudaStream_t as
+ * void*, NULL = legacy default stream).
+ * Errors: INVALID for null S/H/f, n < 1, lds < n, k outside 1..64, an
+ * unknown dtype, or FP8 without scales or with ld_scales < ceil(n/128);
+ * UNSUPPORTED for the scratch limit above; CUDA for a failed launch or
+ * look-up. */
+int symnmf_objective_noalloc(const void *S, int64_t n, int64_t lds, int32_t dtype,
+                             const float *scales, int64_t ld_scales, const float *H, int32_t k,
+                             double normS2, double *f, void *stream);
+
 const char *symnmf_last_error(symnmf_t h);
 const char *symnmf_status_string(int32_t status);
 

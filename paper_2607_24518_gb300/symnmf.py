@@ -72,6 +72,7 @@ def _load():
         "symnmf_set_stream": [vp, vp],
         "symnmf_set_tile_scales": [vp, vp, i64],
         "symnmf_set_norm": [vp, dbl],
+        "symnmf_objective_noalloc": [vp, i64, i64, i32, vp, i64, vp, i32, dbl, vp, vp],
         "symnmf_quantize_fp8": [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, vp],
         "symnmf_get_norm": [vp, P(dbl)],
         "symnmf_set_impl": [vp, i32],
@@ -121,8 +122,17 @@ DECLARED = [
     "symnmf_set_profiling", "symnmf_get_profile",
     "symnmf_state_bytes", "symnmf_get_state", "symnmf_set_state", "symnmf_last_error",
     "symnmf_status_string", "symnmf_splitmix64", "symnmf_sample_blocks",
-    "symnmf_controller_check",
+    "symnmf_controller_check", "symnmf_objective_noalloc",
 ]
+
+NOALLOC_SCRATCH_BYTES = 8 << 20
+
+
+def noalloc_scratch_need(n, k):
+    """Scratch bytes symnmf_objective_noalloc needs for n rows and rank k."""
+    kp = 8 if k <= 8 else 16 if k <= 16 else 32 if k <= 32 else 64
+    nt = -(-n // 128)
+    return (nt * 64 + 255) // 256 * 256 + nt * kp * kp * 4
 
 
 def _ptr(x):
@@ -180,6 +190,17 @@ def symnmf_quantize_fp8(src, src_dtype, rows, cols, ld_src, q, ldq, scales, ld_s
     s = getattr(stream, "cuda_stream", stream)
     return _check(LIB.symnmf_quantize_fp8(_ptr(src), src_dtype, rows, cols, ld_src, _ptr(q), ldq,
                                           _ptr(scales), ld_scales, _ptr(tile_sumsq), s))
+
+
+def symnmf_objective_noalloc(S, n, lds, dtype, scales, ld_scales, H, k, normS2, f, stream=None):
+    """f (device double) = normS2 - 2 tr(H^T S H) + ||H^T H||^2 with no allocation."""
+    s = getattr(stream, "cuda_stream", stream)
+    st = LIB.symnmf_objective_noalloc(_ptr(S), n, lds, dtype, _ptr(scales), ld_scales, _ptr(H), k,
+                                      float(normS2), _ptr(f), s)
+    if st == ERR_UNSUPPORTED:
+        raise SymNMFError(st, "n=%d, k=%d needs %d bytes of scratch, above the fixed %d"
+                          % (n, k, noalloc_scratch_need(n, k), NOALLOC_SCRATCH_BYTES))
+    return _check(st)
 
 
 def symnmf_set_norm(h, normS2):
