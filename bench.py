@@ -18,6 +18,7 @@ time.  ``--impl reference`` times the FP64 CPU oracle on the host cores.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -38,9 +39,49 @@ WORKLOADS = {
     "tpdm_n20000_k32_fp32_adagrad": ("tpdm", 20000, 32, "f32", 0, 2.0),
     "tpdm_n20000_k32_fp32_rmsprop": ("tpdm", 20000, 32, "f32", 1, 0.05),
     "tpdm_n20000_k32_bf16_adagrad": ("tpdm", 20000, 32, "bf16", 0, 2.0),
+    "tpdm_n20000_k32_fp8_adagrad": ("tpdm", 20000, 32, "fp8", 0, 2.0),
     "corr_n100000_k32_fp32_adagrad": ("corr", 100000, 32, "f32", 0, 2.0),
     "corr_n100000_k32_bf16_adagrad": ("corr", 100000, 32, "bf16", 0, 2.0),
 }
+ESIZE = {"f32": 4, "bf16": 2, "fp8": 1}
+# bytes per entry of the MMA copy of H (hi + lo pieces) for each storage type
+BT_ESIZE = {"f32": 4, "bf16": 2, "fp8": 1}
+KERNEL_SOURCES = ("k_prod_tc.cu", "tc_ptx.cuh", "epi_common.cuh", "symnmf_internal.h")
+
+
+def alg_bytes_full_step(n, k, dt, method):
+    """Algorithmic DRAM bytes of one full fused step: S once, plus the n x k
+    state: H_t and G read, H_{t+1}, G and g written (RMSprop adds m read and
+    written), the hi/lo MMA copy of H read once and written once; FP8 adds
+    the tile scales."""
+    nt = -(-n // 128)
+    b = n * n * ESIZE[dt]
+    b += 20 * n * k + (8 * n * k if method == 1 else 0)
+    b += 2 * (2 * k * n * BT_ESIZE[dt])
+    if dt == "fp8":
+        b += 4 * nt * nt
+    return b
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2607_24518_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, or None when the kernel sources changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    cur = kernel_source_hash()
+    for line in open(p):
+        f = line.split()
+        if len(f) == 3 and not line.startswith("#") and f[0] == workload and f[1] == cur:
+            return float(f[2])
+    return None
 DEFAULT = "tpdm_n20000_k32_fp32_adagrad"
 
 
@@ -56,7 +97,7 @@ def make_input(name, device):
     import torch
     import gen
     kind, n, k, dt, method, eta = WORKLOADS[name]
-    tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dt]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "fp8": torch.float32}[dt]
     if kind == "tpdm":
         inst = gen.tpdm_groups(n=n, groups=32, T=5000, q=0.05, seed=0, device=device,
                                dtype=tdt, materialize="torch")
@@ -152,11 +193,25 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     kind, n, k, dt, method, eta = WORKLOADS[args.workload]
     S, H0, inst = make_input(args.workload, dev)
-    dtype = L.F32 if dt == "f32" else L.BF16
+    dtype = {"f32": L.F32, "bf16": L.BF16, "fp8": L.FP8E4M3}[dt]
     H0_t = torch.tensor(H0, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    scales = None
+    if dt == "fp8":
+        # per-tile E4M3 storage made by the library's quantiser; ||S||^2 of
+        # the unquantised source from the quantiser's per-tile sums
+        nt = -(-n // 128)
+        q = torch.empty(n, n, dtype=torch.uint8, device=dev)
+        scales = torch.empty(nt, nt, dtype=torch.float32, device=dev)
+        ss = torch.empty(nt, nt, dtype=torch.float64, device=dev)
+        L.symnmf_quantize_fp8(S, L.F32, n, n, n, q, n, scales, nt, ss)
+        torch.cuda.synchronize()
+        del S
+        S = q
     h = L.symnmf_create(S, n, k, dtype)
     L.symnmf_set_stream(h, stream)
+    if scales is not None:
+        L.symnmf_set_tile_scales(h, scales, scales.shape[1])
     hp = L.symnmf_hparams_default(method, eta=eta, tau_g=1e-30)  # never stop early: fixed work
     L.symnmf_set_H(h, H0_t)
     L.symnmf_step(h, hp, args.warmup)
@@ -172,7 +227,7 @@ def run_native(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    prod_ms, prod_launches, prod_bytes = L.symnmf_get_profile(h)
+    prod_ms, prod_launches, prod_bytes, kernel_launches = L.symnmf_get_profile(h)
     L.symnmf_set_profiling(h, False)
     ck = clocks.stop() if clocks else None
     iters = int(st.iter) - args.warmup
@@ -200,6 +255,8 @@ def run_native(args, rank, world, local_rank):
         H_res = torch.empty_like(H0_t)
         he = L.symnmf_create(S_dev, n, k, dtype)
         L.symnmf_set_stream(he, stream)
+        if scales is not None:
+            L.symnmf_set_tile_scales(he, scales, scales.shape[1])
         per = 10
         reps = max(2, min(5, args.steps // per))
         for rep in range(reps + 1):
@@ -231,18 +288,18 @@ def run_native(args, rank, world, local_rank):
     if rank == 0:
         peak, src = peaks()
         per_launch_ms = prod_ms / max(1, prod_launches)
-        per_launch_bytes = prod_bytes / max(1, prod_launches)
+        # every timed iteration is a full step: one fused launch each
+        per_launch_bytes = alg_bytes_full_step(n, k, dt, method)
         achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
-        traffic = None
-        prof_json = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(prof_json):
-            tj = json.load(open(prof_json))
-            key = f"{args.workload}:{['', 'simt', 'tc'][impl]}"
-            if key in tj:
-                traffic = tj[key]
+        traffic = measured_traffic(args.workload) if impl == 2 else None
         cpu = None
         if args.cpu_baseline:
-            S64 = S.double().cpu().numpy()
+            if dt == "fp8":
+                from oracle import symnmf_oracle as O
+                S64 = O.dequantize_fp8(S.cpu().view(torch.float8_e4m3fn).double().numpy(),
+                                       scales.double().cpu().numpy())
+            else:
+                S64 = S.double().cpu().numpy()
             rate, it, el = oracle_rate(S64, H0_t.double().cpu().numpy(), method, eta,
                                        budget_s=args.cpu_budget)
             del S64
@@ -253,7 +310,8 @@ def run_native(args, rank, world, local_rank):
             "metric": METRIC, "value": total_iters / (ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / max(1, iters),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"f32": "f32", "bf16": "bf16"}[dt] + " storage, f32 accumulate, f64 reductions",
+            "dtype": {"f32": "f32", "bf16": "bf16", "fp8": "e4m3"}[dt]
+                     + " storage, f32 accumulate, f64 reductions",
             "data": "synthetic (seeded TPDM / correlation generator)",
             "config": {"workload": args.workload, "n": n, "k": k, "method": ["adagrad", "rmsprop"][method],
                        "eta": eta, "storage": dt, "l2": "S larger than L2 (no flush needed)",
@@ -261,12 +319,15 @@ def run_native(args, rank, world, local_rank):
                        "product_impl": ["", "simt", "tcgen05"][impl]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": src,
-                         "kernel": "S H product", "bytes_per_launch": per_launch_bytes,
-                         "ms_per_launch": per_launch_ms, "frac_of_8TBps_nominal": achieved / 8000.0},
+                         "kernel": "fused step (S H product + epilogue)" if impl == 2 else "S H product",
+                         "bytes_per_launch": per_launch_bytes, "s_bytes_per_launch":
+                         prod_bytes / max(1, prod_launches), "ms_per_launch": per_launch_ms,
+                         "frac_of_8TBps_nominal": achieved / 8000.0,
+                         "kernel_source": kernel_source_hash()},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": ck,
-            "gpu_launches": int(prod_launches) * 4,
+            "gpu_launches": int(kernel_launches),
             "status": L.symnmf_status_string(status),
         }
     return out
@@ -285,6 +346,8 @@ def run_reference(args, rank):
     H0_64 = torch.tensor(H0, dtype=torch.float32).double().numpy()
     del S
     from oracle import symnmf_oracle as O
+    if dt == "fp8":
+        S64 = O.dequantize_fp8(*O.quantize_fp8(S64))
     hp = O.HParams.paper(method)
     hp.eta = eta
     hp.tau_g = 1e-30

@@ -228,9 +228,13 @@ int symnmf_batch_step(symnmf_t *hs, int32_t count, const symnmf_hparams *hps, in
  * accumulation; enable == 0 stops recording. */
 int symnmf_set_profiling(symnmf_t h, int32_t enable);
 /* Synchronise the stream and return the accumulated product-kernel time in
- * milliseconds (host), the number of timed launches, and the algorithmic
- * bytes of S those launches streamed (rows x columns x element size). */
-int symnmf_get_profile(symnmf_t h, double *product_ms, int64_t *launches, double *s_bytes);
+ * milliseconds (host), the number of timed launches, the algorithmic bytes
+ * of S those launches streamed (rows x columns x element size), and the
+ * number of kernels of this library that symnmf_step / symnmf_batch_step
+ * launched while profiling was on (product, epilogue, reductions, median,
+ * reset).  Any output pointer may be NULL. */
+int symnmf_get_profile(symnmf_t h, double *product_ms, int64_t *launches, double *s_bytes,
+                       int64_t *kernel_launches);
 /* Copy up to max per-iteration records (oldest first) to out (host) and the
  * number available to *count.  The handle keeps the last 1<<20 records. */
 int symnmf_get_trace(symnmf_t h, symnmf_record *out, int64_t max, int64_t *count);

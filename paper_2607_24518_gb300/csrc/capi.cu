@@ -89,6 +89,7 @@ struct symnmf_ctx {
   std::vector<cudaEvent_t> prof_ev;   // pairs
   size_t prof_used = 0;                // events used (2 per launch)
   double prof_bytes = 0.0;
+  int64_t prof_kernels = 0;  // kernels launched by the solver loop while profiling
 };
 
 namespace {
@@ -332,6 +333,10 @@ void blocks_to_tiles(symnmf_t h, const std::vector<int64_t> &blocks, int64_t blo
     }
 }
 
+void count_kernels(symnmf_t h, int64_t n) {
+  if (h->profiling) h->prof_kernels += n;
+}
+
 int prod(symnmf_t h, const int *row_list, int n_rows, const int *col_list, int n_cols, float *out,
          PartLayout *lay, const EpiArgs *fuse = nullptr) {
   ProdArgs a{};
@@ -376,6 +381,7 @@ int prod(symnmf_t h, const int *row_list, int n_rows, const int *col_list, int n
     e = launch_prod_simt(a, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "product kernel");
+  count_kernels(h, 1);
   if (h->profiling) {
     CK(cudaEventRecord(e1, h->stream));
     const double rows = std::min<double>((double)n_rows * kTileRows, (double)h->n);
@@ -485,6 +491,7 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t) {
     } else {
       CK(launch_gram_subset(h->gram_part[cur], h->kp, dI, (int)tI.size(), dJ, (int)tJ.size(),
                             h->gramI, h->gramJ, h->stream));
+      count_kernels(h, 1);
       PartLayout l1, l2;
       if ((rc = prod(h, dI, (int)tI.size(), dJ, (int)tJ.size(), h->P, &l1))) return rc;
       if ((rc = prod(h, dJ, (int)tJ.size(), dI, (int)tI.size(), h->Q, &l2))) return rc;
@@ -509,6 +516,7 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t) {
   if (!fused_done) CK(launch_epilogue(e, h->stream));
   CK(launch_reduce_iter(reduce_args(h, h->slots, h->gram_part[nxt], t, full ? 1 : 0), h->kp,
                         h->stream));
+  count_kernels(h, fused_done ? 1 : 2);
   h->cur = nxt;
   return SYMNMF_OK;
 }
@@ -555,6 +563,7 @@ int sync_records(symnmf_t h, int64_t upto, const std::vector<double> &phis) {
 
 int median_g2(symnmf_t h, double *out) {
   CK(launch_median_g2(h->g, h->n, h->k, h->kp, h->hist, h->sel, h->dmed, h->stream));
+  count_kernels(h, 7);  // selection init + 3 x (histogram, select)
   CK(cudaMemcpyAsync(h->hmed, h->dmed, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   *out = (double)h->hmed[0];
@@ -564,6 +573,7 @@ int median_g2(symnmf_t h, double *out) {
 int apply_reset(symnmf_t h, const symnmf_hparams *hp) {
   CK(launch_reset(h->A, h->g, h->dmed, (float)hp->c, h->n, h->k, h->kp, h->slots, h->stream));
   CK(launch_sum_slot(h->slots, h->ntiles, 2, h->dsum, h->stream));
+  count_kernels(h, 2);
   CK(cudaMemcpyAsync(h->hsum, h->dsum, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   h->ctrl.sumA_post = h->hsum[0];
@@ -1024,12 +1034,14 @@ int symnmf_set_profiling(symnmf_t h, int32_t enable) {
   if (enable) {
     h->prof_used = 0;
     h->prof_bytes = 0.0;
+    h->prof_kernels = 0;
   }
   h->profiling = enable != 0;
   return SYMNMF_OK;
 }
 
-int symnmf_get_profile(symnmf_t h, double *product_ms, int64_t *launches, double *s_bytes) {
+int symnmf_get_profile(symnmf_t h, double *product_ms, int64_t *launches, double *s_bytes,
+                       int64_t *kernel_launches) {
   if (!h) return SYMNMF_ERR_INVALID;
   CK(cudaStreamSynchronize(h->stream));
   double ms = 0.0;
@@ -1041,6 +1053,7 @@ int symnmf_get_profile(symnmf_t h, double *product_ms, int64_t *launches, double
   if (product_ms) *product_ms = ms;
   if (launches) *launches = (int64_t)(h->prof_used / 2);
   if (s_bytes) *s_bytes = h->prof_bytes;
+  if (kernel_launches) *kernel_launches = h->prof_kernels;
   return SYMNMF_OK;
 }
 

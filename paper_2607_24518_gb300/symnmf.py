@@ -90,7 +90,7 @@ def _load():
         "symnmf_batch_step": [P(vp), i32, P(symnmf_hparams), i32, P(symnmf_stats)],
         "symnmf_get_trace": [vp, P(symnmf_record), i64, P(i64)],
         "symnmf_set_profiling": [vp, i32],
-        "symnmf_get_profile": [vp, P(dbl), P(i64), P(dbl)],
+        "symnmf_get_profile": [vp, P(dbl), P(i64), P(dbl), P(i64)],
         "symnmf_state_bytes": [vp, P(C.c_size_t)],
         "symnmf_get_state": [vp, vp, C.c_size_t],
         "symnmf_set_state": [vp, vp, C.c_size_t],
@@ -296,9 +296,10 @@ def symnmf_set_profiling(h, enable):
 
 
 def symnmf_get_profile(h):
-    ms, n, b = C.c_double(), C.c_int64(), C.c_double()
-    _check(LIB.symnmf_get_profile(h, C.byref(ms), C.byref(n), C.byref(b)), h)
-    return ms.value, n.value, b.value
+    """(product ms, product launches, S bytes streamed, kernels launched)."""
+    ms, n, b, kl = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
+    _check(LIB.symnmf_get_profile(h, C.byref(ms), C.byref(n), C.byref(b), C.byref(kl)), h)
+    return ms.value, n.value, b.value, kl.value
 
 
 def symnmf_state_bytes(h):
