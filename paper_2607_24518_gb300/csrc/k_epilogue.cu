@@ -80,12 +80,14 @@ __device__ void tile_tail(const float (*Hn)[KP + 1], int64_t r0, void *Bt, int b
     __syncthreads();
   } else if (Bt) {
     float *B = reinterpret_cast<float *>(Bt);
+    uint16_t *B16 = bt_b16(Bt, KP, ldb);
     for (int e = tid; e < KP * kTileRows; e += blockDim.x) {
       const int c = e / kTileRows, r = e % kTileRows;
       const float v = Hn[r][c];
       const float hi = tf32_trunc(v);
       B[(int64_t)c * ldb + r0 + r] = hi;
       B[(int64_t)(KP + c) * ldb + r0 + r] = tf32_round(v - hi);
+      B16[(int64_t)c * ldb + r0 + r] = bf16_bits(v);
     }
   }
   if (gram_part) {

@@ -64,6 +64,8 @@ using namespace tc;
 struct TcArgs {
   int64_t W;             // units = n_rows_list * n_cols_list
   int G;                 // CTAs
+  int R;                 // leading row positions shared stream-K style
+  int D;                 // row positions owned whole by each CTA after those
   int n_cols;
   const int *row_list;
   const int *col_list;
@@ -80,6 +82,10 @@ template <int DT, int KP>
 struct Cfg {
   static constexpr bool F32 = (DT == 0);
   static constexpr bool F8 = (DT == 2);
+  // FP32 with kp <= 32: the S_lo H product runs as kind::f16 on a bf16
+  // S_lo (in TMEM) and a bf16 copy of H (N2 rows, zero past kp)
+  static constexpr bool SLO16 = F32 && KP <= 32;
+  static constexpr int N2 = SLO16 ? (KP < 16 ? 16 : KP) : 0;
   static constexpr int N = 2 * KP;
   static constexpr int ATOM_COLS = F32 ? 32 : F8 ? 128 : 64;  // elements per 128-byte row
   static constexpr int APS = (KP == 64 || F8) ? 1 : 2;    // swizzle atoms per stage
@@ -88,11 +94,14 @@ struct Cfg {
   static constexpr uint32_t A_BYTES = APS * kAtomBytes;
   static constexpr uint32_t B_ATOM = N * 128;
   static constexpr uint32_t B_BYTES = APS * B_ATOM;
-  static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+  static constexpr uint32_t B2_BYTES = SLO16 ? (uint32_t)N2 * 128u : 0u;
+  static constexpr uint32_t STAGE = A_BYTES + B_BYTES + B2_BYTES;
   // stages per accumulator chain: the tensor core's FP32 accumulation is
   // kept to at most 8 chained MMAs per accumulator, the rest is summed in
   // FP32 registers
   static constexpr int FOLD = F32 ? 1 : SPU;
+  // accumulator columns per part read before one wait when folding
+  static constexpr int FOLD_CW = F32 ? 8 : (KP == 64 ? 16 : 32);
   static constexpr uint32_t EPI_FLOATS = 128 * (KP + 1) + KP * KP;
   static constexpr uint32_t EPI_BYTES = EPI_FLOATS * 4 + 512;
   static constexpr uint32_t BAR_BYTES = 512;
@@ -102,16 +111,48 @@ struct Cfg {
   static constexpr int THREADS = 448;  // 14 warps: TMA, MMA, 8 epilogue, 4 folder
   // FP32: TMEM columns of one S_lo buffer, number of S_lo buffers, width
   // of the separate S_lo H accumulator (0: shared with the main one)
-  static constexpr uint32_t ABUF = F32 ? 32u * APS : 0u;
-  static constexpr int NABUF = F32 ? 2 : 1;
-  static constexpr int NL = (F32 && KP <= 32) ? (KP >= 16 ? KP : N) : 0;
+  // (SLO16: one bf16 S_lo buffer of 32 columns per ring stage, so a
+  // stage's release also frees its S_lo buffer)
+  static constexpr uint32_t ABUF = SLO16 ? 32u : F32 ? 32u * APS : 0u;
+  static constexpr int NABUF = SLO16 ? STAGES : F32 ? 2 : 1;
+  static constexpr int NL = SLO16 ? N2 : 0;
   static constexpr uint32_t ACC0 = F32 ? NABUF * ABUF : 0u;
   static constexpr uint32_t ACCW = N + NL;                // columns per accumulator buffer
   static constexpr uint32_t PB0 = ACC0 + 2 * ACCW;        // double-buffered P rows
   static constexpr uint32_t TMEM_NEED = PB0 + 2 * KP;
   static constexpr uint32_t TMEM_COLS = TMEM_NEED <= 32 ? 32 : TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
   static_assert(STAGES >= 2, "shared memory ring too small");
+  static_assert(TMEM_NEED <= 512, "tensor memory budget exceeded");
 };
+
+// The units of CTA b: first its stream-K share [b W_R / G, (b+1) W_R / G)
+// of the R shared row positions (W_R = R n_cols), then its D whole row
+// positions R + b D .. R + b D + D - 1.  Every CTA streams the same number
+// of units and, when D > 0, ends on a tile it owns alone.
+// Within an owned tile CTA b visits the columns from rot = b n_cols / G
+// onwards (wrapping), so the CTAs do not all read the same column of S and
+// the same slice of the MMA copy of H at the same moment.
+struct Segs {
+  int64_t lo[2], hi[2];
+  int rot;
+};
+__device__ __forceinline__ Segs cta_segments(const TcArgs &a, int b) {
+  const int64_t WR = (int64_t)a.R * a.n_cols;
+  Segs s;
+  s.lo[0] = (int64_t)b * WR / a.G;
+  s.hi[0] = (int64_t)(b + 1) * WR / a.G;
+  s.lo[1] = ((int64_t)a.R + (int64_t)b * a.D) * a.n_cols;
+  s.hi[1] = s.lo[1] + (int64_t)a.D * a.n_cols;
+  s.rot = (int)((int64_t)b * a.n_cols / a.G);
+  return s;
+}
+// column position visited for unit L of segment si
+__device__ __forceinline__ int unit_col(const TcArgs &a, const Segs &sg, int64_t L, int si) {
+  const int ci = (int)(L % a.n_cols);
+  if (si == 0) return ci;
+  const int r = ci + sg.rot;
+  return r >= a.n_cols ? r - a.n_cols : r;
+}
 
 // ------------------------------------------------------------------ epilogue
 // Register-block shape of the per-thread share of the kp x kp Gram partial
@@ -294,11 +335,13 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
             }
           } else {
             float *B = reinterpret_cast<float *>(e.Btn);
+            uint16_t *B16 = bt_b16(e.Btn, KP, e.ldb);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const float hi = tf32_trunc(hn[j]);
               B[(int64_t)(cb + cc + j) * e.ldb + r0 + row] = hi;
               B[(int64_t)(KP + cb + cc + j) * e.ldb + r0 + row] = tf32_round(hn[j] - hi);
+              B16[(int64_t)(cb + cc + j) * e.ldb + r0 + row] = bf16_bits(hn[j]);
             }
           }
         }
@@ -393,7 +436,7 @@ struct Hand {
 template <int DT, int KP>
 __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_base, float *Hs,
                               float *Gs, double *scratch, const Hand &hd,
-                              volatile int *abort_flag, int64_t L0, int64_t L1) {
+                              volatile int *abort_flag, const Segs &sg) {
   using C = Cfg<DT, KP>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3;
@@ -405,7 +448,8 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
   epi_bar();
   int pb = 0;
   uint32_t pph[2] = {0u, 0u};
-  for (int64_t L = L0; L < L1;) {
+  for (int si = 0; si < 2; ++si)
+  for (int64_t L = sg.lo[si], L1 = sg.hi[si]; L < L1;) {
     const int tp = (int)(L / a.n_cols);
     const int64_t tile_end = (int64_t)(tp + 1) * a.n_cols;
     L = L1 < tile_end ? L1 : tile_end;
@@ -417,10 +461,10 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
       return;
     }
     fence_after();
-    const int epi = hd.pflag[pb];
+    const int epi = hd.pflag[pb];  // 0: none, 1: P in TMEM, 2: add the partial slots
     constexpr int KH = Own<KP>::KH;
     float p[KH];
-    if (epi) {
+    if (epi == 1) {
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + C::PB0 +
                           (uint32_t)(pb * KP + ((KP >= 16) ? half * KH : 0));
 #pragma unroll
@@ -436,6 +480,40 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     if (lane == 0) mbar_arrive(&hd.pempty[pb]);
     pph[pb] ^= 1;
     pb ^= 1;
+    if (epi == 2) {
+      // shared row position: its partials in slots cta + tp, CTA order
+      const int64_t WR = (int64_t)a.R * a.n_cols;
+      const int64_t b0 = sk_cta((int64_t)tp * a.n_cols, WR, a.G);
+      const int64_t b1 = sk_cta((int64_t)tp * a.n_cols + a.n_cols - 1, WR, a.G);
+      const int cb = (KP >= 16) ? half * KH : 0;
+#pragma unroll
+      for (int j = 0; j < KH; ++j) p[j] = 0.f;
+      __threadfence();
+      if (KP >= 16 || half == 0) {
+        // GB slots' loads in flight at once, then added in CTA order
+        constexpr int GB = (KH <= 16) ? 4 : 2;
+        for (int64_t bb = b0; bb <= b1; bb += GB) {
+          float4 v[GB][KH / 4];
+#pragma unroll
+          for (int g = 0; g < GB; ++g) {
+            const float4 *src =
+                reinterpret_cast<const float4 *>(a.out + ((bb + g + tp) * 128 + row) * KP + cb);
+#pragma unroll
+            for (int c4 = 0; c4 < KH / 4; ++c4)
+              v[g][c4] = (bb + g <= b1) ? __ldcg(src + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int g = 0; g < GB; ++g)
+#pragma unroll
+            for (int c4 = 0; c4 < KH / 4; ++c4) {
+              p[4 * c4 + 0] += v[g][c4].x;
+              p[4 * c4 + 1] += v[g][c4].y;
+              p[4 * c4 + 2] += v[g][c4].z;
+              p[4 * c4 + 3] += v[g][c4].w;
+            }
+        }
+      }
+    }
     if (epi) tile_epilogue<DT, KP>(e, tp, p, Hs, Gs, scratch, et, row, half);
   }
 }
@@ -448,7 +526,7 @@ template <int DT, int KP>
 __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, uint64_t *full,
                             uint64_t *empty, uint64_t *afull, uint64_t *aempty, uint64_t *tfull,
                             uint64_t *tempty, const Hand &hd, int *sflag,
-                            volatile int *abort_flag, int64_t L0, int64_t L1, int b) {
+                            volatile int *abort_flag, const Segs &sg, int b) {
   using C = Cfg<DT, KP>;
   constexpr int STAGES = C::STAGES;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -456,7 +534,6 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
   const int row = q * 32 + lane;
   const int ft = (warp - 10) * 32 + lane;
   const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-  const int64_t c0 = L0 * C::SPU, c1 = L1 * C::SPU;
   float p[KP];
 #pragma unroll
   for (int c = 0; c < KP; ++c) p[c] = 0.f;
@@ -476,8 +553,11 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     int64_t b0 = b, b1 = b;
     int epi = 0;
     if (a.fused) {
-      b0 = sk_cta((int64_t)tp * a.n_cols, a.W, a.G);
-      b1 = sk_cta((int64_t)tp * a.n_cols + a.n_cols - 1, a.W, a.G);
+      if (tp < a.R) {  // shared row position: the CTAs holding its units
+        const int64_t WR = (int64_t)a.R * a.n_cols;
+        b0 = sk_cta((int64_t)tp * a.n_cols, WR, a.G);
+        b1 = sk_cta((int64_t)tp * a.n_cols + a.n_cols - 1, WR, a.G);
+      }
       epi = (b0 == b1);
     }
     if (!epi) {
@@ -495,10 +575,12 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
           *reinterpret_cast<volatile int *>(sflag) = last;
         }
         fold_bar();
-        epi = *reinterpret_cast<volatile int *>(sflag);
-        if (epi) {
-          // the tile's partials, added in CTA order
-          __threadfence();
+        // last to arrive: the tile's partials are added in CTA order, here
+        // for a few sharers, else by the epilogue warps while this CTA
+        // keeps streaming
+        epi = *reinterpret_cast<volatile int *>(sflag) ? 2 : 0;
+        if (epi) __threadfence();
+        if (epi && b1 - b0 < 4) {
 #pragma unroll
           for (int c = 0; c < KP; ++c) p[c] = 0.f;
           for (int64_t bb = b0; bb <= b1; ++bb) {
@@ -506,13 +588,14 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
                 reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP);
 #pragma unroll
             for (int c4 = 0; c4 < KP / 4; ++c4) {
-              const float4 v = src[c4];
+              const float4 v = __ldcg(src + c4);
               p[4 * c4 + 0] += v.x;
               p[4 * c4 + 1] += v.y;
               p[4 * c4 + 2] += v.z;
               p[4 * c4 + 3] += v.w;
             }
           }
+          epi = 1;
         }
       }
     }
@@ -522,7 +605,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
         return;
       }
       fence_after();
-      if (epi) {
+      if (epi == 1) {
         const uint32_t tb = tmem_base + lane_off + C::PB0 + (uint32_t)(pb * KP);
 #pragma unroll
         for (int cc = 0; cc < KP; cc += 8) {
@@ -544,15 +627,46 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     for (int c = 0; c < KP; ++c) p[c] = 0.f;
   };
   // fold accumulator chain f (stage-sized chunks [f FOLD, (f+1) FOLD))
-  auto fold = [&](int64_t f) {
+  // FP8: the scale of each unit (S tile scale over the H tile factor),
+  // loaded one fold ahead; (ntp, nci, nu, nsi) walk this CTA's units
+  int64_t nu = sg.hi[0] > sg.lo[0] ? sg.lo[0] : sg.lo[1];
+  int nsi = sg.hi[0] > sg.lo[0] ? 0 : 1;
+  int ntp = (int)(nu / a.n_cols), nci = (int)(nu % a.n_cols);
+  auto load_scale = [&]() -> float {
+    if (nu >= sg.hi[nsi]) return 1.f;
+    int cpos = nci;
+    if (nsi == 1) {
+      cpos += sg.rot;
+      if (cpos >= a.n_cols) cpos -= a.n_cols;
+    }
+    const int rt = a.row_list ? a.row_list[ntp] : ntp;
+    const int ct = a.col_list ? a.col_list[cpos] : cpos;
+    return a.sS[(int64_t)rt * a.ld_sS + ct] * a.deq[ct];
+  };
+  auto advance_unit = [&]() {
+    ++nu;
+    if (++nci == a.n_cols) {
+      nci = 0;
+      ++ntp;
+    }
+    if (nsi == 0 && nu >= sg.hi[0]) {
+      nsi = 1;
+      nu = sg.lo[1];
+      ntp = (int)(nu / a.n_cols);
+      nci = (int)(nu % a.n_cols);
+    }
+  };
+  float sc_next = 1.f;
+  if constexpr (C::F8) sc_next = load_scale();
+  // fold accumulator chain f (stage-sized chunks [f FOLD, (f+1) FOLD)) of
+  // segment si, which ends at unit Lhi
+  auto fold = [&](int64_t f, int64_t Lhi, int si) {
     float sc = 1.f;
     if constexpr (C::F8) {
-      // one unit per chain: its S tile scale over the H tile factor
-      const int64_t u = f;
-      const int tp = (int)(u / a.n_cols), ci = (int)(u % a.n_cols);
-      const int rt = a.row_list ? a.row_list[tp] : tp;
-      const int ct = a.col_list ? a.col_list[ci] : ci;
-      sc = a.sS[(int64_t)rt * a.ld_sS + ct] * a.deq[ct];
+      // one unit per chain, visited in this CTA's order
+      sc = sc_next;
+      advance_unit();
+      sc_next = load_scale();
     }
     if (!warp_wait(&tfull[acc], tph[acc], abort_flag)) {
       fail(5);
@@ -560,32 +674,32 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     }
     fence_after();
     const uint32_t tb = tmem_base + lane_off + C::ACC0 + (uint32_t)acc * C::ACCW;
+    // CW columns of each accumulator part per round: all of a round's
+    // loads are in flight before its one wait
+    constexpr int NPART = 2 + (C::NL > 0 ? 1 : 0);
+    constexpr int CW = (KP < C::FOLD_CW) ? KP : C::FOLD_CW;
 #pragma unroll
-    for (int cc = 0; cc < KP; cc += 8) {
-      uint32_t x[16];
-      tmem_ld_pair(tb + cc, tb + KP + cc, x);
-      float v[8];
-      if constexpr (C::F8) {
+    for (int cc = 0; cc < KP; cc += CW) {
+      uint32_t x[NPART * CW];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          v[j] = fmaf(__uint_as_float(x[8 + j]), 0.0625f, __uint_as_float(x[j])) * sc;
-      } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(x[j]) + __uint_as_float(x[8 + j]);
+      for (int u = 0; u < CW; u += 8) {
+        tmem_ld8_nw(tb + cc + u, x, u);                 // [H_hi] part
+        tmem_ld8_nw(tb + KP + cc + u, x, CW + u);       // [H_lo] part
+        if constexpr (C::NL > 0)                        // S_lo bf16(H)
+          tmem_ld8_nw(tb + C::N + cc + u, x, 2 * CW + u);
       }
-      if constexpr (C::NL == KP) {  // S_lo H_hi
-        uint32_t y[8];
-        tmem_ld8(tb + C::N + cc, y);
+      tmem_wait_ld_all(x);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] += __uint_as_float(y[j]);
-      } else if constexpr (C::NL == C::N) {  // S_lo [H_hi | H_lo]
-        uint32_t y[16];
-        tmem_ld_pair(tb + C::N + cc, tb + C::N + KP + cc, y);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] += __uint_as_float(y[j]) + __uint_as_float(y[8 + j]);
+      for (int j = 0; j < CW; ++j) {
+        float v;
+        if constexpr (C::F8) {
+          v = fmaf(__uint_as_float(x[CW + j]), 0.0625f, __uint_as_float(x[j])) * sc;
+        } else {
+          v = __uint_as_float(x[j]) + __uint_as_float(x[CW + j]);
+        }
+        if constexpr (C::NL > 0) v += __uint_as_float(x[2 * CW + j]);
+        p[cc + j] += v;
       }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) p[cc + j] += v[j];
     }
     fence_before();
     __syncwarp();
@@ -595,7 +709,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     const int64_t cend = (f + 1) * C::FOLD;
     if (cend % C::SPU == 0) {
       const int64_t u = cend / C::SPU - 1;  // unit just completed
-      if (u + 1 == L1 || (u + 1) % a.n_cols == 0) finish_segment((int)(u / a.n_cols));
+      if (u + 1 == Lhi || (u + 1) % a.n_cols == 0) finish_segment((int)(u / a.n_cols));
     }
   };
 
@@ -603,15 +717,38 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     int stage = 0;
     uint32_t phase = 0;
     uint32_t eph[4] = {0u, 0u, 0u, 0u};
-    for (int64_t c = c0; c < c1 && ok; ++c) {
-      const int ab = (int)((c - c0) % C::NABUF);
+    int64_t prev = -1, prev_hi = 0;  // chunk waiting to be folded
+    int prev_si = 0;
+    int64_t run = 0;                  // chunks converted so far
+    for (int si = 0; si < 2 && ok; ++si)
+    for (int64_t c = sg.lo[si] * C::SPU; c < sg.hi[si] * C::SPU && ok; ++c, ++run) {
+      const int ab = C::SLO16 ? stage : (int)(run % C::NABUF);
       if (!warp_wait(&full[stage], phase, abort_flag) ||
-          !warp_wait(&aempty[ab], eph[ab] ^ 1, abort_flag)) {
+          (!C::SLO16 && !warp_wait(&aempty[ab], eph[ab] ^ 1, abort_flag))) {
         fail(15);
         break;
       }
       fence_after();
       const uint8_t *sa = smem + stage * C::STAGE;
+      if constexpr (C::SLO16) {
+        // S_lo = S - tf32_trunc(S) (exact), rounded to bf16, two per column
+#pragma unroll
+        for (int at = 0; at < C::APS; ++at) {
+          const uint8_t *rowp = sa + at * kAtomBytes + row * 128;
+          uint32_t pk[16];
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) {  // 16-byte chunk of the 128-byte row
+            const float4 v = *reinterpret_cast<const float4 *>(rowp + ((ch ^ (row & 7)) << 4));
+            const __nv_bfloat162 l01 =
+                __floats2bfloat162_rn(v.x - tf32_trunc(v.x), v.y - tf32_trunc(v.y));
+            const __nv_bfloat162 l23 =
+                __floats2bfloat162_rn(v.z - tf32_trunc(v.z), v.w - tf32_trunc(v.w));
+            pk[2 * ch] = *reinterpret_cast<const uint32_t *>(&l01);
+            pk[2 * ch + 1] = *reinterpret_cast<const uint32_t *>(&l23);
+          }
+          tmem_st16(tmem_base + lane_off + (uint32_t)ab * C::ABUF + (uint32_t)at * 16u, pk);
+        }
+      } else
 #pragma unroll
       for (int at = 0; at < C::APS; ++at) {
         const uint8_t *rowp = sa + at * kAtomBytes + row * 128;
@@ -639,16 +776,21 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
         mbar_arrive(&empty[stage]);
         mbar_arrive(&afull[ab]);
       }
-      eph[ab] ^= 1;
+      if constexpr (!C::SLO16) eph[ab] ^= 1;
       if (++stage == STAGES) {
         stage = 0;
         phase ^= 1;
       }
-      if (c > c0) fold(c - 1);  // FOLD == 1: one chain per stage
+      if (prev >= 0) fold(prev, prev_hi, prev_si);  // FOLD == 1: one chain per stage
+      prev = c;
+      prev_hi = sg.hi[si];
+      prev_si = si;
     }
-    if (ok && c1 > c0) fold(c1 - 1);
+    if (ok && prev >= 0) fold(prev, prev_hi, prev_si);
   } else {
-    for (int64_t f = c0 / C::FOLD; f < c1 / C::FOLD && ok; ++f) fold(f);
+    for (int si = 0; si < 2; ++si)
+      for (int64_t f = sg.lo[si] * C::SPU / C::FOLD; f < sg.hi[si] * C::SPU / C::FOLD && ok; ++f)
+        fold(f, sg.hi[si], si);
   }
 }
 
@@ -656,7 +798,8 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
 template <int DT, int KP>
 __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
     step_tc_kernel(const __grid_constant__ CUtensorMap mapS,
-                   const __grid_constant__ CUtensorMap mapB, const TcArgs a, const EpiArgs e) {
+                   const __grid_constant__ CUtensorMap mapB,
+                   const __grid_constant__ CUtensorMap mapB2, const TcArgs a, const EpiArgs e) {
   using C = Cfg<DT, KP>;
   constexpr int N = C::N;
   constexpr int STAGES = C::STAGES;
@@ -667,7 +810,7 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * C::STAGE);
   uint64_t *empty = full + STAGES;
   uint64_t *afull = empty + STAGES;
-  uint64_t *aempty = afull + 4;
+  uint64_t *aempty = afull + 8;
   uint64_t *tfull = aempty + 4;
   uint64_t *tempty = tfull + 2;
   uint64_t *pfull = tempty + 2;
@@ -690,10 +833,8 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], F32 ? 5 : 1);  // (4 converter warps +) the MMA commit
     }
-    for (int i = 0; i < 4; ++i) {
-      mbar_init(&afull[i], 4);
-      mbar_init(&aempty[i], 1);
-    }
+    for (int i = 0; i < 8; ++i) mbar_init(&afull[i], 4);
+    for (int i = 0; i < 4; ++i) mbar_init(&aempty[i], 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], 4);
@@ -711,26 +852,29 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
   const uint32_t tmem_base = *holder;
 
   const int b = blockIdx.x;
-  const int64_t L0 = (int64_t)b * a.W / a.G;
-  const int64_t L1 = (int64_t)(b + 1) * a.W / a.G;
-  const int64_t c0 = L0 * C::SPU, c1 = L1 * C::SPU;  // stage-sized chunks
+  const Segs sg = cta_segments(a, b);
   int issued = 0;
 
   if (warp == 0) {
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapS)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+      if constexpr (C::SLO16)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB2)) : "memory");
       int stage = 0;
       uint32_t phase = 0;
-      for (int64_t c = c0; c < c1; ++c) {
+      bool stop = false;
+      for (int si = 0; si < 2 && !stop; ++si)
+      for (int64_t c = sg.lo[si] * C::SPU; c < sg.hi[si] * C::SPU; ++c) {
         const int64_t L = c / C::SPU;
         const int kc = (int)(c % C::SPU);
-        const int tp = (int)(L / a.n_cols), ci = (int)(L % a.n_cols);
+        const int tp = (int)(L / a.n_cols), ci = unit_col(a, sg, L, si);
         const int rt = a.row_list ? a.row_list[tp] : tp;
         const int ct = a.col_list ? a.col_list[ci] : ci;
         if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) {
           set_err(a.err, 1);
           *abort_flag = 1;
+          stop = true;
           break;
         }
         uint8_t *sa = smem + stage * C::STAGE;
@@ -742,6 +886,8 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
           tma_load_2d(sa + at * kAtomBytes, &mapS, &full[stage], x0 + at * C::ATOM_COLS, rt * 128);
           tma_load_2d(sb + at * C::B_ATOM, &mapB, &full[stage], x0 + at * C::ATOM_COLS, 0);
         }
+        if constexpr (C::SLO16)  // bf16 H^T rows for the stage's 64 columns
+          tma_load_2d(sb + C::B_BYTES, &mapB2, &full[stage], x0, 0);
         ++issued;
         if (++stage == STAGES) {
           stage = 0;
@@ -755,28 +901,26 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
       uint32_t phase = 0;
       int acc = 0;
       uint32_t tph[2] = {0u, 0u};
-      uint32_t aph[4] = {0u, 0u, 0u, 0u};
+      uint32_t aph[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
       constexpr uint32_t idesc =
           F32 ? idesc_tf32(128, N) : C::F8 ? idesc_e4m3(128, N) : idesc_bf16(128, N);
       int done = 0;
-      for (int64_t c = c0; c < c1; ++c) {
-        const int64_t L = c / C::SPU;
-        const int kc = (int)(c % C::SPU);
-        const int ci = (int)(L % a.n_cols);
-        (void)L;
-        (void)kc;
-        (void)ci;
+      bool stop = false;
+      for (int si = 0; si < 2 && !stop; ++si)
+      for (int64_t c = sg.lo[si] * C::SPU; c < sg.hi[si] * C::SPU; ++c) {
         const bool seg_start = (c % C::FOLD) == 0;
         const bool seg_end = (c % C::FOLD) == C::FOLD - 1;
-        const int ab = (int)((c - c0) % C::NABUF);
+        const int ab = C::SLO16 ? stage : done % C::NABUF;
         if (seg_start && !mbar_wait(&tempty[acc], tph[acc] ^ 1, abort_flag)) {
           set_err(a.err, 2);
           *abort_flag = 1;
+          stop = true;
           break;
         }
         if (!mbar_wait(&full[stage], phase, abort_flag)) {
           set_err(a.err, 3);
           *abort_flag = 1;
+          stop = true;
           break;
         }
         fence_after();
@@ -785,8 +929,8 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
         const uint32_t d = tmem_base + C::ACC0 + (uint32_t)acc * C::ACCW;
         if constexpr (F32) {
           // S_hi [H_hi | H_lo] straight from the staged tile, then, once the
-          // converters have stored S_lo, S_lo H_hi from TMEM (S_lo [H_hi |
-          // H_lo] when kp = 8, the narrowest MMA being N = 16)
+          // converters have stored S_lo in TMEM, S_lo H: as kind::f16 against
+          // bf16(H) (kp <= 32), else as tf32 against H_hi into the H_lo part
           constexpr uint32_t idesc_lo = idesc_tf32(128, KP >= 16 ? KP : N);
 #pragma unroll
           for (int j = 0; j < C::KSL; ++j) {
@@ -798,17 +942,26 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
           if (!mbar_wait(&afull[ab], aph[ab], abort_flag)) {
             set_err(a.err, 3);
             *abort_flag = 1;
+            stop = true;
             break;
           }
           fence_after();
+          if constexpr (C::SLO16) {
+            // bf16 S_lo (TMEM, 8 columns per k-step of 16) against bf16(H)
+            constexpr uint32_t idesc16 = idesc_bf16(128, C::N2);
+            const uint32_t sb2 = sb + C::B_BYTES;
 #pragma unroll
-          for (int j = 0; j < C::KSL; ++j) {
-            const uint32_t within = (uint32_t)(j & 3) * 32u;
-            const uint64_t bd = sdesc(sb + (uint32_t)(j >> 2) * C::B_ATOM + within);
-            const uint32_t alo = tmem_base + (uint32_t)ab * C::ABUF + (uint32_t)j * 8u;
-            if constexpr (C::NL > 0) {
-              mma_tf32_ta(d + N, alo, bd, idesc_lo, (seg_start && j == 0) ? 0u : 1u);
-            } else {
+            for (int j = 0; j < C::APS * 2; ++j) {
+              const uint64_t bd = sdesc(sb2 + (uint32_t)j * 32u);
+              const uint32_t alo = tmem_base + (uint32_t)ab * C::ABUF + (uint32_t)j * 8u;
+              mma_bf16_ta(d + N, alo, bd, idesc16, (seg_start && j == 0) ? 0u : 1u);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < C::KSL; ++j) {
+              const uint32_t within = (uint32_t)(j & 3) * 32u;
+              const uint64_t bd = sdesc(sb + (uint32_t)(j >> 2) * C::B_ATOM + within);
+              const uint32_t alo = tmem_base + (uint32_t)ab * C::ABUF + (uint32_t)j * 8u;
               mma_tf32_ta(d + (KP >= 16 ? KP : 0), alo, bd, idesc_lo, 1u);
             }
           }
@@ -826,7 +979,7 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
         }
         mma_commit(&empty[stage]);
         if (F32) {
-          mma_commit(&aempty[ab]);
+          if (!C::SLO16) mma_commit(&aempty[ab]);
           aph[ab] ^= 1;
         }
         ++done;
@@ -847,10 +1000,10 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
   } else if (warp >= 10) {
     const Hand hd{pfull, pempty, pflag};
     folder_role<DT, KP>(a, tmem_base, smem, full, empty, afull, aempty, tfull, tempty, hd, sflag,
-                        abort_flag, L0, L1, b);
+                        abort_flag, sg, b);
   } else {
     const Hand hd{pfull, pempty, pflag};
-    epilogue_role<DT, KP>(a, e, tmem_base, Hs, Gs, scratch, hd, abort_flag, L0, L1);
+    epilogue_role<DT, KP>(a, e, tmem_base, Hs, Gs, scratch, hd, abort_flag, sg);
   }
   __syncthreads();
   if (warp == 0 && lane == 0 && *abort_flag) {
@@ -914,10 +1067,17 @@ cudaError_t launch_cfg(const ProdArgs &p, const EpiArgs &e, cudaStream_t s, cons
   if (!make_map_2d(&mB, p.Bt, t, (uint64_t)p.ldb, (uint64_t)(2 * KP), (uint64_t)p.ldb * es,
                    C::ATOM_COLS, 2 * KP))
     return cudaErrorInvalidValue;
+  CUtensorMap mB2 = mB;
+  if constexpr (C::SLO16) {
+    if (!make_map_2d(&mB2, bt_b16(const_cast<void *>(p.Bt), KP, p.ldb),
+                     CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (uint64_t)p.ldb, (uint64_t)C::N2,
+                     (uint64_t)p.ldb * 2, 64, C::N2))
+      return cudaErrorInvalidValue;
+  }
   cudaError_t err = cudaFuncSetAttribute(step_tc_kernel<DT, KP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   if (err != cudaSuccess) return err;
-  step_tc_kernel<DT, KP><<<ta.G, C::THREADS, C::SMEM, s>>>(mS, mB, ta, e);
+  step_tc_kernel<DT, KP><<<ta.G, C::THREADS, C::SMEM, s>>>(mS, mB, mB2, ta, e);
   return cudaGetLastError();
 }
 
@@ -941,6 +1101,11 @@ cudaError_t launch_step_tc(const ProdArgs &a, const EpiArgs *epi, int *tile_cnt,
   ta.err = err;
   ta.fused = (epi != nullptr) ? 1 : 0;
   ta.tile_cnt = tile_cnt;
+  // all row positions shared stream-K style (D = 0).  Owning whole tiles
+  // (D = n_rows / G) makes the R leftover tiles' last arrivers add ~G / R
+  // partials each while HBM is saturated, which measured slower.
+  ta.D = 0;
+  ta.R = a.n_rows_list - ta.D * ta.G;
   ta.sS = a.scales;
   ta.ld_sS = a.ld_scales;
   *G_out = ta.G;

@@ -10,7 +10,9 @@
 //     are 0), in one of two formats (bt_fmt):
 //       0: bfloat16, hi = bf16(H), lo = bf16(H - hi)      (BF16 / FP8 S)
 //       1: float holding tf32 values, hi = H with the 13 low mantissa bits
-//          cleared, lo = (H - hi) likewise truncated       (FP32 S)
+//          cleared, lo = (H - hi) rounded to tf32, followed by a bf16
+//          copy [max(kp,16)][ldb] with rows 0..kp-1 = bf16(H^T) and the
+//          rest 0 (the operand of the S_lo H product)      (FP32 S)
 //       2: e4m3 bytes, hi = e4m3(H / d), lo = e4m3(16 (H / d - hi)), with d a
 //          power of two per 128-row tile of H (the smallest with
 //          max|H_tile| / d <= 448); the 2 kp rows are followed by the
@@ -24,11 +26,17 @@ namespace symnmf {
 constexpr int kTileRows = 128;
 
 // bytes of one MMA copy of H in format fmt, and the tile factors d of format 2
+__host__ __device__ inline int bt_n2(int kp) { return kp < 16 ? 16 : kp; }
 inline size_t bt_bytes(int fmt, int kp, int64_t ldb) {
   const size_t es = fmt == 1 ? 4 : fmt == 2 ? 1 : 2;
   size_t b = (size_t)2 * kp * ldb * es;
+  if (fmt == 1) b += (size_t)bt_n2(kp) * ldb * 2;
   if (fmt == 2) b += (size_t)(ldb / kTileRows) * sizeof(float);
   return b;
+}
+// format 1: the bf16 copy of H^T after the tf32 hi/lo rows
+__host__ __device__ inline uint16_t *bt_b16(void *Bt, int kp, int64_t ldb) {
+  return reinterpret_cast<uint16_t *>(reinterpret_cast<uint8_t *>(Bt) + (size_t)2 * kp * ldb * 4);
 }
 __host__ __device__ inline float *bt_deq(void *Bt, int kp, int64_t ldb) {
   return reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(Bt) + (size_t)2 * kp * ldb);

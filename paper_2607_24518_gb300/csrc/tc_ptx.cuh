@@ -107,6 +107,14 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
+// kind::f16 MMA (bf16) with the A operand in tensor memory
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
+}
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -250,6 +258,24 @@ __device__ __forceinline__ void tmem_ld8(uint32_t ta, uint32_t (&x)[8]) {
                  "+r"(x[6]), "+r"(x[7])
                :
                : "memory");
+}
+
+// 8 consecutive TMEM columns of this thread's lane into x[off .. off+7],
+// without waiting (pair with tmem_wait_ld_all on the same array)
+template <int N>
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t ta, uint32_t (&x)[N], int off) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(x[off + 0]), "=r"(x[off + 1]), "=r"(x[off + 2]), "=r"(x[off + 3]),
+                 "=r"(x[off + 4]), "=r"(x[off + 5]), "=r"(x[off + 6]), "=r"(x[off + 7])
+               : "r"(ta));
+}
+// wait for every outstanding tcgen05.ld of the warp; the empty statements
+// tie each register of x to the wait so no use moves above it
+template <int N>
+__device__ __forceinline__ void tmem_wait_ld_all(uint32_t (&x)[N]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < N; ++i) asm volatile("" : "+r"(x[i]));
 }
 
 }  // namespace tc
