@@ -220,17 +220,25 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clocks = Clocks(local_rank) if rank == 0 else None
     time.sleep(0.3 if clocks else 0)
-    L.symnmf_set_profiling(h, True)
+    # timed region: no events between the kernels (an event would break
+    # the overlap of each step with the previous iteration's reduction)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     status, st = L.symnmf_step(h, hp, args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    iters = int(st.iter) - args.warmup
+    # the same steps again with an event pair around every step kernel:
+    # its average duration (roofline) and the kernels launched per step
+    prof_steps = max(10, min(args.steps, 100))
+    L.symnmf_set_profiling(h, True)
+    L.symnmf_step(h, hp, prof_steps)
+    torch.cuda.synchronize()
     prod_ms, prod_launches, prod_bytes, kernel_launches = L.symnmf_get_profile(h)
     L.symnmf_set_profiling(h, False)
     ck = clocks.stop() if clocks else None
-    iters = int(st.iter) - args.warmup
+    kernels_per_step = kernel_launches / max(1, prof_steps)
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -327,7 +335,7 @@ def run_native(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": ck,
-            "gpu_launches": int(kernel_launches),
+            "gpu_launches": int(round(kernels_per_step * iters)),
             "status": L.symnmf_status_string(status),
         }
     return out

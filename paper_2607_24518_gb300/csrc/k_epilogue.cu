@@ -284,6 +284,9 @@ __global__ void __launch_bounds__(256) prepare_kernel(const float *H, int64_t n,
 // forms the iteration record f = ||S||^2 - 2 tr + ||Gram_t||^2 (Eq. 2).
 template <int KP>
 __global__ void __launch_bounds__(128) reduce_iter_kernel(ReduceArgs a) {
+  // let the next step kernel start streaming now: only its epilogue warps
+  // read what this kernel writes, and they wait for it (griddepcontrol.wait)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ double red[40];
   __shared__ double sc[4];
   __shared__ int last;

@@ -444,6 +444,9 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
   const int et = (warp - 2) * 32 + lane;  // 0..255
   const int half = (warp - 2) >> 2;       // column half owned
   if (!a.fused) return;
+  // the Gram of H_t and the tile slots belong to the preceding reduction
+  // kernel, which may still run (programmatic dependent launch)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int i = et; i < KP * KP; i += 256) Gs[i] = e.gram[i];
   epi_bar();
   int pb = 0;
@@ -1077,8 +1080,19 @@ cudaError_t launch_cfg(const ProdArgs &p, const EpiArgs &e, cudaStream_t s, cons
   cudaError_t err = cudaFuncSetAttribute(step_tc_kernel<DT, KP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   if (err != cudaSuccess) return err;
-  step_tc_kernel<DT, KP><<<ta.G, C::THREADS, C::SMEM, s>>>(mS, mB, mB2, ta, e);
-  return cudaGetLastError();
+  // fused steps may start while the previous iteration's reduction kernel
+  // runs: the stream of S needs only H_t, which the previous step wrote
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ta.G);
+  cfg.blockDim = dim3(C::THREADS);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = ta.fused ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, step_tc_kernel<DT, KP>, mS, mB, mB2, ta, e);
 }
 
 }  // namespace
