@@ -343,6 +343,76 @@ def run_native(args, rank, world, local_rank):
     return out
 
 
+def run_time_to_tol(args):
+    """Time to a relative objective tolerance at n=1e5 (correlation, k=32,
+    full-batch AdaGrad), S stored FP32 vs BF16.  E* is the E at which a long
+    FP32 run stops under the AND rule (Eq. 11) or at its iteration cap; a
+    run reaches tolerance at the first check with (E_t - E*) / E* <= tol.
+    The final H of each run is also evaluated on the FP32 S."""
+    import numpy as np
+    import torch
+    import gen
+    from paper_2607_24518_gb300 import build
+    build.build()
+    from paper_2607_24518_gb300 import symnmf as L
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n, k, tol = args.ttt_n, 32, 1e-3
+    t_gen = time.perf_counter()
+    inst = gen.corr_factor(n=n, T=500, seed=0, device=dev, dtype=torch.float32, materialize="torch")
+    S32 = inst.S
+    Sbf = S32.to(torch.bfloat16)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    mean = float(S32[:4096].double().mean())
+    H0 = torch.tensor(gen.init_scaled(mean, n, k, seed=0), dtype=torch.float32, device=dev)
+    hp = L.symnmf_hparams_default(L.ADAGRAD)
+    per = hp.check_interval
+
+    def solve(S, dt, stop, cap):
+        h = L.symnmf_create(S, n, k, dt)
+        L.symnmf_set_H(h, H0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, E, conv = 0, float("nan"), False
+        while it < cap:
+            status, st = L.symnmf_step(h, hp, per)
+            it = int(st.iter)
+            E = float(st.E)
+            if status == L.CONVERGED:
+                conv = True
+                break
+            if stop is not None and st.last_check >= 0 and (E - stop) / stop <= tol:
+                break
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        Hf = torch.empty(n, k, dtype=torch.float32, device=dev)
+        L.symnmf_get_H(h, Hf)
+        L.symnmf_destroy(h)
+        return {"iters": it, "seconds": el, "E": E, "converged": conv}, Hf
+
+    ref, Href = solve(S32, L.F32, None, args.ttt_cap)
+    Estar = ref["E"]
+    h32 = L.symnmf_create(S32, n, k, L.F32)
+    runs = {}
+    for name, S, dt in (("fp32", S32, L.F32), ("bf16", Sbf, L.BF16)):
+        r, Hf = solve(S, dt, Estar, args.ttt_cap)
+        L.symnmf_set_H(h32, Hf)
+        r["E_on_fp32_S"] = L.symnmf_objective(h32)[1]
+        runs[name] = r
+    L.symnmf_destroy(h32)
+    sp = runs["fp32"]["seconds"] / runs["bf16"]["seconds"]
+    return {"metric": "time-to-tol at n=1e5 BF16 vs FP32 (relative objective 1e-3)",
+            "value": runs["bf16"]["seconds"], "unit": "s", "higher_is_better": False,
+            "speedup_bf16_vs_fp32": sp, "n_gpus": 1, "data": "synthetic (seeded correlation generator)",
+            "dtype": "bf16 vs f32 storage, f32 accumulate, f64 reductions",
+            "config": {"workload": "corr_n%d_k32_adagrad_time_to_tol" % n, "n": n, "k": k,
+                       "method": "adagrad", "eta": hp.eta, "tol": tol,
+                       "E_star_rule": "E of an FP32 run stopped by the AND rule (or the cap)"},
+            "reference_run": ref, "E_star": Estar, "runs": runs,
+            "generation_seconds": t_gen}
+
+
 def run_reference(args, rank):
     """The FP64 CPU oracle on the same workload, bounded per step."""
     if rank != 0:
@@ -388,11 +458,18 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--time-to-tol", dest="time_to_tol", action="store_true",
+                    help="time to relative objective 1e-3 at n=1e5, BF16 vs FP32 (own JSON line)")
+    ap.add_argument("--ttt-n", dest="ttt_n", type=int, default=100000)
+    ap.add_argument("--ttt-cap", dest="ttt_cap", type=int, default=4000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.time_to_tol:
+        print(json.dumps(run_time_to_tol(args)), flush=True)
+        return
     if args.impl == "reference":
         out = run_reference(args, rank)
         if out:
