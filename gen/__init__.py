@@ -54,7 +54,8 @@ def _torch():
 
 
 def _gram_abs_unitdiag(Y: np.ndarray, scale: float, device: str, out_dtype,
-                       absolute: bool, chunk: int = 8192, ld: int | None = None):
+                       absolute: bool, chunk: int = 8192, ld: int | None = None,
+                       block_fn=None, compute_dtype=None):
     """S = D^-1/2 |scale * Y Y^T| D^-1/2, filled chunk pair by chunk pair.
 
     ``Y`` is n x T (float64).  Only chunk pairs (r, c) with c >= r are
@@ -62,14 +63,21 @@ def _gram_abs_unitdiag(Y: np.ndarray, scale: float, device: str, out_dtype,
     stored matrix is exactly symmetric.  Returns a torch tensor n x ld
     (columns past n zero) of ``out_dtype`` on ``device`` and the float64 sum
     of squares of the float64 values before the final cast.
+
+    With ``block_fn`` nothing is stored: each chunk pair (c >= r) is passed
+    as ``block_fn(r0, r1, c0, c1, blk)`` (the caller stores it and, for
+    c0 != r0, its transpose) and the first return value is None.
+    ``compute_dtype`` (default float64) is the precision of the products.
     """
     torch = _torch()
     n = Y.shape[0]
     ld = n if ld is None else ld
+    cdt = compute_dtype or torch.float64
     Yt = torch.from_numpy(np.ascontiguousarray(Y)).to(device=device, dtype=torch.float64)
     d = (Yt * Yt).sum(dim=1) * scale
-    rs = torch.rsqrt(d)
-    out = torch.zeros((n, ld), dtype=out_dtype, device=device)
+    rs = torch.rsqrt(d).to(cdt)
+    Yt = Yt.to(cdt)
+    out = torch.zeros((n, ld), dtype=out_dtype, device=device) if block_fn is None else None
     norm2 = 0.0
     for r0 in range(0, n, chunk):
         r1 = min(n, r0 + chunk)
@@ -85,7 +93,10 @@ def _gram_abs_unitdiag(Y: np.ndarray, scale: float, device: str, out_dtype,
                 blk = lower + lower.T
                 blk.fill_diagonal_(1.0)
             w = 1.0 if c0 == r0 else 2.0
-            norm2 += w * float((blk * blk).sum())
+            norm2 += w * float((blk.double() * blk.double()).sum())
+            if block_fn is not None:
+                block_fn(r0, r1, c0, c1, blk)
+                continue
             out[r0:r1, c0:c1] = blk.to(out_dtype)
             if c0 != r0:
                 out[c0:c1, r0:r1] = blk.T.to(out_dtype)
@@ -126,7 +137,7 @@ def corr_planted(n: int = 512, groups: int = 8, T: int = 2000, lo: float = 0.3,
 def tpdm_groups(n: int = 20000, groups: int = 32, T: int = 5000, overlap: float = 0.03,
                 q: float = 0.05, lo: float = 0.2, hi: float = 1.0, common: tuple | None = None,
                 seed: int = 0, device: str = "cpu", dtype=None, materialize: str = "numpy",
-                ld: int | None = None) -> Instance:
+                ld: int | None = None, block_fn=None, compute_dtype=None) -> Instance:
     """Unit-diagonal empirical TPDM of a Pareto(2) factor model.
 
     A (n x groups, non-negative): each row loads U[lo, hi] on its own group
@@ -166,9 +177,12 @@ def tpdm_groups(n: int = 20000, groups: int = 32, T: int = 5000, overlap: float 
     Xk = At @ Zt[:, keep]                      # n x n_exc
     W = Xk / torch.sqrt(R2[keep])[None, :]     # angular parts, columns = Omega rows
     S_t, norm2 = _gram_abs_unitdiag(W.cpu().numpy() if device == "cpu" else W.double().cpu().numpy(),
-                                    n / n_exc, device, dtype or torch.float64, False, ld=ld)
-    return _finish(S_t, n, "tpdm", seed, perm, labels,
-                   {"T": T, "groups": groups, "n_exc": n_exc, "normS2_f64": norm2}, materialize)
+                                    n / n_exc, device, dtype or torch.float64, False, ld=ld,
+                                    block_fn=block_fn, compute_dtype=compute_dtype)
+    meta = {"T": T, "groups": groups, "n_exc": n_exc, "normS2_f64": norm2}
+    if block_fn is not None:
+        return Instance(S=None, n=n, kind="tpdm", seed=seed, perm=perm, labels=labels, meta=meta)
+    return _finish(S_t, n, "tpdm", seed, perm, labels, meta, materialize)
 
 
 def corr_factor(n: int = 100000, T: int = 500, sectors: int = 49, density: float = 0.1,

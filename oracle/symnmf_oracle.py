@@ -75,6 +75,15 @@ def gradient(S, H):
     return 4.0 * (H @ (H.T @ H) - S @ H)
 
 
+def gradient_rows(S_rows, H, rows):
+    """Rows `rows` of grad_H f = 4 (H (H^T H) - S H) (Sec. 2.1), from the
+    matching rows of S only (for checks at sizes where S does not fit)."""
+    S_rows = np.asarray(S_rows, dtype=np.float64)
+    H = np.asarray(H, dtype=np.float64)
+    rows = np.asarray(rows)
+    return 4.0 * (H[rows] @ (H.T @ H) - S_rows @ H)
+
+
 def projected_gradient(H, G):
     """Projected gradient of Eq. 6: G where H > 0, min(0, G) where H == 0."""
     return np.where(H > 0, G, np.minimum(0.0, G))

@@ -484,3 +484,11 @@ def test_quantize_dequantize_error_bound():
     big = inst.S > 1e-2
     assert np.all(np.abs(D[big] - inst.S[big]) <= 2.0 ** -4 * inst.S[big])
     assert np.all(np.abs(q) <= 448.0)
+
+
+def test_gradient_rows_is_the_full_gradient_restricted():
+    inst = gen.tpdm_groups(n=260, groups=5, T=1100, q=0.05, seed=9)
+    H = gen.init_scaled(float(inst.S.mean()), 260, 6, seed=9)
+    rows = np.array([0, 7, 128, 259])
+    G = O.gradient(inst.S, H)
+    np.testing.assert_allclose(O.gradient_rows(inst.S[rows], H, rows), G[rows], rtol=1e-13, atol=1e-12)
