@@ -66,6 +66,7 @@ struct TcArgs {
   int G;                 // CTAs
   int R;                 // leading row positions shared stream-K style
   int D;                 // row positions owned whole by each CTA after those
+  int thr;               // fused: boundary shift limit in units (see sk_start)
   int n_cols;
   const int *row_list;
   const int *col_list;
@@ -136,11 +137,30 @@ struct Segs {
   int64_t lo[2], hi[2];
   int rot;
 };
+// First shared unit of CTA b (b = G: the end).  The even split b W_R / G is
+// moved down to a tile boundary when CTA b-1 would otherwise hold a whole
+// tile and then fewer than `thr` units of the next one: that tile's
+// epilogue and the next one's would both fall after CTA b-1's stream, while
+// CTA b absorbs the few units at the cost of a few units of streaming.
+__device__ __forceinline__ int64_t sk_start(const TcArgs &a, int b, int64_t WR) {
+  const int64_t x = (int64_t)b * WR / a.G;
+  if (!a.fused || b <= 0 || b >= a.G) return x;
+  const int64_t prev = (int64_t)(b - 1) * WR / a.G;
+  const int64_t B = x / a.n_cols * a.n_cols;
+  if (x > B && x - B < a.thr && B - a.n_cols >= prev) return B;
+  return x;
+}
+// CTA holding shared unit u
+__device__ __forceinline__ int64_t sk_owner(const TcArgs &a, int64_t u, int64_t WR) {
+  int64_t b = sk_cta(u, WR, a.G);
+  if (b + 1 < a.G && u >= sk_start(a, (int)b + 1, WR)) ++b;
+  return b;
+}
 __device__ __forceinline__ Segs cta_segments(const TcArgs &a, int b) {
   const int64_t WR = (int64_t)a.R * a.n_cols;
   Segs s;
-  s.lo[0] = (int64_t)b * WR / a.G;
-  s.hi[0] = (int64_t)(b + 1) * WR / a.G;
+  s.lo[0] = sk_start(a, b, WR);
+  s.hi[0] = sk_start(a, b + 1, WR);
   s.lo[1] = ((int64_t)a.R + (int64_t)b * a.D) * a.n_cols;
   s.hi[1] = s.lo[1] + (int64_t)a.D * a.n_cols;
   s.rot = (int)((int64_t)b * a.n_cols / a.G);
@@ -175,34 +195,34 @@ struct Own {
   static constexpr int HW = KH <= 16 ? KH : 16;  // columns whose state is held at once
 };
 
+// What a tile's epilogue needs before its S H rows exist: H_t of the tile in
+// Hs (both column halves), the thread's optimizer state (the first HW
+// owned columns) and its share of H_t Gram_t.  Ends with the tile's H_t in
+// Hs for every thread.
 template <int DT, int KP>
-__device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&p)[Own<KP>::KH],
-                                              float *Hs, const float *Gs, double *scratch, int et,
-                                              int row, int half) {
+__device__ __forceinline__ void tile_prep(const EpiArgs &e, int tp, float *Hs, const float *Gs,
+                                          int row, int half, float (&hg)[Own<KP>::KH],
+                                          float (&av)[Own<KP>::HW], float (&mv)[Own<KP>::HW]) {
   constexpr int KH = Own<KP>::KH;
   constexpr int HW = Own<KP>::HW;
   const bool works = (KP >= 16) || half == 0;
-  const int cb = (KP >= 16) ? half * KH : 0;  // first owned column
+  const int cb = (KP >= 16) ? half * KH : 0;
   const int64_t r0 = (int64_t)tp * 128;
   const int rows = (int)((e.n - r0) < 128 ? (e.n - r0) : 128);
   const bool vrow = works && row < rows;
   const bool rms = (e.method == SYMNMF_RMSPROP);
   const int64_t base = (r0 + row) * KP + cb;
   float *hrow = Hs + row * (KP + 1);
-  float av[HW], mv[HW];
-  auto load_state = [&](int c0) {
 #pragma unroll
-    for (int c4 = 0; c4 < HW / 4; ++c4) {
-      float4 u = make_float4(0.f, 0.f, 0.f, 0.f), w = u;
-      if (vrow && e.update) {
-        u = reinterpret_cast<const float4 *>(e.A + base + c0)[c4];
-        if (rms) w = reinterpret_cast<const float4 *>(e.M + base + c0)[c4];
-      }
-      av[4 * c4 + 0] = u.x; av[4 * c4 + 1] = u.y; av[4 * c4 + 2] = u.z; av[4 * c4 + 3] = u.w;
-      mv[4 * c4 + 0] = w.x; mv[4 * c4 + 1] = w.y; mv[4 * c4 + 2] = w.z; mv[4 * c4 + 3] = w.w;
+  for (int c4 = 0; c4 < HW / 4; ++c4) {
+    float4 u = make_float4(0.f, 0.f, 0.f, 0.f), w = u;
+    if (vrow && e.update) {
+      u = reinterpret_cast<const float4 *>(e.A + base)[c4];
+      if (rms) w = reinterpret_cast<const float4 *>(e.M + base)[c4];
     }
-  };
-  load_state(0);
+    av[4 * c4 + 0] = u.x; av[4 * c4 + 1] = u.y; av[4 * c4 + 2] = u.z; av[4 * c4 + 3] = u.w;
+    mv[4 * c4 + 0] = w.x; mv[4 * c4 + 1] = w.y; mv[4 * c4 + 2] = w.z; mv[4 * c4 + 3] = w.w;
+  }
   if (works) {
     const bool in = row < rows;
     const float4 *src = reinterpret_cast<const float4 *>(e.H + base);
@@ -216,14 +236,9 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
     }
   }
   epi_bar();  // both halves of each H_t row are in Hs
-  // tr(H^T S H) share of the row, then g = coef ((H Gram_t) - S H) formed
-  // in place of p, H Gram_t right to left (Sec. 2.1)
-  float tr = 0.f, kkt2 = 0.f, sumA = 0.f, nonfin = 0.f, hmax = 0.f;
+  // (H_t Gram_t) for the owned columns, right to left (Sec. 2.1)
 #pragma unroll
-  for (int j = 0; j < KH; ++j) {
-    if (cb + j < e.k) tr = fmaf(hrow[cb + j], p[j], tr);
-    p[j] = -p[j];
-  }
+  for (int j = 0; j < KH; ++j) hg[j] = 0.f;
 #pragma unroll 2
   for (int d = 0; d < KP; ++d) {
     const float hv = hrow[d];
@@ -231,17 +246,56 @@ __device__ __forceinline__ void tile_epilogue(const EpiArgs &e, int tp, float (&
 #pragma unroll
     for (int c4 = 0; c4 < KH / 4; ++c4) {
       const float4 gv = gr[c4];
-      p[4 * c4 + 0] = fmaf(hv, gv.x, p[4 * c4 + 0]);
-      p[4 * c4 + 1] = fmaf(hv, gv.y, p[4 * c4 + 1]);
-      p[4 * c4 + 2] = fmaf(hv, gv.z, p[4 * c4 + 2]);
-      p[4 * c4 + 3] = fmaf(hv, gv.w, p[4 * c4 + 3]);
+      hg[4 * c4 + 0] = fmaf(hv, gv.x, hg[4 * c4 + 0]);
+      hg[4 * c4 + 1] = fmaf(hv, gv.y, hg[4 * c4 + 1]);
+      hg[4 * c4 + 2] = fmaf(hv, gv.z, hg[4 * c4 + 2]);
+      hg[4 * c4 + 3] = fmaf(hv, gv.w, hg[4 * c4 + 3]);
     }
   }
+}
+
+// The rest of tile tp's epilogue once p holds the thread's S H values (the
+// rows of S H_t, summed in FP32 in a fixed order) and tile_prep has run for
+// tp: g = coef (H Gram_t - S H), the update and projection into the other H
+// buffer, the MMA copy of the new rows, and the tile partials.  Everything
+// the iteration produces for this tile is written here; the cross-tile sums
+// are left to the reduction kernel.
+template <int DT, int KP>
+__device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)[Own<KP>::KH],
+                                            const float (&hg)[Own<KP>::KH],
+                                            float (&av)[Own<KP>::HW], float (&mv)[Own<KP>::HW],
+                                            float *Hs, double *scratch, int et, int row,
+                                            int half) {
+  constexpr int KH = Own<KP>::KH;
+  constexpr int HW = Own<KP>::HW;
+  const bool works = (KP >= 16) || half == 0;
+  const int cb = (KP >= 16) ? half * KH : 0;  // first owned column
+  const int64_t r0 = (int64_t)tp * 128;
+  const int rows = (int)((e.n - r0) < 128 ? (e.n - r0) : 128);
+  const bool vrow = works && row < rows;
+  const bool rms = (e.method == SYMNMF_RMSPROP);
+  const int64_t base = (r0 + row) * KP + cb;
+  float *hrow = Hs + row * (KP + 1);
+  auto load_state = [&](int c0) {
+#pragma unroll
+    for (int c4 = 0; c4 < HW / 4; ++c4) {
+      float4 u = make_float4(0.f, 0.f, 0.f, 0.f), w = u;
+      if (vrow && e.update) {
+        u = reinterpret_cast<const float4 *>(e.A + base + c0)[c4];
+        if (rms) w = reinterpret_cast<const float4 *>(e.M + base + c0)[c4];
+      }
+      av[4 * c4 + 0] = u.x; av[4 * c4 + 1] = u.y; av[4 * c4 + 2] = u.z; av[4 * c4 + 3] = u.w;
+      mv[4 * c4 + 0] = w.x; mv[4 * c4 + 1] = w.y; mv[4 * c4 + 2] = w.z; mv[4 * c4 + 3] = w.w;
+    }
+  };
+  // tr(H^T S H) share of the row (Eq. 2) and g = coef ((H Gram_t) - S H)
+  float tr = 0.f, kkt2 = 0.f, sumA = 0.f, nonfin = 0.f, hmax = 0.f;
 #pragma unroll
   for (int j = 0; j < KH; ++j) {
     float g = 0.f;
     if (cb + j < e.k) {
-      g = e.coef * p[j];
+      tr = fmaf(hrow[cb + j], p[j], tr);
+      g = e.coef * (hg[j] - p[j]);
       const float pg = (hrow[cb + j] > 0.f) ? g : fminf(0.f, g);
       kkt2 = fmaf(pg, pg, kkt2);
       if (!isfinite(g)) nonfin += 1.f;
@@ -449,6 +503,19 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
   asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int i = et; i < KP * KP; i += 256) Gs[i] = e.gram[i];
   epi_bar();
+  constexpr int KH = Own<KP>::KH;
+  constexpr int HW = Own<KP>::HW;
+  float hg[KH], av[HW], mv[HW];
+  // The tile holding this CTA's last unit is, in practice, finished here
+  // (the next CTA streams the rest of it first): prepare it while idle.
+  int prepared = -1;
+  if constexpr (KH == HW) {
+    const int last_si = (sg.hi[1] > sg.lo[1]) ? 1 : 0;
+    if (sg.hi[last_si] > sg.lo[last_si]) {
+      prepared = (int)((sg.hi[last_si] - 1) / a.n_cols);
+      tile_prep<DT, KP>(e, prepared, Hs, Gs, row, half, hg, av, mv);
+    }
+  }
   int pb = 0;
   uint32_t pph[2] = {0u, 0u};
   for (int si = 0; si < 2; ++si)
@@ -465,7 +532,6 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     }
     fence_after();
     const int epi = hd.pflag[pb];  // 0: none, 1: P in TMEM, 2: add the partial slots
-    constexpr int KH = Own<KP>::KH;
     float p[KH];
     if (epi == 1) {
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + C::PB0 +
@@ -486,8 +552,8 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     if (epi == 2) {
       // shared row position: its partials in slots cta + tp, CTA order
       const int64_t WR = (int64_t)a.R * a.n_cols;
-      const int64_t b0 = sk_cta((int64_t)tp * a.n_cols, WR, a.G);
-      const int64_t b1 = sk_cta((int64_t)tp * a.n_cols + a.n_cols - 1, WR, a.G);
+      const int64_t b0 = sk_owner(a, (int64_t)tp * a.n_cols, WR);
+      const int64_t b1 = sk_owner(a, (int64_t)tp * a.n_cols + a.n_cols - 1, WR);
       const int cb = (KP >= 16) ? half * KH : 0;
 #pragma unroll
       for (int j = 0; j < KH; ++j) p[j] = 0.f;
@@ -517,7 +583,14 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
         }
       }
     }
-    if (epi) tile_epilogue<DT, KP>(e, tp, p, Hs, Gs, scratch, et, row, half);
+    if (epi) {
+      if (tp != prepared) {
+        epi_bar();  // no thread still reads Hs of an earlier tile
+        tile_prep<DT, KP>(e, tp, Hs, Gs, row, half, hg, av, mv);
+      }
+      prepared = -1;
+      tile_finish<DT, KP>(e, tp, p, hg, av, mv, Hs, scratch, et, row, half);
+    }
   }
 }
 
@@ -558,8 +631,8 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     if (a.fused) {
       if (tp < a.R) {  // shared row position: the CTAs holding its units
         const int64_t WR = (int64_t)a.R * a.n_cols;
-        b0 = sk_cta((int64_t)tp * a.n_cols, WR, a.G);
-        b1 = sk_cta((int64_t)tp * a.n_cols + a.n_cols - 1, WR, a.G);
+        b0 = sk_owner(a, (int64_t)tp * a.n_cols, WR);
+        b1 = sk_owner(a, (int64_t)tp * a.n_cols + a.n_cols - 1, WR);
       }
       epi = (b0 == b1);
     }
@@ -1120,6 +1193,9 @@ cudaError_t launch_step_tc(const ProdArgs &a, const EpiArgs *epi, int *tile_cnt,
   // partials each while HBM is saturated, which measured slower.
   ta.D = 0;
   ta.R = a.n_rows_list - ta.D * ta.G;
+  // about half an epilogue's worth of streaming: 128 x 128 units of 64 KB
+  // (FP32), 32 KB (BF16), 16 KB (FP8) at a CTA's share of HBM bandwidth
+  ta.thr = a.dtype == 0 ? 4 : a.dtype == 1 ? 9 : 18;
   ta.sS = a.scales;
   ta.ld_sS = a.ld_scales;
   *G_out = ta.G;
