@@ -520,6 +520,97 @@ def run_large_fp8(args):
             "clocks": ck, "generation_seconds": t_gen, "status": L.symnmf_status_string(status)}
 
 
+def run_batch(args):
+    """Batching workload: 64 instances (n ~ U{2000..30000}, k in {8,16,32,64},
+    even = correlation, odd = TPDM), BF16 S, 4 random restarts each (256
+    handles, each on its own stream, the 4 restarts sharing S), Piecewise
+    AdaGrad (eta 1, c 10, c_r 10).  The library's autotuner picks the CTA
+    caps (its trial iterations are part of the solves); then the batch runs
+    to the AND rule.  Reports aggregate iterations/s and per-instance time
+    to tolerance (first restart to converge)."""
+    import numpy as np
+    import torch
+    import gen
+    from paper_2607_24518_gb300 import build
+    build.build()
+    from paper_2607_24518_gb300 import symnmf as L
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    specs = gen.batch_specs(args.batch_count)
+    t_gen = time.perf_counter()
+    mats, handles, hps, owner, streams = [], [], [], [], []
+    for i, sp in enumerate(specs):
+        n, k = sp["n"], sp["k"]
+        ld = -(-n // 8) * 8  # 16-byte row pitch for the tensor-core path
+        if sp["kind"] == "corr":
+            inst = gen.corr_planted(n=n, groups=k, T=2000, seed=sp["seed"], device=dev,
+                                    dtype=torch.bfloat16, materialize="torch", ld=ld)
+        else:
+            inst = gen.tpdm_groups(n=n, groups=k, T=5000, q=0.05, seed=sp["seed"], device=dev,
+                                   dtype=torch.bfloat16, materialize="torch", ld=ld)
+        S = inst.S
+        mats.append(S)
+        mean = float(S[: min(n, 4096), :n].double().mean())
+        for r in range(args.restarts):
+            st = torch.cuda.Stream(device=dev)
+            h = L.symnmf_create_ld(S, n, ld, k, L.BF16)
+            L.symnmf_set_stream(h, st)
+            H0 = torch.tensor(gen.init_scaled(mean, n, k, seed=sp["seed"], stream=r),
+                              dtype=torch.float32, device=dev)
+            L.symnmf_set_H(h, H0)
+            handles.append(h)
+            streams.append(st)
+            hps.append(L.symnmf_hparams_default(L.PIECEWISE_ADAGRAD, eta=1.0, c=10.0, c_r=10.0))
+            owner.append(i)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    t0 = time.perf_counter()
+    caps = L.symnmf_batch_autotune(handles, hps, args.tune_iters)
+    conv_at = [None] * len(handles)
+    iters_done = [0] * len(handles)
+    while True:
+        status, stats = L.symnmf_batch_step(handles, hps, 10)
+        now = time.perf_counter() - t0
+        live = 0
+        for j, stt in enumerate(stats):
+            iters_done[j] = int(stt.iter)
+            if stt.converged and conv_at[j] is None:
+                conv_at[j] = now
+            if not stt.converged:
+                live += 1
+        if live == 0 or max(iters_done) >= args.batch_cap:
+            break
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    total_iters = sum(iters_done)
+    per_inst = []
+    for i, sp in enumerate(specs):
+        js = [j for j in range(len(handles)) if owner[j] == i]
+        times = [conv_at[j] for j in js if conv_at[j] is not None]
+        per_inst.append({"n": sp["n"], "k": sp["k"], "kind": sp["kind"],
+                         "converged_restarts": len(times),
+                         "time_to_tol_s": min(times) if times else None,
+                         "iters": [iters_done[j] for j in js]})
+    for h in handles:
+        L.symnmf_destroy(h)
+    tt = [p["time_to_tol_s"] for p in per_inst if p["time_to_tol_s"] is not None]
+    return {"metric": "batched solves: aggregate iters/s (64 instances x 4 restarts, BF16, Piecewise AdaGrad)",
+            "value": total_iters / wall, "unit": "iters/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "bf16 storage, f32 accumulate, f64 reductions",
+            "data": "synthetic (seeded correlation / TPDM generators, seeds 0-%d)" % (len(specs) - 1),
+            "config": {"workload": "batch_%dx%d_bf16_piecewise" % (len(specs), args.restarts),
+                       "instances": len(specs), "restarts": args.restarts,
+                       "sum_n2": int(sum(sp["n"] ** 2 for sp in specs)),
+                       "autotune_iters_per_candidate": args.tune_iters, "iteration_cap": args.batch_cap},
+            "wall_s": wall, "total_iters": total_iters,
+            "converged_handles": sum(1 for c in conv_at if c is not None),
+            "instances_converged": len(tt),
+            "time_to_tol_s": {"median": float(np.median(tt)) if tt else None,
+                              "max": float(max(tt)) if tt else None},
+            "cta_caps": {"min": min(caps), "max": max(caps), "distinct": len(set(caps))},
+            "per_instance": per_inst, "generation_seconds": t_gen}
+
+
 def run_reference(args, rank):
     """The FP64 CPU oracle on the same workload, bounded per step."""
     if rank != 0:
@@ -572,6 +663,12 @@ def main():
     ap.add_argument("--large-fp8", dest="large_fp8", action="store_true",
                     help="n=3e5 k=64 FP8 Block-SVRG AdaptGrow (own JSON line)")
     ap.add_argument("--large-n", dest="large_n", type=int, default=300000)
+    ap.add_argument("--batch", action="store_true",
+                    help="64 instances x 4 restarts, BF16, Piecewise AdaGrad (own JSON line)")
+    ap.add_argument("--batch-count", dest="batch_count", type=int, default=64)
+    ap.add_argument("--restarts", type=int, default=4)
+    ap.add_argument("--tune-iters", dest="tune_iters", type=int, default=10)
+    ap.add_argument("--batch-cap", dest="batch_cap", type=int, default=3000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -582,6 +679,9 @@ def main():
         return
     if args.large_fp8:
         print(json.dumps(run_large_fp8(args)), flush=True)
+        return
+    if args.batch:
+        print(json.dumps(run_batch(args)), flush=True)
         return
     if args.impl == "reference":
         out = run_reference(args, rank)

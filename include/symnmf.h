@@ -217,12 +217,28 @@ int symnmf_hparams_default(int32_t method, symnmf_hparams *hp);
  * SYMNMF_CONVERGED when the rule holds; the handle's H is then the certified
  * iterate H_t.  stats (host) may be NULL. */
 int symnmf_step(symnmf_t h, const symnmf_hparams *hp, int32_t iters, symnmf_stats *stats);
-/* Step count handles together: each iteration of every handle is launched
- * back to back on each handle's own stream, sharing one host loop.  hps and
+/* Step count handles together: each iteration of every live handle is
+ * launched on the handle's own stream before any of them is checked, so
+ * the handles' kernels overlap on the GPU; one host loop.  hps and
  * outs are arrays of count (outs may be NULL).  Returns the first error, or
  * SYMNMF_OK; per-handle convergence is in outs[i].converged. */
 int symnmf_batch_step(symnmf_t *hs, int32_t count, const symnmf_hparams *hps, int32_t iters,
                       symnmf_stats *outs);
+/* Cap the CTAs of the handle's tensor-core launches (0 = one per SM, the
+ * default).  Several handles with small caps on different streams run
+ * their iterations side by side (batching: symnmf_batch_step).  This
+ * library's scheduling knob; the paper runs one solve at a time. */
+int symnmf_set_ctas(symnmf_t h, int32_t ctas);
+/* The CTA count the handle's launches use (host). */
+int symnmf_get_ctas(symnmf_t h, int32_t *ctas);
+/* Autotune the CTA caps of a batch of handles (each on its own stream):
+ * tries every handle on all SMs, then shares m * SMs * w_i / sum(w) for
+ * m = 1, 2, 4 (w_i = bytes of S the handle streams per iteration), each
+ * for iters real iterations of symnmf_batch_step (they advance the solves),
+ * and keeps the schedule with the most iterations per second.  ctas_out
+ * (host, count entries, may be NULL) receives the chosen caps. */
+int symnmf_batch_autotune(symnmf_t *hs, int32_t count, const symnmf_hparams *hps, int32_t iters,
+                          int32_t *ctas_out);
 /* Time every product-kernel launch (the S H stream, the dominant kernel)
  * with a CUDA event pair on the handle's stream.  enable != 0 starts a new
  * accumulation; enable == 0 stops recording. */

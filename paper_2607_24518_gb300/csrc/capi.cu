@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -90,6 +91,7 @@ struct symnmf_ctx {
   size_t prof_used = 0;                // events used (2 per launch)
   double prof_bytes = 0.0;
   int64_t prof_kernels = 0;  // kernels launched by the solver loop while profiling
+  int ctas = 0;              // CTA cap of the tensor-core launches (0: all SMs)
 };
 
 namespace {
@@ -376,7 +378,8 @@ int prod(symnmf_t h, const int *row_list, int n_rows, const int *col_list, int n
   if (tc) {
     a.nsplit = 1;
     lay->nsplit = 1;
-    e = launch_step_tc(a, fuse, h->tile_cnt, h->stream, h->num_sms, &lay->skG, h->dev_err);
+    const int sms = (h->ctas > 0 && h->ctas < h->num_sms) ? h->ctas : h->num_sms;
+    e = launch_step_tc(a, fuse, h->tile_cnt, h->stream, sms, &lay->skG, h->dev_err);
   } else {
     e = launch_prod_simt(a, h->stream);
   }
@@ -535,8 +538,9 @@ symnmf_record to_record(const DevRecord &d, double phi) {
   return r;
 }
 
-// copy device records [h->copied_upto, upto) into the host trace
-int sync_records(symnmf_t h, int64_t upto, const std::vector<double> &phis) {
+// enqueue the copy of device records [h->copied_upto, upto) and of the
+// device error word to the host (no wait)
+int enqueue_records(symnmf_t h, int64_t upto) {
   const int64_t from = h->copied_upto;
   if (upto <= from) return SYMNMF_OK;
   int64_t a = from;
@@ -548,6 +552,13 @@ int sync_records(symnmf_t h, int64_t upto, const std::vector<double> &phis) {
     a += len;
   }
   CK(cudaMemcpyAsync(h->host_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  return SYMNMF_OK;
+}
+
+// wait for enqueue_records and append the records to the host trace
+int finish_records(symnmf_t h, int64_t upto, const std::vector<double> &phis) {
+  const int64_t from = h->copied_upto;
+  if (upto <= from) return SYMNMF_OK;
   CK(cudaStreamSynchronize(h->stream));
   if (h->host_err[0] != 0)
     return fail(h, SYMNMF_ERR_TIMEOUT,
@@ -559,6 +570,13 @@ int sync_records(symnmf_t h, int64_t upto, const std::vector<double> &phis) {
   }
   h->copied_upto = upto;
   return SYMNMF_OK;
+}
+
+// copy device records [h->copied_upto, upto) into the host trace
+int sync_records(symnmf_t h, int64_t upto, const std::vector<double> &phis) {
+  int rc = enqueue_records(h, upto);
+  if (rc) return rc;
+  return finish_records(h, upto, phis);
 }
 
 int median_g2(symnmf_t h, double *out) {
@@ -602,16 +620,27 @@ void fill_stats(symnmf_t h, symnmf_stats *st) {
   st->resets = h->ctrl.resets;
 }
 
-// one iteration plus its check; returns OK, CONVERGED or an error
-int iterate_once(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &phis) {
+// first half of an iteration: launch it and, when its records are due on
+// the host (a check, or a ring about to wrap), enqueue their copy
+int iterate_launch(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &phis) {
   const int64_t t = h->ctrl.t;
   if (t == 0 && h->copied_upto == 0 && h->trace.empty())
     h->ctrl.phi = hp->method == SYMNMF_BLOCK_SVRG_ADAPTGROW ? hp->phi0 : 1.0;
   phis.push_back(h->ctrl.phi);
   int rc = run_iteration(h, hp, t);
   if (rc) return rc;
+  if (t % hp->check_interval == 0 || t + 1 - h->copied_upto >= kRing / 2)
+    return enqueue_records(h, t + 1);
+  return SYMNMF_OK;
+}
+
+// second half: the check (Eq. 11 and the method's control); returns OK,
+// CONVERGED or an error
+int iterate_finish(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &phis) {
+  const int64_t t = h->ctrl.t;
+  int rc;
   if (t % hp->check_interval == 0) {
-    if ((rc = sync_records(h, t + 1, phis))) return rc;
+    if ((rc = finish_records(h, t + 1, phis))) return rc;
     phis.clear();
     symnmf_record &rec = h->trace.back();
     if (rec.nonfinite > 0) {
@@ -639,11 +668,18 @@ int iterate_once(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &phis
     }
     if (o.reset && (rc = apply_reset(h, hp))) return rc;
   } else if (t + 1 - h->copied_upto >= kRing / 2) {
-    if ((rc = sync_records(h, t + 1, phis))) return rc;
+    if ((rc = finish_records(h, t + 1, phis))) return rc;
     phis.clear();
   }
   h->ctrl.t = t + 1;
   return SYMNMF_OK;
+}
+
+// one iteration plus its check; returns OK, CONVERGED or an error
+int iterate_once(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &phis) {
+  int rc = iterate_launch(h, hp, phis);
+  if (rc) return rc;
+  return iterate_finish(h, hp, phis);
 }
 
 }  // namespace
@@ -1001,10 +1037,20 @@ int symnmf_batch_step(symnmf_t *hs, int32_t count, const symnmf_hparams *hps, in
     }
   }
   for (int32_t it = 0; it < iters; ++it) {
+    // every live handle's iteration is launched before any check waits, so
+    // one handle's check does not hold back the others' launches
+    for (int32_t i = 0; i < count; ++i) {
+      if (!live[i]) continue;
+      const int rc = iterate_launch(hs[i], &hps[i], phis[i]);
+      if (rc) {
+        live[i] = 0;
+        if (!first_err) first_err = rc;
+      }
+    }
     bool any = false;
     for (int32_t i = 0; i < count; ++i) {
       if (!live[i]) continue;
-      const int rc = iterate_once(hs[i], &hps[i], phis[i]);
+      const int rc = iterate_finish(hs[i], &hps[i], phis[i]);
       if (rc == SYMNMF_CONVERGED) {
         live[i] = 0;
       } else if (rc) {
@@ -1027,6 +1073,66 @@ int symnmf_batch_step(symnmf_t *hs, int32_t count, const symnmf_hparams *hps, in
     if (outs) fill_stats(hs[i], &outs[i]);
   }
   return first_err;
+}
+
+int symnmf_set_ctas(symnmf_t h, int32_t ctas) {
+  if (!h || ctas < 0) return SYMNMF_ERR_INVALID;
+  h->ctas = ctas;
+  return SYMNMF_OK;
+}
+
+int symnmf_get_ctas(symnmf_t h, int32_t *ctas) {
+  if (!h || !ctas) return SYMNMF_ERR_INVALID;
+  *ctas = (h->ctas > 0 && h->ctas < h->num_sms) ? h->ctas : h->num_sms;
+  return SYMNMF_OK;
+}
+
+int symnmf_batch_autotune(symnmf_t *hs, int32_t count, const symnmf_hparams *hps, int32_t iters,
+                          int32_t *ctas_out) {
+  if (!hs || !hps || count < 1 || iters < 1) return SYMNMF_ERR_INVALID;
+  for (int32_t i = 0; i < count; ++i)
+    if (!hs[i]) return SYMNMF_ERR_INVALID;
+  const int sms = std::max(1, hs[0]->num_sms);
+  std::vector<double> w(count);
+  double W = 0.0;
+  for (int32_t i = 0; i < count; ++i) {
+    w[i] = (double)hs[i]->n * (double)hs[i]->n * (double)esize(hs[i]->dtype);
+    W += w[i];
+  }
+  // schedule m = 0: every handle on all SMs; m > 0: handle i gets a share
+  // m * sms * w_i / W of the SMs (at least one CTA), so that m = 1 fills
+  // the GPU once if all handles stream at the same time
+  const double ms[] = {0.0, 1.0, 2.0, 4.0};
+  double best_rate = -1.0;
+  std::vector<int32_t> best(count, 0), cur(count, 0);
+  std::vector<symnmf_stats> st(count);
+  for (double m : ms) {
+    for (int32_t i = 0; i < count; ++i) {
+      cur[i] = (m == 0.0)
+                   ? 0
+                   : (int32_t)std::min<double>(sms, std::max(1.0, std::ceil(m * sms * w[i] / W)));
+      hs[i]->ctas = cur[i];
+    }
+    int64_t before = 0, after = 0;
+    for (int32_t i = 0; i < count; ++i) before += hs[i]->ctrl.t;
+    if (cudaDeviceSynchronize() != cudaSuccess) return SYMNMF_ERR_CUDA;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int rc = symnmf_batch_step(hs, count, hps, iters, st.data());
+    if (cudaDeviceSynchronize() != cudaSuccess) return SYMNMF_ERR_CUDA;
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rc < 0) return rc;
+    for (int32_t i = 0; i < count; ++i) after += hs[i]->ctrl.t;
+    const double rate = (double)(after - before) / std::max(el, 1e-9);
+    if (rate > best_rate) {
+      best_rate = rate;
+      best = cur;
+    }
+  }
+  for (int32_t i = 0; i < count; ++i) {
+    hs[i]->ctas = best[i];
+    if (ctas_out) ctas_out[i] = best[i] > 0 ? best[i] : sms;
+  }
+  return SYMNMF_OK;
 }
 
 int symnmf_set_profiling(symnmf_t h, int32_t enable) {

@@ -90,6 +90,9 @@ def _load():
         "symnmf_batch_step": [P(vp), i32, P(symnmf_hparams), i32, P(symnmf_stats)],
         "symnmf_get_trace": [vp, P(symnmf_record), i64, P(i64)],
         "symnmf_set_profiling": [vp, i32],
+        "symnmf_set_ctas": [vp, i32],
+        "symnmf_get_ctas": [vp, P(i32)],
+        "symnmf_batch_autotune": [P(vp), i32, P(symnmf_hparams), i32, P(i32)],
         "symnmf_get_profile": [vp, P(dbl), P(i64), P(dbl), P(i64)],
         "symnmf_state_bytes": [vp, P(C.c_size_t)],
         "symnmf_get_state": [vp, vp, C.c_size_t],
@@ -119,7 +122,8 @@ DECLARED = [
     "symnmf_get_impl", "symnmf_set_H", "symnmf_get_H", "symnmf_get_buffer", "symnmf_set_buffer",
     "symnmf_get_ctrl", "symnmf_set_ctrl", "symnmf_grad", "symnmf_objective",
     "symnmf_hparams_default", "symnmf_step", "symnmf_batch_step", "symnmf_get_trace",
-    "symnmf_set_profiling", "symnmf_get_profile",
+    "symnmf_set_profiling", "symnmf_get_profile", "symnmf_set_ctas", "symnmf_get_ctas",
+    "symnmf_batch_autotune",
     "symnmf_state_bytes", "symnmf_get_state", "symnmf_set_state", "symnmf_last_error",
     "symnmf_status_string", "symnmf_splitmix64", "symnmf_sample_blocks",
     "symnmf_controller_check", "symnmf_objective_noalloc",
@@ -289,6 +293,25 @@ def symnmf_get_trace(h, max_records=None):
     arr = (symnmf_record * max(1, m))()
     _check(LIB.symnmf_get_trace(h, arr, m, C.byref(cnt)), h)
     return list(arr)[:m]
+
+
+def symnmf_set_ctas(h, ctas):
+    return _check(LIB.symnmf_set_ctas(h, ctas), h)
+
+
+def symnmf_get_ctas(h):
+    v = C.c_int32()
+    _check(LIB.symnmf_get_ctas(h, C.byref(v)), h)
+    return v.value
+
+
+def symnmf_batch_autotune(hs, hps, iters):
+    """Chosen CTA caps (list) after autotuning the batch (advances the solves)."""
+    arr = (C.c_void_p * len(hs))(*[h.value if isinstance(h, C.c_void_p) else h for h in hs])
+    hp_arr = (symnmf_hparams * len(hs))(*hps)
+    out = (C.c_int32 * len(hs))()
+    _check(LIB.symnmf_batch_autotune(arr, len(hs), hp_arr, iters, out))
+    return list(out)
 
 
 def symnmf_set_profiling(h, enable):

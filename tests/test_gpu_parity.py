@@ -338,3 +338,43 @@ def test_full_size_sampled_rows_n20000(L):
         ref = 4.0 * (H64[rows] @ gram - Srows @ H64)
         got = G.double().cpu().numpy()[rows]
         assert O.rel_err(got, ref) < REL_FP32
+
+
+def test_batch_step_caps_and_autotune(L):
+    """symnmf_batch_step over handles on their own streams matches stepping
+    each alone; a CTA cap changes only the stream-K split (FP32 sums in
+    another order); the autotuner leaves caps in range and advances every
+    solve by 4 x its trial iterations."""
+    sizes = [(700, 8), (1000, 16), (1500, 32)]
+    probs = [problem(n, k, seed=n) for n, k in sizes]
+    hp = L.symnmf_hparams_default(L.PIECEWISE_ADAGRAD)
+    hs = []
+    streams = []
+    for (n, k), (S_t, _, H0_t, _) in zip(sizes, probs):
+        st = torch.cuda.Stream()
+        h = L.symnmf_create(S_t, n, k, L.F32)
+        L.symnmf_set_stream(h, st)
+        L.symnmf_set_H(h, H0_t)
+        hs.append(h)
+        streams.append(st)
+    try:
+        L.symnmf_set_ctas(hs[1], 7)
+        assert L.symnmf_get_ctas(hs[1]) == 7
+        L.symnmf_batch_step(hs, [hp] * 3, 30)
+        for (n, k), (S_t, _, H0_t, _), h in zip(sizes, probs, hs):
+            with Handle(L, S_t, n, k, L.F32) as solo:
+                L.symnmf_set_H(solo.h, H0_t)
+                L.symnmf_step(solo.h, hp, 30)
+                ref = solo.get()
+            out = torch.empty(n, k, dtype=torch.float32, device=DEV)
+            L.symnmf_get_H(h, out)
+            assert O.rel_err(out.double().cpu().numpy(), ref) < 1e-5
+        caps = L.symnmf_batch_autotune(hs, [hp] * 3, 5)
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        assert all(1 <= c <= nsm for c in caps)
+        for h, c in zip(hs, caps):
+            assert L.symnmf_get_ctas(h) == c
+            assert L.symnmf_get_ctrl(h).t == 30 + 4 * 5
+    finally:
+        for h in hs:
+            L.symnmf_destroy(h)
