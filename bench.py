@@ -51,12 +51,13 @@ KERNEL_SOURCES = ("k_prod_tc.cu", "tc_ptx.cuh", "epi_common.cuh", "symnmf_intern
 
 def alg_bytes_full_step(n, k, dt, method):
     """Algorithmic DRAM bytes of one full fused step: S once, plus the n x k
-    state: H_t and G read, H_{t+1}, G and g written (RMSprop adds m read and
-    written), the hi/lo MMA copy of H read once and written once (FP32 also
+    state: H_t and G read, H_{t+1} and G written (RMSprop adds m read and
+    written; the gradient g is written only at check iterations and is not
+    counted), the hi/lo MMA copy of H read once and written once (FP32 also
     its bf16 copy); FP8 adds the tile scales."""
     nt = -(-n // 128)
     b = n * n * ESIZE[dt]
-    b += 20 * n * k + (8 * n * k if method == 1 else 0)
+    b += 16 * n * k + (8 * n * k if method == 1 else 0)
     b += 2 * (2 * k * n * BT_ESIZE[dt])
     if dt == "f32":
         b += 2 * (max(k, 16) * n * 2)  # bf16 copy of H for the S_lo H product

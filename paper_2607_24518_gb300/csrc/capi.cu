@@ -422,7 +422,9 @@ bool is_full(symnmf_t h, const symnmf_hparams *hp, int64_t t) {
   return true;
 }
 
-int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t) {
+// need_g: also write the gradient buffer g (read by the Piecewise reset at
+// checks and by symnmf_get_buffer after a call)
+int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t, bool need_g) {
   const int cur = h->cur, nxt = 1 - cur;
   const bool full = is_full(h, hp, t);
   EpiArgs e = base_epi(h, hp);
@@ -431,7 +433,7 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t) {
   e.bt_fmt = h->bt_fmt;
   e.gram_part = h->gram_part[nxt];
   e.slots = h->slots;
-  e.gout = h->g;
+  e.gout = need_g ? h->g : nullptr;
   e.update = 1;
   int rc;
   bool fused_done = false;
@@ -622,12 +624,12 @@ void fill_stats(symnmf_t h, symnmf_stats *st) {
 
 // first half of an iteration: launch it and, when its records are due on
 // the host (a check, or a ring about to wrap), enqueue their copy
-int iterate_launch(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &phis) {
+int iterate_launch(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &phis, bool last) {
   const int64_t t = h->ctrl.t;
   if (t == 0 && h->copied_upto == 0 && h->trace.empty())
     h->ctrl.phi = hp->method == SYMNMF_BLOCK_SVRG_ADAPTGROW ? hp->phi0 : 1.0;
   phis.push_back(h->ctrl.phi);
-  int rc = run_iteration(h, hp, t);
+  int rc = run_iteration(h, hp, t, last || t % hp->check_interval == 0);
   if (rc) return rc;
   if (t % hp->check_interval == 0 || t + 1 - h->copied_upto >= kRing / 2)
     return enqueue_records(h, t + 1);
@@ -676,8 +678,8 @@ int iterate_finish(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &ph
 }
 
 // one iteration plus its check; returns OK, CONVERGED or an error
-int iterate_once(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &phis) {
-  int rc = iterate_launch(h, hp, phis);
+int iterate_once(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &phis, bool last) {
+  int rc = iterate_launch(h, hp, phis, last);
   if (rc) return rc;
   return iterate_finish(h, hp, phis);
 }
@@ -1010,7 +1012,7 @@ int symnmf_step(symnmf_t h, const symnmf_hparams *hp, int32_t iters, symnmf_stat
   std::vector<double> phis;
   rc = SYMNMF_OK;
   for (int32_t i = 0; i < iters; ++i) {
-    rc = iterate_once(h, hp, phis);
+    rc = iterate_once(h, hp, phis, i + 1 == iters);
     if (rc) break;
   }
   if (rc == SYMNMF_OK || rc == SYMNMF_CONVERGED) {
@@ -1041,7 +1043,7 @@ int symnmf_batch_step(symnmf_t *hs, int32_t count, const symnmf_hparams *hps, in
     // one handle's check does not hold back the others' launches
     for (int32_t i = 0; i < count; ++i) {
       if (!live[i]) continue;
-      const int rc = iterate_launch(hs[i], &hps[i], phis[i]);
+      const int rc = iterate_launch(hs[i], &hps[i], phis[i], it + 1 == iters);
       if (rc) {
         live[i] = 0;
         if (!first_err) first_err = rc;

@@ -636,6 +636,35 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       }
       epi = (b0 == b1);
     }
+    // the tile's first CTA, when every other CTA sharing the tile has
+    // already left its partial: finish here without storing its own
+    if (!epi && a.fused && b == b0) {
+      if (ft == 0) {
+        const int arrived = *reinterpret_cast<volatile int *>(&a.tile_cnt[tp]);
+        const int last = (arrived == (int)(b1 - b0));
+        if (last) a.tile_cnt[tp] = 0;
+        *reinterpret_cast<volatile int *>(sflag) = last;
+      }
+      fold_bar();
+      if (*reinterpret_cast<volatile int *>(sflag)) {
+        __threadfence();
+        // partials added in CTA order after this CTA's own (b == b0)
+        for (int64_t bb = b0 + 1; bb <= b1; ++bb) {
+          const float4 *src =
+              reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP);
+#pragma unroll
+          for (int c4 = 0; c4 < KP / 4; ++c4) {
+            const float4 v = __ldcg(src + c4);
+            p[4 * c4 + 0] += v.x;
+            p[4 * c4 + 1] += v.y;
+            p[4 * c4 + 2] += v.z;
+            p[4 * c4 + 3] += v.w;
+          }
+        }
+        epi = 1;
+      }
+      fold_bar();  // sflag is read before it is reused
+    }
     if (!epi) {
       float *dst = a.out + ((int64_t)(b + tp) * 128 + row) * KP;
 #pragma unroll
