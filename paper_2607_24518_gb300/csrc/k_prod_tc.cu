@@ -104,7 +104,8 @@ struct Cfg {
   // accumulator columns per part read before one wait when folding
   static constexpr int FOLD_CW = F32 ? 8 : (KP == 64 ? 16 : 32);
   static constexpr uint32_t EPI_FLOATS = 128 * (KP + 1) + KP * KP;
-  static constexpr uint32_t EPI_BYTES = EPI_FLOATS * 4 + 512;
+  // + FP8: a ring of 256 unit scales after the epilogue scratch
+  static constexpr uint32_t EPI_BYTES = EPI_FLOATS * 4 + 512 + (F8 ? 1024 : 0);
   static constexpr uint32_t BAR_BYTES = 512;
   static constexpr uint32_t BUDGET = 232448u - 1024u - BAR_BYTES - EPI_BYTES;
   static constexpr int STAGES = (BUDGET / STAGE) < 8u ? (int)(BUDGET / STAGE) : 8;
@@ -602,7 +603,7 @@ template <int DT, int KP>
 __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, uint64_t *full,
                             uint64_t *empty, uint64_t *afull, uint64_t *aempty, uint64_t *tfull,
                             uint64_t *tempty, const Hand &hd, int *sflag,
-                            volatile int *abort_flag, const Segs &sg, int b) {
+                            volatile int *abort_flag, const Segs &sg, int b, float *sring) {
   using C = Cfg<DT, KP>;
   constexpr int STAGES = C::STAGES;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -625,7 +626,60 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     ok = false;
   };
   // hand the finished segment of tile tp over (or leave a partial)
+  // hand a tile segment over to the epilogue warps: epi 0 (another CTA
+  // finishes the tile), 1 (P in TMEM buffer pb, stored from p), 2 (the
+  // epilogue warps add the partial slots)
+  auto handoff = [&](int epi) {
+    if (!warp_wait_idle(&hd.pempty[pb], pph[pb] ^ 1, abort_flag)) {
+      fail(7);
+      return;
+    }
+    fence_after();
+    if (epi == 1) {
+      const uint32_t tb = tmem_base + lane_off + C::PB0 + (uint32_t)(pb * KP);
+#pragma unroll
+      for (int cc = 0; cc < KP; cc += 8) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = p[cc + j];
+        tmem_st8(tb + cc, v);
+      }
+      tmem_wait_st();
+    }
+    if (ft == 0) hd.pflag[pb] = epi;
+    fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&hd.pfull[pb]);
+    pph[pb] ^= 1;
+    pb ^= 1;
+  };
+  // A partial left for another CTA is published (fence, arrival count)
+  // some folds later, once its stores have drained: a fence right behind
+  // them, with HBM saturated, stalls the folders long enough to drain the
+  // ring.  Whoever arrives last still finishes the tile.
+  constexpr int kDefer = 8;
+  int pend_tp = -1, pend_cd = 0;
+  int64_t pend_b0 = 0, pend_b1 = 0;
+  auto publish_pending = [&]() {
+    const int tp = pend_tp;
+    pend_tp = -1;
+    __threadfence();
+    fold_bar();
+    if (ft == 0) {
+      const int old = atomicAdd(&a.tile_cnt[tp], 1);
+      const int last = (old == (int)(pend_b1 - pend_b0));
+      if (last) a.tile_cnt[tp] = 0;
+      *reinterpret_cast<volatile int *>(sflag) = last;
+    }
+    fold_bar();
+    const int epi = *reinterpret_cast<volatile int *>(sflag) ? 2 : 0;
+    if (epi) __threadfence();
+    fold_bar();  // sflag is read before it is reused
+    handoff(epi);
+  };
+  // hand the finished segment of tile tp over (or leave a partial)
   auto finish_segment = [&](int tp) {
+    if (pend_tp >= 0) publish_pending();
     int64_t b0 = b, b1 = b;
     int epi = 0;
     if (a.fused) {
@@ -671,107 +725,52 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       for (int cc = 0; cc < KP; cc += 4)
         reinterpret_cast<float4 *>(dst + cc)[0] = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
       if (a.fused) {
-        __threadfence();
-        fold_bar();
-        if (ft == 0) {
-          const int old = atomicAdd(&a.tile_cnt[tp], 1);
-          const int last = (old == (int)(b1 - b0));
-          if (last) a.tile_cnt[tp] = 0;
-          *reinterpret_cast<volatile int *>(sflag) = last;
-        }
-        fold_bar();
-        // last to arrive: the tile's partials are added in CTA order, here
-        // for a few sharers, else by the epilogue warps while this CTA
-        // keeps streaming
-        epi = *reinterpret_cast<volatile int *>(sflag) ? 2 : 0;
-        if (epi) __threadfence();
-        if (epi && b1 - b0 < 4) {
-#pragma unroll
-          for (int c = 0; c < KP; ++c) p[c] = 0.f;
-          for (int64_t bb = b0; bb <= b1; ++bb) {
-            const float4 *src =
-                reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP);
-#pragma unroll
-            for (int c4 = 0; c4 < KP / 4; ++c4) {
-              const float4 v = __ldcg(src + c4);
-              p[4 * c4 + 0] += v.x;
-              p[4 * c4 + 1] += v.y;
-              p[4 * c4 + 2] += v.z;
-              p[4 * c4 + 3] += v.w;
-            }
-          }
-          epi = 1;
-        }
+        pend_tp = tp;
+        pend_b0 = b0;
+        pend_b1 = b1;
+        pend_cd = kDefer;
       }
-    }
-    if (a.fused) {
-      if (!warp_wait_idle(&hd.pempty[pb], pph[pb] ^ 1, abort_flag)) {
-        fail(7);
-        return;
-      }
-      fence_after();
-      if (epi == 1) {
-        const uint32_t tb = tmem_base + lane_off + C::PB0 + (uint32_t)(pb * KP);
-#pragma unroll
-        for (int cc = 0; cc < KP; cc += 8) {
-          float v[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = p[cc + j];
-          tmem_st8(tb + cc, v);
-        }
-        tmem_wait_st();
-      }
-      if (ft == 0) hd.pflag[pb] = epi;
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&hd.pfull[pb]);
-      pph[pb] ^= 1;
-      pb ^= 1;
+    } else if (a.fused) {
+      handoff(epi);
     }
 #pragma unroll
     for (int c = 0; c < KP; ++c) p[c] = 0.f;
   };
   // fold accumulator chain f (stage-sized chunks [f FOLD, (f+1) FOLD))
-  // FP8: the scale of each unit (S tile scale over the H tile factor),
-  // loaded one fold ahead; (ntp, nci, nu, nsi) walk this CTA's units
-  int64_t nu = sg.hi[0] > sg.lo[0] ? sg.lo[0] : sg.lo[1];
-  int nsi = sg.hi[0] > sg.lo[0] ? 0 : 1;
-  int ntp = (int)(nu / a.n_cols), nci = (int)(nu % a.n_cols);
-  auto load_scale = [&]() -> float {
-    if (nu >= sg.hi[nsi]) return 1.f;
-    int cpos = nci;
-    if (nsi == 1) {
-      cpos += sg.rot;
-      if (cpos >= a.n_cols) cpos -= a.n_cols;
-    }
-    const int rt = a.row_list ? a.row_list[ntp] : ntp;
-    const int ct = a.col_list ? a.col_list[cpos] : cpos;
-    return a.sS[(int64_t)rt * a.ld_sS + ct] * a.deq[ct];
+  // FP8: the scale of each unit (S tile scale over the H tile factor) comes
+  // from a shared ring of 2 x 128 entries in this CTA's unit order.  The
+  // 128 folder threads load block j + 2 together at the end of block j and
+  // store it 128 folds later, so no fold waits on these loads.
+  const int64_t len0 = sg.hi[0] - sg.lo[0];
+  const int64_t nunits = len0 + (sg.hi[1] - sg.lo[1]);
+  auto scale_of = [&](int64_t i) -> float {
+    if (i >= nunits) return 1.f;
+    const int si = i < len0 ? 0 : 1;
+    const int64_t u = i < len0 ? sg.lo[0] + i : sg.lo[1] + (i - len0);
+    const int tp = (int)(u / a.n_cols), ci = unit_col(a, sg, u, si);
+    const int rt = a.row_list ? a.row_list[tp] : tp;
+    const int ct = a.col_list ? a.col_list[ci] : ci;
+    return __ldg(a.sS + (int64_t)rt * a.ld_sS + ct) * __ldg(a.deq + ct);
   };
-  auto advance_unit = [&]() {
-    ++nu;
-    if (++nci == a.n_cols) {
-      nci = 0;
-      ++ntp;
-    }
-    if (nsi == 0 && nu >= sg.hi[0]) {
-      nsi = 1;
-      nu = sg.lo[1];
-      ntp = (int)(nu / a.n_cols);
-      nci = (int)(nu % a.n_cols);
-    }
-  };
-  float sc_next = 1.f;
-  if constexpr (C::F8) sc_next = load_scale();
+  int64_t fcount = 0;  // units folded so far
+  float pre = 1.f;     // this thread's entry of the block two ahead
+  if constexpr (C::F8) {
+    sring[ft] = scale_of(ft);
+    fold_bar();
+    pre = scale_of(128 + ft);
+  }
   // fold accumulator chain f (stage-sized chunks [f FOLD, (f+1) FOLD)) of
   // segment si, which ends at unit Lhi
   auto fold = [&](int64_t f, int64_t Lhi, int si) {
     float sc = 1.f;
-    if constexpr (C::F8) {
-      // one unit per chain, visited in this CTA's order
-      sc = sc_next;
-      advance_unit();
-      sc_next = load_scale();
+    if constexpr (C::F8) {  // one unit per chain, in this CTA's order
+      sc = sring[fcount & 255];
+      if ((fcount & 127) == 127) {
+        sring[(((fcount >> 7) + 1) & 1) * 128 + ft] = pre;
+        fold_bar();
+        pre = scale_of(((fcount >> 7) + 2) * 128 + ft);
+      }
+      ++fcount;
     }
     if (!warp_wait(&tfull[acc], tph[acc], abort_flag)) {
       fail(5);
@@ -816,6 +815,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       const int64_t u = cend / C::SPU - 1;  // unit just completed
       if (u + 1 == Lhi || (u + 1) % a.n_cols == 0) finish_segment((int)(u / a.n_cols));
     }
+    if (pend_tp >= 0 && --pend_cd <= 0 && ok) publish_pending();
   };
 
   if constexpr (C::F32) {
@@ -897,6 +897,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       for (int64_t f = sg.lo[si] * C::SPU / C::FOLD; f < sg.hi[si] * C::SPU / C::FOLD && ok; ++f)
         fold(f, sg.hi[si], si);
   }
+  if (ok && pend_tp >= 0) publish_pending();
 }
 
 // -------------------------------------------------------------------- kernel
@@ -1105,7 +1106,7 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
   } else if (warp >= 10) {
     const Hand hd{pfull, pempty, pflag};
     folder_role<DT, KP>(a, tmem_base, smem, full, empty, afull, aempty, tfull, tempty, hd, sflag,
-                        abort_flag, sg, b);
+                        abort_flag, sg, b, reinterpret_cast<float *>(scratch + 64));
   } else {
     const Hand hd{pfull, pempty, pflag};
     epilogue_role<DT, KP>(a, e, tmem_base, Hs, Gs, scratch, hd, abort_flag, sg);
