@@ -182,6 +182,19 @@ def oracle_rate(S64, H0, method, eta, budget_s=15.0, min_iters=2, max_iters=None
     return it / el, it, el
 
 
+def aggregate_ranks(ms, iters, world, device):
+    """Replicas: the slowest rank's time and the iterations of all ranks
+    (one value per rank; no data-path collective exists)."""
+    if world <= 1:
+        return ms, iters
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    it_t = torch.tensor([iters], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(it_t)
+    return float(t.item()), int(it_t.item())
+
+
 def run_native(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -242,15 +255,7 @@ def run_native(args, rank, world, local_rank):
     L.symnmf_set_profiling(h, False)
     ck = clocks.stop() if clocks else None
     kernels_per_step = kernel_launches / max(1, prof_steps)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        it_t = torch.tensor([iters], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(it_t)
-        total_iters = int(it_t.item())
-    else:
-        total_iters = iters
+    ms, total_iters = aggregate_ranks(ms, iters, world, dev)
     impl = L.symnmf_get_impl(h)
 
     # end to end through the public API with host buffers: every e2e step

@@ -492,3 +492,32 @@ def test_gradient_rows_is_the_full_gradient_restricted():
     rows = np.array([0, 7, 128, 259])
     G = O.gradient(inst.S, H)
     np.testing.assert_allclose(O.gradient_rows(inst.S[rows], H, rows), G[rows], rtol=1e-13, atol=1e-12)
+
+
+def test_hparams_match_the_printed_anchors():
+    """Golden values: tests/golden/hparams_anchors.txt (appendix, Family 3;
+    Sec. 5.1 for Piecewise AdaGrad)."""
+    names = {"adagrad": O.ADAGRAD, "rmsprop": O.RMSPROP, "piecewise": O.PIECEWISE}
+    path = os.path.join(os.path.dirname(__file__), "golden", "hparams_anchors.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 6
+    for method, param, value in rows:
+        assert getattr(O.HParams.paper(names[method]), param) == float(value)
+
+
+def test_blocks_to_rows_example():
+    assert list(O.blocks_to_rows([0, 2], 4, 10)) == [0, 1, 2, 3, 8, 9]
+    assert list(O.blocks_to_rows([1], 4, 10)) == [4, 5, 6, 7]
+    assert len(O.blocks_to_rows([], 4, 10)) == 0
+
+
+def test_comparison_helpers():
+    # ||(3,4) - (0,0)|| / ||(0,0)|| falls back to the absolute norm 5
+    assert O.rel_err([3.0, 4.0], [0.0, 0.0]) == 5.0
+    assert abs(O.rel_err([1.0, 1.0], [1.0, 2.0]) - 1.0 / math.sqrt(5.0)) < 1e-15
+    rng = np.random.default_rng(3)
+    H = rng.random((20, 4))
+    assert O.factor_error(H[:, [2, 0, 3, 1]], H) < 1e-15
+    A = np.array([[0.0, 1.0], [2.0, 0.0]])
+    B = np.array([[0.0, 0.0], [2.0, 3.0]])
+    assert O.boundary_disagreement(A, B) == 2
