@@ -16,6 +16,7 @@ fusion or reordering:
 * projected gradient / KKT                                      (Sec. 4.1, Eqs. 5-6)
 * AND stopping rule, tau_g(n), stagnation with warm-up          (Sec. 4.1, Eqs. 7-11)
 * AdaGrad, RMSprop, Piecewise AdaGrad updates                   (Appendix, Family 3)
+* ADMM (H least-squares update, W = [H + U]_+, dual U)           (Appendix, Family 6)
 * Row-Stochastic SVRG, Block-SVRG AdaptGrow                     (Sec. 5.1; Appendix, Family 3)
 * SplitMix64 counter-based sampling of row blocks (Steele, Lea & Flood,
   OOPSLA 2014), partial Fisher-Yates selection
@@ -45,9 +46,9 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-ADAGRAD, RMSPROP, PIECEWISE, ROW_SVRG, BLOCK_SVRG = 0, 1, 2, 3, 4
+ADAGRAD, RMSPROP, PIECEWISE, ROW_SVRG, BLOCK_SVRG, ADMM = 0, 1, 2, 3, 4, 5
 METHOD_NAMES = {ADAGRAD: "adagrad", RMSPROP: "rmsprop", PIECEWISE: "piecewise",
-                ROW_SVRG: "row_svrg", BLOCK_SVRG: "block_svrg"}
+                ROW_SVRG: "row_svrg", BLOCK_SVRG: "block_svrg", ADMM: "admm"}
 
 # --------------------------------------------------------------------------
 # objective, gradient, projected gradient (Sec. 2, 2.1, 4.1)
@@ -189,6 +190,7 @@ class HParams:
     tau_stag: float = 1e-5
     growth_kkt_mult: float = 3.0
     seed: int = 0
+    rho: float = 500.0          # ADMM penalty
 
     @staticmethod
     def paper(method):
@@ -203,6 +205,8 @@ class HParams:
             return HParams(method=ROW_SVRG, eta=2.0, row_frac=0.5, snapshot_period=10, eps=1e-10)
         if method == BLOCK_SVRG:
             return HParams(method=BLOCK_SVRG, eta=2.0, phi0=0.5, snapshot_period=2, eps=1e-10)
+        if method == ADMM:
+            return HParams(method=ADMM, rho=500.0)
         raise ValueError(method)
 
 
@@ -377,10 +381,21 @@ class Solver:
         g[J] += 2.0 * (R.T @ H[I])
         return g
 
-    # ---- updates (Appendix, Family 3) -----------------------------------
+    # ---- updates (Appendix, Families 3 and 6) -----------------------------
     def apply_update(self, g):
         hp = self.hp
-        if hp.method == RMSPROP:
+        if hp.method == ADMM:
+            # Appendix, Family 6, Eqs. admm_H / admm_W / admm_U: W = self.H
+            # (the feasible factor the objective and the check track), the
+            # scaled dual U = self.A
+            W, U = self.H, self.A
+            rhs = 2.0 * (self.S @ W) + hp.rho * (W - U)
+            Mk = 2.0 * (W.T @ W) + hp.rho * np.eye(self.k)
+            Hn = np.linalg.solve(Mk, rhs.T).T          # rhs Mk^-1 (Mk symmetric)
+            Wn = np.maximum(Hn + U, 0.0)
+            self.A = U + Hn - Wn
+            self.H = Wn
+        elif hp.method == RMSPROP:
             self.A = hp.alpha * self.A + (1.0 - hp.alpha) * g * g
             self.M = hp.mu * self.M + hp.eta * g / (np.sqrt(self.A) + hp.eps)
             self.H = np.maximum(self.H - self.M, 0.0)

@@ -521,3 +521,45 @@ def test_comparison_helpers():
     A = np.array([[0.0, 1.0], [2.0, 0.0]])
     B = np.array([[0.0, 0.0], [2.0, 3.0]])
     assert O.boundary_disagreement(A, B) == 2
+
+
+# ------------------------------------------------------------ ADMM (Family 6)
+def test_admm_planted_solution_is_a_fixed_point():
+    """At S = W0 W0^T with U = 0: S W0 = W0 G, so the H-update returns W0,
+    W = [W0]_+ = W0 and U stays 0."""
+    W0, S = gen.planted_exact(60, 4, seed=2)
+    s = O.Solver(S, W0, O.HParams.paper(O.ADMM))
+    s.step()
+    np.testing.assert_allclose(s.H, W0, rtol=0, atol=1e-10)
+    assert np.max(np.abs(s.A)) < 1e-10
+
+
+def test_admm_h_update_is_the_least_squares_minimiser():
+    """The H-update minimises ||S - H W^T||^2 + (rho/2) ||H - W + U||^2
+    (Appendix, Family 6): checked against numpy's least-squares solver on
+    the stacked system, row by row."""
+    inst = gen.tpdm_groups(n=90, groups=3, T=600, q=0.05, seed=8)
+    rng = np.random.default_rng(4)
+    W = rng.random((90, 3))
+    U = -0.1 * rng.random((90, 3))
+    hp = O.HParams.paper(O.ADMM)
+    hp.rho = 7.0
+    s = O.Solver(inst.S, W, hp)
+    s.A = U.copy()
+    s.step()
+    # row i: min_h ||S_i - W h||^2 + (rho/2) ||h - (W_i - U_i)||^2
+    A = np.vstack([W, np.sqrt(hp.rho / 2.0) * np.eye(3)])
+    Hn = np.array([np.linalg.lstsq(A, np.concatenate([inst.S[i], np.sqrt(hp.rho / 2.0) * (W[i] - U[i])]),
+                                   rcond=None)[0] for i in range(90)])
+    Wn = np.maximum(Hn + U, 0.0)
+    np.testing.assert_allclose(s.H, Wn, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(s.A, U + Hn - Wn, rtol=1e-10, atol=1e-12)
+
+
+def test_admm_dual_stays_non_positive_and_w_non_negative():
+    """U' = U + H - [H + U]_+ = min(H + U, 0) <= 0, and W >= 0, at every step."""
+    inst = gen.corr_planted(n=120, groups=4, T=800, seed=6)
+    s = O.Solver(inst.S, gen.init_uniform(120, 4, 0.1, seed=6), O.HParams.paper(O.ADMM))
+    for _ in range(15):
+        s.step()
+        assert np.all(s.A <= 0.0) and np.all(s.H >= 0.0)
