@@ -35,14 +35,17 @@ METRIC = "fused SH-step iters/s, HBM GB/s vs peak; time-to-tol at n=1e5 BF16 vs 
 UNIT = "iters/s"
 
 WORKLOADS = {
-    # name: (generator, n, k, dtype, method, eta)
+    # name: (generator, n, k, dtype, method, eta (None: the method has none))
     "tpdm_n20000_k32_fp32_adagrad": ("tpdm", 20000, 32, "f32", 0, 2.0),
     "tpdm_n20000_k32_fp32_rmsprop": ("tpdm", 20000, 32, "f32", 1, 0.05),
     "tpdm_n20000_k32_bf16_adagrad": ("tpdm", 20000, 32, "bf16", 0, 2.0),
     "tpdm_n20000_k32_fp8_adagrad": ("tpdm", 20000, 32, "fp8", 0, 2.0),
+    "tpdm_n20000_k32_fp32_admm": ("tpdm", 20000, 32, "f32", 5, None),  # rho 500
     "corr_n100000_k32_fp32_adagrad": ("corr", 100000, 32, "f32", 0, 2.0),
     "corr_n100000_k32_bf16_adagrad": ("corr", 100000, 32, "bf16", 0, 2.0),
 }
+METHOD = {0: "adagrad", 1: "rmsprop", 2: "piecewise_adagrad", 3: "row_svrg",
+          4: "block_svrg_adaptgrow", 5: "admm"}
 ESIZE = {"f32": 4, "bf16": 2, "fp8": 1}
 # bytes per entry of the MMA copy of H (hi + lo pieces) for each storage type
 BT_ESIZE = {"f32": 4, "bf16": 2, "fp8": 1}
@@ -51,10 +54,10 @@ KERNEL_SOURCES = ("k_prod_tc.cu", "tc_ptx.cuh", "epi_common.cuh", "symnmf_intern
 
 def alg_bytes_full_step(n, k, dt, method):
     """Algorithmic DRAM bytes of one full fused step: S once, plus the n x k
-    state: H_t and G read, H_{t+1} and G written (RMSprop adds m read and
-    written; the gradient g is written only at check iterations and is not
-    counted), the hi/lo MMA copy of H read once and written once (FP32 also
-    its bf16 copy); FP8 adds the tile scales."""
+    state: H_t and G read, H_{t+1} and G written (ADMM: U in place of G;
+    RMSprop adds m read and written; the gradient g is written only at
+    check iterations and is not counted), the hi/lo MMA copy of H read once
+    and written once (FP32 also its bf16 copy); FP8 adds the tile scales."""
     nt = -(-n // 128)
     b = n * n * ESIZE[dt]
     b += 16 * n * k + (8 * n * k if method == 1 else 0)
@@ -167,7 +170,8 @@ def oracle_rate(S64, H0, method, eta, budget_s=15.0, min_iters=2, max_iters=None
     """Iterations/s of the FP64 oracle on the host cores (bounded sample)."""
     from oracle import symnmf_oracle as O
     hp = O.HParams.paper(method)
-    hp.eta = eta
+    if eta is not None:
+        hp.eta = eta
     hp.tau_g = 1e-30
     s = O.Solver(S64, H0, hp)
     s.step()  # warm-up (first touch of S)
@@ -228,7 +232,8 @@ def run_native(args, rank, world, local_rank):
     L.symnmf_set_stream(h, stream)
     if scales is not None:
         L.symnmf_set_tile_scales(h, scales, scales.shape[1])
-    hp = L.symnmf_hparams_default(method, eta=eta, tau_g=1e-30)  # never stop early: fixed work
+    over = {} if eta is None else {"eta": eta}
+    hp = L.symnmf_hparams_default(method, tau_g=1e-30, **over)  # never stop early: fixed work
     L.symnmf_set_H(h, H0_t)
     L.symnmf_step(h, hp, args.warmup)
     if world > 1:
@@ -329,8 +334,9 @@ def run_native(args, rank, world, local_rank):
             "dtype": {"f32": "f32", "bf16": "bf16", "fp8": "e4m3"}[dt]
                      + " storage, f32 accumulate, f64 reductions",
             "data": "synthetic (seeded TPDM / correlation generator)",
-            "config": {"workload": args.workload, "n": n, "k": k, "method": ["adagrad", "rmsprop"][method],
-                       "eta": eta, "storage": dt, "l2": "S larger than L2 (no flush needed)",
+            "config": {"workload": args.workload, "n": n, "k": k, "method": METHOD[method],
+                       "eta": eta, **({"rho": hp.rho} if method == 5 else {}),
+                       "storage": dt, "l2": "S larger than L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "product_impl": ["", "simt", "tcgen05"][impl]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -633,7 +639,8 @@ def run_reference(args, rank):
     if dt == "fp8":
         S64 = O.dequantize_fp8(*O.quantize_fp8(S64))
     hp = O.HParams.paper(method)
-    hp.eta = eta
+    if eta is not None:
+        hp.eta = eta
     hp.tau_g = 1e-30
     s = O.Solver(S64, H0_64, hp)
     for _ in range(args.warmup):

@@ -50,7 +50,10 @@ enum symnmf_method {
   SYMNMF_RMSPROP = 1,             /* v = a v + (1-a) g*g; m = mu m + eta g/(sqrt(v)+eps); H = [H - m]_+ */
   SYMNMF_PIECEWISE_ADAGRAD = 2,   /* AdaGrad + stagnation-triggered accumulator reset */
   SYMNMF_ROW_SVRG = 3,            /* fresh rows on sampled I, snapshot mu elsewhere   */
-  SYMNMF_BLOCK_SVRG_ADAPTGROW = 4 /* I x J block estimate, snapshot elsewhere, phi growth */
+  SYMNMF_BLOCK_SVRG_ADAPTGROW = 4, /* I x J block estimate, snapshot elsewhere, phi growth */
+  SYMNMF_ADMM = 5                  /* appendix, Family 6: H = (2 S W + rho (W - U)) (2 W^T W + rho I)^-1,
+                                      W = [H + U]_+, U += H - W; the handle's H is W, its
+                                      accumulator buffer holds U; f, E and the check use W */
 };
 
 enum symnmf_status {
@@ -97,6 +100,7 @@ typedef struct symnmf_hparams {
   double tau_stag;         /* stagnation threshold tau of Eq. 10, default 1e-5  */
   double growth_kkt_mult;  /* AdaptGrow grows only while KKT > mult * tau_g (3) */
   uint64_t seed;           /* sampling seed (SplitMix64 counter streams)        */
+  double rho;              /* ADMM penalty (default 500)                        */
 } symnmf_hparams;
 
 /* Scalar controller state carried between iterations (part of a checkpoint). */

@@ -59,6 +59,7 @@ struct symnmf_ctx {
   double *slots = nullptr, *chunk = nullptr;
   int nchunks = 1;
   float *gramI = nullptr, *gramJ = nullptr;
+  float *minv = nullptr;    // ADMM: (2 Gram_t + rho I)^-1
   int *dlists = nullptr;    // kStages x 4 x ntiles
   int *hlists = nullptr;    // pinned mirror
   cudaEvent_t stage_ev[kStages] = {};
@@ -143,7 +144,7 @@ void free_all(symnmf_t h) {
   }
   for (void *p : {(void *)h->A, (void *)h->M, (void *)h->mu, (void *)h->g, (void *)h->tmp,
                   (void *)h->P, (void *)h->Q, (void *)h->slots, (void *)h->chunk,
-                  (void *)h->gramI, (void *)h->gramJ, (void *)h->dlists, (void *)h->ring,
+                  (void *)h->gramI, (void *)h->gramJ, (void *)h->minv, (void *)h->dlists, (void *)h->ring,
                   (void *)h->hist, (void *)h->sel, (void *)h->dmed, (void *)h->dsum,
                   (void *)h->norm_parts, (void *)h->dev_err, (void *)h->counters, (void *)h->tile_cnt,
                   (void *)h->lvl1})
@@ -294,7 +295,8 @@ void ctrl_check(symnmf_ctrl *c, const symnmf_hparams *hp, int64_t n, int64_t t, 
 
 int validate_hp(const symnmf_hparams *hp) {
   if (!hp) return SYMNMF_ERR_INVALID;
-  if (hp->method < 0 || hp->method > 4) return SYMNMF_ERR_INVALID;
+  if (hp->method < 0 || hp->method > SYMNMF_ADMM) return SYMNMF_ERR_INVALID;
+  if (hp->method == SYMNMF_ADMM && !(hp->rho > 0)) return SYMNMF_ERR_INVALID;
   if (hp->check_interval < 1 || hp->snapshot_period < 1 || hp->warmup < 0)
     return SYMNMF_ERR_INVALID;
   if (hp->block_rows < kTileRows || hp->block_rows % kTileRows) return SYMNMF_ERR_INVALID;
@@ -411,6 +413,8 @@ EpiArgs base_epi(symnmf_t h, const symnmf_hparams *hp) {
   e.M = h->M;
   e.mu = h->mu;
   e.coef = 4.f;
+  e.rho = hp ? (float)hp->rho : 0.f;
+  e.minv = h->minv;
   return e;
 }
 
@@ -437,6 +441,11 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t, bool need_g) 
   e.update = 1;
   int rc;
   bool fused_done = false;
+  if (hp->method == SYMNMF_ADMM) {
+    // (2 W^T W + rho I)^-1 from the FP64 Gram of W = H_t (appendix, Family 6)
+    CK(launch_admm_minv(h->gram64[cur], h->k, h->kp, hp->rho, h->minv, h->stream));
+    count_kernels(h, 1);
+  }
   if (full) {
     e.mode = MODE_FULL;
     e.gram = h->gram32[cur];
@@ -707,7 +716,7 @@ const char *symnmf_status_string(int32_t s) {
 const char *symnmf_last_error(symnmf_t h) { return h ? h->err.c_str() : "null handle"; }
 
 int symnmf_hparams_default(int32_t method, symnmf_hparams *hp) {
-  if (!hp || method < 0 || method > 4) return SYMNMF_ERR_INVALID;
+  if (!hp || method < 0 || method > SYMNMF_ADMM) return SYMNMF_ERR_INVALID;
   std::memset(hp, 0, sizeof(*hp));
   hp->method = method;
   hp->check_interval = 10;
@@ -727,6 +736,7 @@ int symnmf_hparams_default(int32_t method, symnmf_hparams *hp) {
   hp->tau_stag = 1e-5;
   hp->growth_kkt_mult = 3.0;
   hp->seed = 0;
+  hp->rho = 500.0;
   if (method == SYMNMF_RMSPROP) {
     hp->eta = 0.05;
     hp->eps = 1e-8;
@@ -783,6 +793,7 @@ int symnmf_create_ld(const void *S, int64_t n, int64_t lds, int32_t k, int32_t d
   if (e == cudaSuccess) e = dalloc(&h->chunk, (size_t)h->nchunks * (4 + h->kp * h->kp));
   if (e == cudaSuccess) e = dalloc(&h->gramI, (size_t)h->kp * h->kp);
   if (e == cudaSuccess) e = dalloc(&h->gramJ, (size_t)h->kp * h->kp);
+  if (e == cudaSuccess) e = dalloc(&h->minv, (size_t)h->kp * h->kp);
   if (e == cudaSuccess) e = dalloc(&h->dlists, (size_t)kStages * 4 * h->ntiles);
   if (e == cudaSuccess) e = dalloc(&h->ring, (size_t)kRing + 1);
   if (e == cudaSuccess) e = dalloc(&h->hist, 2048);

@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(EpiArgs a) {
   // phase 1: issue every global load of this thread's elements
   float pv[EPT], qv[EPT], av[EPT], mv[EPT], uv[EPT];
   const bool rms = (a.method == SYMNMF_RMSPROP);
+  const bool admm = (a.method == SYMNMF_ADMM);
 #pragma unroll
   for (int i = 0; i < EPT; ++i) {
     const int e = tid + i * kEpiThreads;
@@ -221,7 +222,10 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(EpiArgs a) {
       if (a.gout) a.gout[gi] = g;
       if (a.gcaller) a.gcaller[(r0 + r) * a.k + c] = g;
       if (a.store_mu) a.mu[gi] = g;
-      if (a.update) {
+      if (a.update && admm) {
+        // ADMM right-hand-side row 2 (S W) + rho (W - U), finished below
+        hn = 2.f * pv[i] + a.rho * (h - av[i]);
+      } else if (a.update) {
         float x;
         if (rms) {
           const float v = a.alpha * av[i] + (1.f - a.alpha) * (g * g);
@@ -245,6 +249,40 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(EpiArgs a) {
     Hn[r][c] = hn;
   }
   __syncthreads();
+  if (a.update && admm) {
+    // H = rhs (2 W^T W + rho I)^-1, W' = [H + U]_+, U' = U + H - W'
+    // (appendix, Family 6)
+    float xv[EPT];
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = tid + i * kEpiThreads;
+      const int r = e / KP, c = e % KP;
+      float x = 0.f;
+      if (r < rows && c < a.k) {
+#pragma unroll 8
+        for (int d = 0; d < KP; ++d) x = fmaf(Hn[r][d], a.minv[d * KP + c], x);
+        x += av[i];
+      }
+      xv[i] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = tid + i * kEpiThreads;
+      const int r = e / KP, c = e % KP;
+      float w = 0.f;
+      if (r < rows && c < a.k) {
+        const int64_t gi = (r0 + r) * KP + c;
+        w = (xv[i] > 0.f) ? xv[i] : 0.f;
+        const float u = xv[i] - w;
+        a.A[gi] = u;
+        a.Hn[gi] = w;
+        sumA += u;
+      }
+      Hn[r][c] = w;
+    }
+    __syncthreads();
+  }
   if (a.update) tile_tail<KP>(Hn, r0, a.Btn, a.bt_fmt, a.ldb, a.gram_part, tile);
   const double s_tr = block_sum((double)tr, red);
   const double s_kkt = block_sum((double)kkt2, red);
@@ -493,6 +531,53 @@ __global__ void __launch_bounds__(256) reset_kernel(float *A, const float *g, co
   if (threadIdx.x == 0) slots[(int64_t)tile * kSlotStride + 2] = tot;
 }
 
+// ADMM (appendix, Family 6): the H-update solves H (2 W^T W + rho I) =
+// 2 S W + rho (W - U) row by row; every row shares the kp x kp matrix, so
+// its inverse is formed once per iteration here and the step's epilogue
+// multiplies each right-hand-side row by it.  M = 2 G + rho I is formed in
+// FP64 from the FP64 Gram of W = H_t, rounded to FP32 and inverted by
+// Gauss-Jordan elimination in place without pivoting (M is symmetric
+// positive definite, rho > 0): pivot p maps a_pp -> 1/a_pp,
+// a_pj -> a_pj/a_pp, a_ip -> -a_ip/a_pp and a_ij -> a_ij - a_ip a_pj/a_pp.
+// Two shared buffers alternate so one barrier per pivot suffices.  Entries
+// past k hold the identity, so the padded block of the inverse is the
+// identity and the padded columns of H stay zero.
+template <int KP>
+__global__ void __launch_bounds__(256) admm_minv_kernel(const double *gram64, int k, double rho,
+                                                        float *minv) {
+  // the next step kernel may start streaming S now; its epilogue warps wait
+  // for this grid (griddepcontrol.wait) before they read minv
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  // gram64 is written by the preceding reduction kernel
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  __shared__ float X[2][KP][KP + 1];
+  for (int e = threadIdx.x; e < KP * KP; e += blockDim.x) {
+    const int i = e / KP, j = e % KP;
+    float v = (i == j) ? 1.f : 0.f;
+    if (i < k && j < k) v = (float)(2.0 * gram64[e] + (i == j ? rho : 0.0));
+    X[0][i][j] = v;
+  }
+  __syncthreads();
+  for (int p = 0; p < KP; ++p) {
+    const float(*src)[KP + 1] = X[p & 1];
+    float(*dst)[KP + 1] = X[(p + 1) & 1];
+    const float d = 1.f / src[p][p];
+    for (int e = threadIdx.x; e < KP * KP; e += blockDim.x) {
+      const int i = e / KP, j = e % KP;
+      float v;
+      if (i == p) {
+        v = (j == p) ? d : src[p][j] * d;
+      } else {
+        const float f = src[i][p] * d;
+        v = (j == p) ? -f : fmaf(-f, src[p][j], src[i][j]);
+      }
+      dst[i][j] = v;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < KP * KP; e += blockDim.x) minv[e] = X[KP & 1][e / KP][e % KP];
+}
+
 }  // namespace
 
 #define KP_SWITCH(kp, ...)                              \
@@ -513,6 +598,21 @@ cudaError_t launch_epilogue(const EpiArgs &a, cudaStream_t s) {
     epilogue_kernel<KPV><<<a.ntiles, kEpiThreads, bytes, s>>>(a);
   });
   return cudaGetLastError();
+}
+
+cudaError_t launch_admm_minv(const double *gram64, int k, int kp, double rho, float *minv,
+                             cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  KP_SWITCH(kp, return cudaLaunchKernelEx(&cfg, admm_minv_kernel<KPV>, gram64, k, rho, minv));
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_prepare_tiles(const float *H, int64_t n, int k, int kp, void *Bt, int bt_fmt,

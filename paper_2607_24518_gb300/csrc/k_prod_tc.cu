@@ -291,20 +291,81 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
   };
   // tr(H^T S H) share of the row (Eq. 2) and g = coef ((H Gram_t) - S H)
   float tr = 0.f, kkt2 = 0.f, sumA = 0.f, nonfin = 0.f, hmax = 0.f;
+  // ADMM (appendix, Family 6): the handle's H is W and its A buffer the
+  // scaled dual U; U of the owned columns is in av when all of them fit
+  const bool admm = (e.method == SYMNMF_ADMM);
+  auto dual = [&](int j) -> float {
+    if constexpr (KH == HW) return av[j];
+    else return (vrow && e.update) ? e.A[base + j] : 0.f;
+  };
+  if (!admm) {
 #pragma unroll
-  for (int j = 0; j < KH; ++j) {
-    float g = 0.f;
-    if (cb + j < e.k) {
-      tr = fmaf(hrow[cb + j], p[j], tr);
-      g = e.coef * (hg[j] - p[j]);
-      const float pg = (hrow[cb + j] > 0.f) ? g : fminf(0.f, g);
-      kkt2 = fmaf(pg, pg, kkt2);
-      if (!isfinite(g)) nonfin += 1.f;
+    for (int j = 0; j < KH; ++j) {
+      float g = 0.f;
+      if (cb + j < e.k) {
+        tr = fmaf(hrow[cb + j], p[j], tr);
+        g = e.coef * (hg[j] - p[j]);
+        const float pg = (hrow[cb + j] > 0.f) ? g : fminf(0.f, g);
+        kkt2 = fmaf(pg, pg, kkt2);
+        if (!isfinite(g)) nonfin += 1.f;
+      }
+      p[j] = g;
     }
-    p[j] = g;
+  } else {
+    // g goes out at once (checks only); p becomes the right-hand side
+    // 2 (S W) + rho (W - U) of the ADMM H-update
+#pragma unroll
+    for (int c4 = 0; c4 < KH / 4; ++c4) {
+      float gg[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int j = 4 * c4 + jj;
+        float g = 0.f, r = 0.f;
+        if (cb + j < e.k) {
+          const float h = hrow[cb + j];
+          tr = fmaf(h, p[j], tr);
+          g = e.coef * (hg[j] - p[j]);
+          const float pg = (h > 0.f) ? g : fminf(0.f, g);
+          kkt2 = fmaf(pg, pg, kkt2);
+          if (!isfinite(g)) nonfin += 1.f;
+          r = 2.f * p[j] + e.rho * (h - dual(j));
+        }
+        gg[jj] = g;
+        p[j] = r;
+      }
+      if (e.gout && vrow)
+        reinterpret_cast<float4 *>(e.gout + base)[c4] = make_float4(gg[0], gg[1], gg[2], gg[3]);
+    }
   }
   if (!vrow) tr = kkt2 = nonfin = 0.f;
   epi_bar();  // every thread has read H_t from Hs
+  if (admm && e.update) {
+    // x = rhs (2 W^T W + rho I)^-1 + U for the owned columns (H = rhs
+    // Minv); the right-hand-side rows go through Hs
+    if (works) {
+#pragma unroll
+      for (int j = 0; j < KH; ++j) hrow[cb + j] = p[j];
+    }
+    epi_bar();  // every right-hand-side row is complete
+    if (works) {
+#pragma unroll
+      for (int j = 0; j < KH; ++j) p[j] = dual(j);
+#pragma unroll 4
+      for (int d = 0; d < KP; ++d) {
+        const float rv = hrow[d];
+        const float4 *mr = reinterpret_cast<const float4 *>(e.minv + d * KP + cb);
+#pragma unroll
+        for (int c4 = 0; c4 < KH / 4; ++c4) {
+          const float4 m = mr[c4];
+          p[4 * c4 + 0] = fmaf(rv, m.x, p[4 * c4 + 0]);
+          p[4 * c4 + 1] = fmaf(rv, m.y, p[4 * c4 + 1]);
+          p[4 * c4 + 2] = fmaf(rv, m.z, p[4 * c4 + 2]);
+          p[4 * c4 + 3] = fmaf(rv, m.w, p[4 * c4 + 3]);
+        }
+      }
+    }
+    epi_bar();  // every thread has read the right-hand sides from Hs
+  }
   // update and projection, HW columns at a time
 #pragma unroll
   for (int hc = 0; hc < KH; hc += HW) {
@@ -321,7 +382,12 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
         if (e.update) {
           if (c < e.k && vrow) {
             float x;
-            if (rms) {
+            if (admm) {
+              // W' = [x]_+, U' = x - W' = U + H - W'
+              x = p[cc + j];
+              av[s] = x - ((x > 0.f) ? x : 0.f);
+              sumA += av[s];
+            } else if (rms) {
               const float v = e.alpha * av[s] + (1.f - e.alpha) * (g * g);
               av[s] = v;
               const float m = e.mom * mv[s] + e.eta * g / (sqrtf(v) + e.eps);
@@ -344,7 +410,7 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
       if (vrow) {
         const float4 p0 = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
         const float4 p1 = make_float4(p[cc + 4], p[cc + 5], p[cc + 6], p[cc + 7]);
-        if (e.gout) {
+        if (e.gout && !admm) {
           float4 *g4 = reinterpret_cast<float4 *>(e.gout + base + cc);
           g4[0] = p0;
           g4[1] = p1;
@@ -354,7 +420,7 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
           m4[0] = p0;
           m4[1] = p1;
         }
-        if (e.gcaller) {
+        if (e.gcaller && !admm) {
 #pragma unroll
           for (int j = 0; j < 8; ++j)
             if (cb + cc + j < e.k) e.gcaller[(r0 + row) * e.k + cb + cc + j] = p[cc + j];

@@ -117,6 +117,8 @@ struct EpiArgs {
   float coef;            // 4 (full/rows) or 2 (block)
   double *slots;         // per tile: [tr, kkt2, sumA, nonfinite]
   float *gram_part;      // per tile kp x kp partial of H_{t+1}^T H_{t+1} (nullptr: skip)
+  float rho;             // ADMM penalty
+  const float *minv;     // ADMM: (2 Gram_t + rho I)^-1, kp x kp row-major
 };
 
 // Cross-tile reduction of one iteration (launch_reduce_iter)
@@ -146,6 +148,11 @@ cudaError_t launch_prod_simt(const ProdArgs &a, cudaStream_t s);
 cudaError_t launch_step_tc(const ProdArgs &a, const EpiArgs *epi, int *tile_cnt, cudaStream_t s,
                            int num_sms, int *G_out, int *err);
 bool tc_supported(int dtype, int kp);
+// ADMM (appendix, Family 6): minv = (2 G + rho I)^-1 for the FP64 Gram G
+// (kp x kp, entries past k ignored; minv is the identity there).  Launched
+// as a programmatic dependent of the preceding kernel.
+cudaError_t launch_admm_minv(const double *gram64, int k, int kp, double rho, float *minv,
+                             cudaStream_t s);
 cudaError_t launch_epilogue(const EpiArgs &a, cudaStream_t s);
 // per-tile Bt copy and Gram partial of H (init / teacher forcing)
 cudaError_t launch_prepare_tiles(const float *H, int64_t n, int k, int kp, void *Bt, int bt_fmt,

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsymnmf.so")
 
 F32, BF16, FP8E4M3 = 0, 1, 2
-ADAGRAD, RMSPROP, PIECEWISE_ADAGRAD, ROW_SVRG, BLOCK_SVRG_ADAPTGROW = 0, 1, 2, 3, 4
+ADAGRAD, RMSPROP, PIECEWISE_ADAGRAD, ROW_SVRG, BLOCK_SVRG_ADAPTGROW, ADMM = 0, 1, 2, 3, 4, 5
 OK, CONVERGED = 0, 1
 ERR_INVALID, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = (
     -1, -2, -3, -4, -5, -6, -7)
@@ -29,7 +29,7 @@ class symnmf_hparams(C.Structure):
                 ("alpha", C.c_double), ("mu", C.c_double), ("c", C.c_double),
                 ("c_r", C.c_double), ("row_frac", C.c_double), ("phi0", C.c_double),
                 ("tau_E", C.c_double), ("tau_g", C.c_double), ("tau_stag", C.c_double),
-                ("growth_kkt_mult", C.c_double), ("seed", C.c_uint64)]
+                ("growth_kkt_mult", C.c_double), ("seed", C.c_uint64), ("rho", C.c_double)]
 
 
 class symnmf_ctrl(C.Structure):

@@ -62,12 +62,12 @@ def test_status_strings(L):
 
 def test_hparams_default_match_oracle(L):
     from oracle import symnmf_oracle as O
-    for m in range(5):
+    for m in range(6):
         hp = L.symnmf_hparams_default(m)
         ref = O.HParams.paper(m)
         for f in ("eta", "eps", "alpha", "mu", "c", "c_r", "row_frac", "phi0", "tau_E",
                   "tau_g", "tau_stag", "growth_kkt_mult", "check_interval", "warmup",
-                  "snapshot_period", "block_rows", "method"):
+                  "snapshot_period", "block_rows", "method", "rho"):
             assert getattr(hp, f) == getattr(ref, f), (m, f)
 
 
@@ -100,7 +100,7 @@ def _ctrl_pair(L, O, method, n):
     return hp, hpo, c, co
 
 
-@pytest.mark.parametrize("method", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("method", [0, 1, 2, 3, 4, 5])
 def test_controller_replay_matches_oracle(L, method):
     """The same recorded scalar trace drives both controllers to identical
     decisions (converged / reset / grow) and identical stagnation ratios."""

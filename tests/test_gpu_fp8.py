@@ -169,11 +169,11 @@ def test_fp8_gradient_matches_oracle(L, n, k):
     assert abs(f_tc - f_emul) <= 1e-6 * normS2
 
 
-@pytest.mark.parametrize("method", [0, 1, 3, 4])
+@pytest.mark.parametrize("method", [0, 1, 3, 4, 5])
 def test_fp8_teacher_forced_step(L, method):
     """One step from an oracle state whose H the two-piece form holds
-    exactly: full-batch AdaGrad / RMSprop through the fused kernel, Row-SVRG
-    and Block-SVRG through the sampled row / column lists."""
+    exactly: full-batch AdaGrad / RMSprop / ADMM through the fused kernel,
+    Row-SVRG and Block-SVRG through the sampled row / column lists."""
     n, k = 1500, 16
     h, keep, S64 = _fp8_handle(L, n, k, seed=21)
     hp = O.HParams.paper(method)
