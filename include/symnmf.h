@@ -313,6 +313,44 @@ int symnmf_objective_noalloc(const void *S, int64_t n, int64_t lds, int32_t dtyp
                              const float *scales, int64_t ld_scales, const float *H, int32_t k,
                              double normS2, double *f, void *stream);
 
+/* ------------------------------------------------ spherical K-means */
+
+typedef struct {
+  int32_t iters;      /* Lloyd iterations this call ran */
+  int32_t converged;  /* 1: the stop rule held at the last iteration */
+  int64_t changed;    /* labels the last iteration changed */
+  double J;           /* objective of the last iteration, sum_i (1 - max_k cos_ik) */
+  double J_prev;      /* the iteration before it (NaN after a single iteration) */
+} symnmf_kmeans_stats;
+
+/* Spherical K-means (Lloyd) on the rows of S (Sec. 6, "Clustering
+ * alternatives", the spherical K-means theorem), K = the handle's k
+ * clusters.  The observations are the normalised rows x_i = s_i / ||s_i||;
+ * cluster k's centroid is the normalised sum of its members,
+ * c_k = sum_{i in C_k} x_i; an iteration assigns every row the cluster of
+ * largest cosine <x_i, c_k / ||c_k||> (lowest index on ties; an empty
+ * cluster has cosine 0 with every row) and J = sum_i (1 - that cosine).
+ * The run stops after the first iteration that changes no label, or whose
+ * relative drop (J_prev - J) <= tol * J_prev (the paper's criterion uses
+ * tol = 1e-4), or after max_iter iterations.
+ * One iteration is two passes of the streamed product (S symmetric):
+ * C = S (D^-1 B) with D = diag ||s_i|| and B the one-hot labels, then
+ * P = S C, with cos_ik = P_ik / (||s_i|| ||c_k||); FP32 products, FP64
+ * norms and FP64 fixed-order cross-tile sums, so runs are bit-reproducible.
+ * Arguments: labels0 (device, n int32, entries in 0..K-1; an entry outside
+ * that range puts its row in no cluster for the first iteration), labels
+ * (device, n int32, written: the final labels), max_iter >= 1, tol >= 0,
+ * J_trace (host, max_iter doubles, J per iteration, or NULL), stats (host,
+ * or NULL).  ||s_i|| is computed on the first call and kept (S is borrowed
+ * and must not change); rows with ||s_i|| = 0 are not valid input.  The
+ * solver state (H, its MMA copy, the Gram, the optimizer buffers) is not
+ * touched; the call synchronises the handle's stream once per iteration.
+ * Errors: INVALID for null labels, max_iter < 1 or tol < 0 or NaN; OOM when
+ * the scratch (n (8 + 8) + ceil(n/128) (16 + 8 kp) bytes) cannot be
+ * allocated; CUDA / STATE as for symnmf_step. */
+int symnmf_spkmeans(symnmf_t h, const int32_t *labels0, int32_t *labels, int32_t max_iter,
+                    double tol, double *J_trace, symnmf_kmeans_stats *stats);
+
 const char *symnmf_last_error(symnmf_t h);
 const char *symnmf_status_string(int32_t status);
 

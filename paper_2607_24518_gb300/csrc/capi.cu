@@ -93,6 +93,14 @@ struct symnmf_ctx {
   double prof_bytes = 0.0;
   int64_t prof_kernels = 0;  // kernels launched by the solver loop while profiling
   int ctas = 0;              // CTA cap of the tensor-core launches (0: all SMs)
+  // spherical K-means scratch, allocated by the first symnmf_spkmeans
+  double *km_rn = nullptr;      // ||s_i||
+  int *km_lab = nullptr;        // two label buffers of n
+  double *km_colsq = nullptr;   // ntiles x kp
+  float *km_inv = nullptr;      // kp
+  double *km_slots = nullptr;   // ntiles x 2
+  double *km_out = nullptr;     // [J, changed]
+  double *km_hout = nullptr;    // pinned mirror
 };
 
 namespace {
@@ -147,10 +155,11 @@ void free_all(symnmf_t h) {
                   (void *)h->gramI, (void *)h->gramJ, (void *)h->minv, (void *)h->dlists, (void *)h->ring,
                   (void *)h->hist, (void *)h->sel, (void *)h->dmed, (void *)h->dsum,
                   (void *)h->norm_parts, (void *)h->dev_err, (void *)h->counters, (void *)h->tile_cnt,
-                  (void *)h->lvl1})
+                  (void *)h->lvl1, (void *)h->km_rn, (void *)h->km_lab, (void *)h->km_colsq,
+                  (void *)h->km_inv, (void *)h->km_slots, (void *)h->km_out})
     cudaFree(p);
   for (void *p : {(void *)h->hlists, (void *)h->hring, (void *)h->hsum, (void *)h->hmed,
-                  (void *)h->host_err})
+                  (void *)h->host_err, (void *)h->km_hout})
     if (p) cudaFreeHost(p);
   for (int i = 0; i < kStages; ++i)
     if (h->stage_ev[i]) cudaEventDestroy(h->stage_ev[i]);
@@ -1012,6 +1021,117 @@ int symnmf_objective(symnmf_t h, double *f, double *E) {
   CK(cudaStreamSynchronize(h->stream));
   if (f) *f = h->hring[kRing].f;
   if (E) *E = h->hring[kRing].E;
+  return SYMNMF_OK;
+}
+
+int symnmf_spkmeans(symnmf_t h, const int32_t *labels0, int32_t *labels, int32_t max_iter,
+                    double tol, double *J_trace, symnmf_kmeans_stats *stats) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!labels0 || !labels || max_iter < 1 || !(tol >= 0))
+    return fail(h, SYMNMF_ERR_INVALID, "spkmeans: null labels, max_iter < 1 or tol < 0");
+  if (!h->km_rn) {
+    cudaError_t e = dalloc(&h->km_rn, (size_t)h->n);
+    if (e == cudaSuccess) e = dalloc(&h->km_lab, (size_t)2 * h->n);
+    if (e == cudaSuccess) e = dalloc(&h->km_colsq, (size_t)h->ntiles * h->kp);
+    if (e == cudaSuccess) e = dalloc(&h->km_inv, (size_t)h->kp);
+    if (e == cudaSuccess) e = dalloc(&h->km_slots, (size_t)h->ntiles * 2);
+    if (e == cudaSuccess) e = dalloc(&h->km_out, 2);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->km_hout, 2 * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      for (void *p : {(void *)h->km_rn, (void *)h->km_lab, (void *)h->km_colsq, (void *)h->km_inv,
+                      (void *)h->km_slots, (void *)h->km_out})
+        cudaFree(p);
+      if (h->km_hout) cudaFreeHost(h->km_hout);
+      h->km_rn = nullptr;
+      h->km_lab = nullptr;
+      h->km_colsq = nullptr;
+      h->km_inv = nullptr;
+      h->km_slots = nullptr;
+      h->km_out = nullptr;
+      h->km_hout = nullptr;
+      return fail(h, SYMNMF_ERR_OOM, "spkmeans scratch");
+    }
+    CK(launch_row_norms(h->S, h->n, h->lds, h->dtype, h->scales, h->ld_scales, h->km_rn,
+                        h->stream));
+    count_kernels(h, 1);
+  }
+  // the two product operands go through the solver's other H buffer and MMA
+  // copy, so H_t, its copy and its Gram stay as they are
+  struct KeepCur {
+    symnmf_t h;
+    int c;
+    ~KeepCur() { h->cur = c; }
+  } keep{h, h->cur};
+  h->cur = 1 - keep.c;
+  float *Hop = h->H[h->cur];
+  const int64_t rows_alloc = (int64_t)h->ntiles * kTileRows;
+  CK(cudaMemcpyAsync(h->km_lab, labels0, sizeof(int32_t) * h->n, cudaMemcpyDeviceToDevice,
+                     h->stream));
+  KmArgs a{};
+  a.n = h->n;
+  a.K = h->k;
+  a.ntiles = h->ntiles;
+  a.P = h->P;
+  a.C = Hop;
+  a.colsq = h->km_colsq;
+  a.inv_norm = h->km_inv;
+  a.rn = h->km_rn;
+  a.slots = h->km_slots;
+  a.out = h->km_out;
+  symnmf_kmeans_stats st{};
+  st.J = st.J_prev = NAN;
+  int li = 0;
+  for (int32_t t = 0; t < max_iter; ++t) {
+    int *lin = h->km_lab + (size_t)li * h->n;
+    int *lout = h->km_lab + (size_t)(1 - li) * h->n;
+    // pass 1: C = S (D^-1 B)
+    CK(launch_km_operand(lin, h->km_rn, h->n, h->kp, Hop, rows_alloc, h->stream));
+    CK(launch_prepare_tiles(Hop, h->n, h->k, h->kp, h->Bt[h->cur], h->bt_fmt, h->ldb, nullptr,
+                            h->stream));
+    PartLayout ly;
+    if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly))) return rc;
+    a.nsplit = ly.nsplit;
+    a.skG = ly.skG;
+    a.ncols = ly.ncols;
+    CK(launch_km_centroids(a, h->kp, h->stream));
+    // pass 2: P = S C, then the assignment
+    CK(launch_prepare_tiles(Hop, h->n, h->k, h->kp, h->Bt[h->cur], h->bt_fmt, h->ldb, nullptr,
+                            h->stream));
+    if ((rc = prod(h, nullptr, h->ntiles, nullptr, h->ntiles, h->P, &ly))) return rc;
+    a.nsplit = ly.nsplit;
+    a.skG = ly.skG;
+    a.ncols = ly.ncols;
+    a.labels_in = lin;
+    a.labels_out = lout;
+    CK(launch_km_assign(a, h->kp, h->stream));
+    count_kernels(h, 6);
+    CK(cudaMemcpyAsync(h->km_hout, h->km_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaMemcpyAsync(h->host_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->host_err[0] != 0)
+      return fail(h, SYMNMF_ERR_TIMEOUT,
+                  "a bounded device wait gave up (code " + std::to_string(h->host_err[0]) + ")");
+    const double J = h->km_hout[0];
+    const int64_t changed = (int64_t)h->km_hout[1];
+    if (!std::isfinite(J)) return fail(h, SYMNMF_ERR_NONFINITE, "spkmeans: non-finite objective");
+    if (J_trace) J_trace[t] = J;
+    li = 1 - li;
+    st.iters = t + 1;
+    st.J_prev = st.J;
+    st.J = J;
+    st.changed = changed;
+    if (changed == 0 || (t >= 1 && st.J_prev - J <= tol * st.J_prev)) {
+      st.converged = 1;
+      break;
+    }
+  }
+  CK(cudaMemcpyAsync(labels, h->km_lab + (size_t)li * h->n, sizeof(int32_t) * h->n,
+                     cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (stats) *stats = st;
   return SYMNMF_OK;
 }
 

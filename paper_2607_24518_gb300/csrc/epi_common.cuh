@@ -62,6 +62,31 @@ __device__ __forceinline__ int64_t sk_cta(int64_t x, int64_t W, int64_t G) {
   return b;
 }
 
+// Partials of a product launch that ran without the fused epilogue: with
+// the stream-K layout (skG > 0) CTAs b0..b1 hold row position p's partials
+// in slots b + p; the SIMT layout has nsplit column shares per position.
+// part_sum adds the partials of row r, column c in that fixed order.
+__device__ __forceinline__ void part_range(int p, int skG, int ncols, int nlist, int64_t &b0,
+                                           int64_t &b1) {
+  b0 = b1 = 0;
+  if (skG > 0) {
+    const int64_t W = (int64_t)nlist * ncols;
+    b0 = sk_cta((int64_t)p * ncols, W, skG);
+    b1 = sk_cta((int64_t)p * ncols + ncols - 1, W, skG);
+  }
+}
+template <int KP>
+__device__ __forceinline__ float part_sum(const float *P, int nsplit, int skG, int ncols, int nlist,
+                                          int p, int r, int c, int64_t b0, int64_t b1) {
+  float v = 0.f;
+  if (skG > 0) {
+    for (int64_t b = b0; b <= b1; ++b) v += P[((b + p) * kTileRows + r) * KP + c];
+  } else {
+    for (int s = 0; s < nsplit; ++s) v += P[(((int64_t)s * nlist + p) * kTileRows + r) * KP + c];
+  }
+  return v;
+}
+
 // Sum, in index order, `count` (<= 32) values at base[i * stride]; every
 // load is issued before the ordered additions.
 template <typename T>

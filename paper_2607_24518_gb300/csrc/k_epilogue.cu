@@ -101,19 +101,6 @@ __device__ void tile_tail(const float (*Hn)[KP + 1], int64_t r0, void *Bt, int b
   }
 }
 
-// sum of the partials of row r, column c of list position p (fixed order)
-template <int KP>
-__device__ __forceinline__ float part_sum(const float *P, int nsplit, int skG, int ncols, int nlist,
-                                          int p, int r, int c, int64_t b0, int64_t b1) {
-  float v = 0.f;
-  if (skG > 0) {
-    for (int64_t b = b0; b <= b1; ++b) v += P[((b + p) * kTileRows + r) * KP + c];
-  } else {
-    for (int s = 0; s < nsplit; ++s) v += P[(((int64_t)s * nlist + p) * kTileRows + r) * KP + c];
-  }
-  return v;
-}
-
 template <int KP>
 constexpr size_t epi_smem_bytes() {
   return (size_t)(2 * kTileRows * (KP + 1) + 2 * KP * (KP + 1)) * sizeof(float);

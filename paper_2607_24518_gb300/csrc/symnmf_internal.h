@@ -184,4 +184,30 @@ cudaError_t launch_quantize_fp8(const void *src, int src_dtype, int64_t rows, in
 cudaError_t launch_sum_slot(const double *slots, int ntiles, int which, double *out,
                             cudaStream_t s);
 
+// Spherical K-means (Sec. 6): the kernels around the two product passes of
+// one Lloyd iteration (k_kmeans.cu)
+struct KmArgs {
+  int64_t n;
+  int K, ntiles;
+  const float *P;        // product partials (layout: nsplit / skG / ncols)
+  int nsplit, skG, ncols;
+  float *C;              // centroid sums, n x kp (the next operand)
+  double *colsq;         // per tile kp FP64 column sums of squares of C
+  float *inv_norm;       // kp: 1 / ||c_k|| (0 for an empty cluster)
+  const double *rn;      // ||s_i||
+  const int *labels_in;
+  int *labels_out;
+  double *slots;         // per tile [sum (1 - cos), changed]
+  double *out;           // [J, changed]
+};
+cudaError_t launch_row_norms(const void *S, int64_t n, int64_t lds, int dtype, const float *scales,
+                             int64_t ld_scales, double *rn, cudaStream_t s);
+// operand D^-1 B (rows_alloc x kp): 1 / ||s_i|| in column labels[i]
+cudaError_t launch_km_operand(const int *labels, const double *rn, int64_t n, int kp, float *H,
+                              int64_t rows_alloc, cudaStream_t s);
+// C from the partials of S (D^-1 B), its column norms
+cudaError_t launch_km_centroids(const KmArgs &a, int kp, cudaStream_t s);
+// labels from the partials of S C, J and the changed count into out
+cudaError_t launch_km_assign(const KmArgs &a, int kp, cudaStream_t s);
+
 }  // namespace symnmf

@@ -53,6 +53,11 @@ class symnmf_stats(C.Structure):
                 ("phi", C.c_double), ("converged", C.c_int32), ("resets", C.c_int32)]
 
 
+class symnmf_kmeans_stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("changed", C.c_int64),
+                ("J", C.c_double), ("J_prev", C.c_double)]
+
+
 class SymNMFError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{message} (status {status})")
@@ -87,6 +92,7 @@ def _load():
         "symnmf_objective": [vp, P(dbl), P(dbl)],
         "symnmf_hparams_default": [i32, P(symnmf_hparams)],
         "symnmf_step": [vp, P(symnmf_hparams), i32, P(symnmf_stats)],
+        "symnmf_spkmeans": [vp, vp, vp, i32, dbl, P(dbl), P(symnmf_kmeans_stats)],
         "symnmf_batch_step": [P(vp), i32, P(symnmf_hparams), i32, P(symnmf_stats)],
         "symnmf_get_trace": [vp, P(symnmf_record), i64, P(i64)],
         "symnmf_set_profiling": [vp, i32],
@@ -126,7 +132,7 @@ DECLARED = [
     "symnmf_batch_autotune",
     "symnmf_state_bytes", "symnmf_get_state", "symnmf_set_state", "symnmf_last_error",
     "symnmf_status_string", "symnmf_splitmix64", "symnmf_sample_blocks",
-    "symnmf_controller_check", "symnmf_objective_noalloc",
+    "symnmf_controller_check", "symnmf_objective_noalloc", "symnmf_spkmeans",
 ]
 
 NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -205,6 +211,17 @@ def symnmf_objective_noalloc(S, n, lds, dtype, scales, ld_scales, H, k, normS2, 
         raise SymNMFError(st, "n=%d, k=%d needs %d bytes of scratch, above the fixed %d"
                           % (n, k, noalloc_scratch_need(n, k), NOALLOC_SCRATCH_BYTES))
     return _check(st)
+
+
+def symnmf_spkmeans(h, labels0, labels, max_iter, tol=1e-4, trace=True):
+    """Spherical K-means (Lloyd) on the rows of S with K = the handle's k;
+    labels0 / labels are device int32 tensors of n.  Returns (stats, J per
+    iteration)."""
+    st = symnmf_kmeans_stats()
+    Jt = (C.c_double * max(1, max_iter))() if trace else None
+    _check(LIB.symnmf_spkmeans(h, _ptr(labels0), _ptr(labels), max_iter, float(tol), Jt,
+                               C.byref(st)), h)
+    return st, (list(Jt)[:st.iters] if trace else None)
 
 
 def symnmf_set_norm(h, normS2):
