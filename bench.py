@@ -623,6 +623,101 @@ def run_batch(args):
             "per_instance": per_inst, "generation_seconds": t_gen}
 
 
+def run_kmeans(args):
+    """Spherical K-means (Lloyd on the rows of S, Sec. 6) on the n=20000 TPDM
+    matrix with K = 32 clusters: Lloyd iterations/s from the same seeded
+    labels (fixed work per iteration: each timed call runs one iteration,
+    two streamed passes of S, and returns its objective to the host), the
+    product kernel's HBM fraction, and the FP64 oracle's rate on the host."""
+    import numpy as np
+    import torch
+    from paper_2607_24518_gb300 import build
+    build.build()
+    from paper_2607_24518_gb300 import symnmf as L
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    name = {"f32": "tpdm_n20000_k32_fp32_adagrad", "bf16": "tpdm_n20000_k32_bf16_adagrad"}[
+        args.km_storage]
+    kind, n, Kc, dt, _, _ = WORKLOADS[name]
+    S, _, _ = make_input(name, dev)
+    h = L.symnmf_create(S, n, Kc, {"f32": L.F32, "bf16": L.BF16}[dt])
+    stream = torch.cuda.Stream(dev)
+    L.symnmf_set_stream(h, stream)
+    rng = np.random.default_rng(0)
+    lab = rng.integers(0, Kc, size=n)
+    lab[:Kc] = np.arange(Kc)
+    lab0 = torch.tensor(rng.permutation(lab), dtype=torch.int32, device=dev)
+    out_l = torch.empty(n, dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        L.symnmf_spkmeans(h, lab0, out_l, 1, 1e-4, trace=False)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        L.symnmf_spkmeans(h, lab0, out_l, 1, 1e-4, trace=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    L.symnmf_set_profiling(h, True)
+    prof = max(5, min(args.steps, 50))
+    for _ in range(prof):
+        L.symnmf_spkmeans(h, lab0, out_l, 1, 1e-4, trace=False)
+    torch.cuda.synchronize()
+    prod_ms, prod_launches, _, kernel_launches = L.symnmf_get_profile(h)
+    L.symnmf_set_profiling(h, False)
+    ck = clocks.stop()
+    # a full run from the same labels: iterations to the paper's stop rule
+    st, Jt = L.symnmf_spkmeans(h, lab0, out_l, 200, 1e-4)
+    torch.cuda.synchronize()
+    impl = L.symnmf_get_impl(h)
+    L.symnmf_destroy(h)
+    peak, src = peaks()
+    per_launch_ms = prod_ms / max(1, prod_launches)
+    pass_bytes = n * n * ESIZE[dt]
+    achieved = pass_bytes / (per_launch_ms * 1e-3) / 1e9
+    cpu = None
+    if args.cpu_baseline:
+        from oracle import spkmeans_oracle as KM
+        S64 = S.double().cpu().numpy()
+        labs = lab0.cpu().numpy().astype(np.int64)
+        KM.lloyd_step(S64, labs, Kc)
+        t0 = time.perf_counter()
+        it = 0
+        while True:
+            KM.lloyd_step(S64, labs, Kc)
+            it += 1
+            el = time.perf_counter() - t0
+            if it >= 2 and el >= args.cpu_budget:
+                break
+        cpu = {"value": it / el, "unit": "Lloyd iterations/s", "cores": cpu_threads(),
+               "kind": "oracle", "sample": f"{it} FP64 oracle Lloyd iterations of the same "
+                                           f"workload ({el:.1f} s)"}
+        del S64
+    return {
+        "metric": "spherical K-means Lloyd iterations/s (two streamed passes of S each)",
+        "value": args.steps / (ms / 1e3), "unit": "Lloyd iterations/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "bf16": "bf16"}[dt] + " storage, f32 accumulate, f64 norms and sums",
+        "data": "synthetic (seeded TPDM generator, seeded initial labels)",
+        "config": {"workload": f"spkmeans_tpdm_n{n}_K{Kc}_{dt}", "n": n, "K": Kc, "storage": dt,
+                   "product_impl": ["", "simt", "tcgen05"][impl],
+                   "l2": "S larger than L2 (no flush needed)",
+                   "run_from_same_labels": {"iterations": st.iters, "converged": st.converged,
+                                            "J": st.J}},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": src,
+                     "kernel": "product pass (S times an n x K operand)",
+                     "bytes_per_launch": pass_bytes, "ms_per_launch": per_launch_ms},
+        "cpu_baseline": cpu,
+        "clocks": ck,
+        "gpu_launches": int(kernel_launches / prof * args.steps),
+        "status": "ok",
+    }
+
+
 def run_reference(args, rank):
     """The FP64 CPU oracle on the same workload, bounded per step."""
     if rank != 0:
@@ -682,6 +777,9 @@ def main():
     ap.add_argument("--restarts", type=int, default=4)
     ap.add_argument("--tune-iters", dest="tune_iters", type=int, default=10)
     ap.add_argument("--batch-cap", dest="batch_cap", type=int, default=3000)
+    ap.add_argument("--kmeans", action="store_true",
+                    help="spherical K-means on the n=20000 TPDM matrix, K=32 (own JSON line)")
+    ap.add_argument("--km-storage", dest="km_storage", default="f32", choices=["f32", "bf16"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -695,6 +793,9 @@ def main():
         return
     if args.batch:
         print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.kmeans:
+        print(json.dumps(run_kmeans(args)), flush=True)
         return
     if args.impl == "reference":
         out = run_reference(args, rank)
