@@ -313,6 +313,40 @@ int symnmf_objective_noalloc(const void *S, int64_t n, int64_t lds, int32_t dtyp
                              const float *scales, int64_t ld_scales, const float *H, int32_t k,
                              double normS2, double *f, void *stream);
 
+/* ------------------------------------------------- dependence matrix */
+
+/* The solver's input from data (Sec. 3, "Correlation matrices" and the
+ * empirical TPDM): S = |D^-1/2 G D^-1/2| with G = Y^T Y and D = diag(G),
+ * i.e. S_ij = |G_ij| / sqrt(G_ii G_jj), S_ii = 1, clamped to [0, 1].
+ * center = 1 subtracts each column's mean first, giving the absolute
+ * Pearson correlation of the n variables over the T observations (rows of
+ * Y); center = 0 with Y = Omega, the n_exc x n matrix of exceedance angles,
+ * gives the unit-diagonal empirical TPDM (its n / n_exc factor cancels).
+ * Arguments: Y (device FP32, T x n, row pitch ldy >= n elements), S
+ * (device, n x n, row pitch lds >= n elements, 16-byte aligned with
+ * lds * element size a multiple of 16) written in out_dtype (SYMNMF_F32,
+ * SYMNMF_BF16 round to nearest, or SYMNMF_FP8E4M3 with one power-of-two
+ * scale per 128 x 128 tile written to scales[ceil(n/128)][ld_scales], the
+ * layout of symnmf_set_tile_scales), normS2 (device, one double, or NULL):
+ * ||S||_F^2 (of the stored values for F32 / BF16, of the values before
+ * quantisation for FP8), summed in FP32 over runs of 32 entries of a row
+ * and in FP64 across runs (relative error below 32 * 2^-24).  stream: cudaStream_t as void* (NULL =
+ * legacy default); the call synchronises it once at the end.
+ * Arithmetic: the centred values are FP32; G is formed on the tensor cores
+ * from tf32 hi / lo pieces of each value (hi hi + hi lo + lo hi, FP32
+ * accumulation), about FP32 accuracy; column norms are FP64.  A column with
+ * zero variance gives a zero row and column in S except S_ii = 1.
+ * Scratch: n (8 T' + 12) + ceil(n/128) ceil(n/256) 8 bytes of stream-ordered
+ * device memory (T' = T rounded up to 32), freed before return.
+ * Errors: INVALID for null pointers, T < 1 (T < 2 with center), n < 1,
+ * pitches below n, a misaligned S or pitch, an unknown out_dtype, or FP8
+ * without scales or with ld_scales < ceil(n/128); UNSUPPORTED for n above
+ * 2,097,120; OOM when the scratch cannot be allocated; TIMEOUT when a
+ * bounded device wait gave up; CUDA for other failures. */
+int symnmf_build_dependence(const float *Y, int64_t T, int64_t n, int64_t ldy, int32_t center,
+                            int32_t out_dtype, void *S, int64_t lds, float *scales,
+                            int64_t ld_scales, double *normS2, void *stream);
+
 /* ------------------------------------------------ spherical K-means */
 
 typedef struct {

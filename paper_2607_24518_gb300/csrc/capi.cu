@@ -1024,6 +1024,44 @@ int symnmf_objective(symnmf_t h, double *f, double *E) {
   return SYMNMF_OK;
 }
 
+int symnmf_build_dependence(const float *Y, int64_t T, int64_t n, int64_t ldy, int32_t center,
+                            int32_t out_dtype, void *S, int64_t lds, float *scales,
+                            int64_t ld_scales, double *normS2, void *stream) {
+  if (!Y || !S || T < 1 || n < 1 || ldy < n || lds < n) return SYMNMF_ERR_INVALID;
+  if (center && T < 2) return SYMNMF_ERR_INVALID;
+  if (out_dtype != SYMNMF_F32 && out_dtype != SYMNMF_BF16 && out_dtype != SYMNMF_FP8E4M3)
+    return SYMNMF_ERR_INVALID;
+  const int64_t es = out_dtype == SYMNMF_F32 ? 4 : out_dtype == SYMNMF_BF16 ? 2 : 1;
+  if ((lds * es) % 16 != 0 || reinterpret_cast<uintptr_t>(S) % 16 != 0) return SYMNMF_ERR_INVALID;
+  const int64_t nt = (n + 127) / 128;
+  if (out_dtype == SYMNMF_FP8E4M3 && (!scales || ld_scales < nt)) return SYMNMF_ERR_INVALID;
+  if (n > 2097120 || T > (int64_t)1 << 30) return SYMNMF_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  int *derr = nullptr;
+  int herr = 0;
+  cudaError_t e = cudaMallocAsync((void **)&derr, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    const int dt = out_dtype == SYMNMF_F32 ? 0 : out_dtype == SYMNMF_BF16 ? 1 : 2;
+    e = launch_dependence(Y, T, n, ldy, center ? 1 : 0, dt, S, lds, scales, ld_scales, normS2,
+                          derr, s);
+  }
+  if (derr) {
+    cudaError_t e2 = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(derr, s);
+    if (e == cudaSuccess) e = e2;
+  }
+  cudaError_t es2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = es2;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return SYMNMF_ERR_OOM;
+  }
+  if (e != cudaSuccess) return SYMNMF_ERR_CUDA;
+  if (herr != 0) return SYMNMF_ERR_TIMEOUT;
+  return SYMNMF_OK;
+}
+
 int symnmf_spkmeans(symnmf_t h, const int32_t *labels0, int32_t *labels, int32_t max_iter,
                     double tol, double *J_trace, symnmf_kmeans_stats *stats) {
   int rc = check_handle(h);

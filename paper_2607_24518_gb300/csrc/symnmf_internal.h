@@ -18,8 +18,10 @@
 //          max|H_tile| / d <= 448); the 2 kp rows are followed by the
 //          ntiles FP32 values d                               (FP8 S)
 #pragma once
-#include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 namespace symnmf {
 
@@ -148,6 +150,10 @@ cudaError_t launch_prod_simt(const ProdArgs &a, cudaStream_t s);
 cudaError_t launch_step_tc(const ProdArgs &a, const EpiArgs *epi, int *tile_cnt, cudaStream_t s,
                            int num_sms, int *G_out, int *err);
 bool tc_supported(int dtype, int kp);
+// TMA descriptor of a 2-D row-major array: inner extent, outer extent, row
+// pitch in bytes, box; 128-byte swizzle, zero fill out of bounds
+bool make_map_2d(CUtensorMap *m, const void *base, CUtensorMapDataType dt, uint64_t inner,
+                 uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
 // ADMM (appendix, Family 6): minv = (2 G + rho I)^-1 for the FP64 Gram G
 // (kp x kp, entries past k ignored; minv is the identity there).  Launched
 // as a programmatic dependent of the preceding kernel.
@@ -183,6 +189,12 @@ cudaError_t launch_quantize_fp8(const void *src, int src_dtype, int64_t rows, in
                                 int64_t ld_scales, double *tile_sumsq, cudaStream_t s);
 cudaError_t launch_sum_slot(const double *slots, int ntiles, int which, double *out,
                             cudaStream_t s);
+
+// Dependence matrix S = |D^-1/2 Y^T Y D^-1/2| (Sec. 3), k_dep.cu; err is a
+// device int the kernels set on a bounded-wait timeout
+cudaError_t launch_dependence(const float *Y, int64_t T, int64_t n, int64_t ldy, int center,
+                              int out, void *S, int64_t lds, float *scales, int64_t ld_scales,
+                              double *normS2, int *err, cudaStream_t s);
 
 // Spherical K-means (Sec. 6): the kernels around the two product passes of
 // one Lloyd iteration (k_kmeans.cu)

@@ -93,6 +93,7 @@ def _load():
         "symnmf_hparams_default": [i32, P(symnmf_hparams)],
         "symnmf_step": [vp, P(symnmf_hparams), i32, P(symnmf_stats)],
         "symnmf_spkmeans": [vp, vp, vp, i32, dbl, P(dbl), P(symnmf_kmeans_stats)],
+        "symnmf_build_dependence": [vp, i64, i64, i64, i32, i32, vp, i64, vp, i64, vp, vp],
         "symnmf_batch_step": [P(vp), i32, P(symnmf_hparams), i32, P(symnmf_stats)],
         "symnmf_get_trace": [vp, P(symnmf_record), i64, P(i64)],
         "symnmf_set_profiling": [vp, i32],
@@ -133,6 +134,7 @@ DECLARED = [
     "symnmf_state_bytes", "symnmf_get_state", "symnmf_set_state", "symnmf_last_error",
     "symnmf_status_string", "symnmf_splitmix64", "symnmf_sample_blocks",
     "symnmf_controller_check", "symnmf_objective_noalloc", "symnmf_spkmeans",
+    "symnmf_build_dependence",
 ]
 
 NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -211,6 +213,14 @@ def symnmf_objective_noalloc(S, n, lds, dtype, scales, ld_scales, H, k, normS2, 
         raise SymNMFError(st, "n=%d, k=%d needs %d bytes of scratch, above the fixed %d"
                           % (n, k, noalloc_scratch_need(n, k), NOALLOC_SCRATCH_BYTES))
     return _check(st)
+
+
+def symnmf_build_dependence(Y, T, n, ldy, center, out_dtype, S, lds, scales=None, ld_scales=0,
+                            normS2=None, stream=None):
+    """S = |D^-1/2 Y^T Y D^-1/2| (centred columns for the correlation)."""
+    s = getattr(stream, "cuda_stream", stream)
+    return _check(LIB.symnmf_build_dependence(_ptr(Y), T, n, ldy, int(center), out_dtype, _ptr(S),
+                                              lds, _ptr(scales), ld_scales, _ptr(normS2), s))
 
 
 def symnmf_spkmeans(h, labels0, labels, max_iter, tol=1e-4, trace=True):
