@@ -718,6 +718,109 @@ def run_kmeans(args):
     }
 
 
+def run_dependence(args):
+    """The solver's input from data on the GPU (Sec. 3): the absolute
+    Pearson correlation of n = 1e5 variables over T = 500 observations of
+    the 50-factor model (market loadings U[0.4, 0.8], 49 sector factors
+    U[0, 0.5] at 10% density, unit Gaussian noise; seed 0), written as FP32
+    (40 GB), BF16 and FP8 E4M3 with tile scales.  One line: the FP32 build's
+    time, its tf32 tensor throughput against the tensor peak (the kernel is
+    tensor-bound: 3 tf32 products per value pair), the S bytes written per
+    second, and the BF16 / FP8 times in the config."""
+    import numpy as np
+    import torch
+    from paper_2607_24518_gb300 import build
+    build.build()
+    from paper_2607_24518_gb300 import symnmf as L
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n, T = args.dep_n, 500
+    rng = np.random.default_rng(0)
+    A = np.zeros((n, 50), dtype=np.float32)
+    A[:, 0] = rng.uniform(0.4, 0.8, size=n)
+    mask = rng.random((n, 49)) < 0.1
+    A[:, 1:] = np.where(mask, rng.uniform(0.0, 0.5, size=(n, 49)), 0.0)
+    Z = rng.standard_normal((T, 50)).astype(np.float32)
+    Y = torch.tensor(Z @ A.T, device=dev) + torch.randn(T, n, device=dev,
+                                                       generator=torch.Generator(dev).manual_seed(0))
+    nt = (n + 127) // 128
+    stream = torch.cuda.Stream(dev)
+    times = {}
+    nrm = torch.zeros(1, dtype=torch.float64, device=dev)
+    clocks = None
+    for out, es, tdt in ((L.F32, 4, torch.float32), (L.BF16, 2, torch.bfloat16),
+                         (L.FP8E4M3, 1, torch.uint8)):
+        lds = (n + 16 // es - 1) // (16 // es) * (16 // es)
+        S = torch.empty(n, lds, dtype=tdt, device=dev)
+        sc = torch.empty(nt, nt, dtype=torch.float32, device=dev) if out == L.FP8E4M3 else None
+        L.symnmf_build_dependence(Y, T, n, n, 1, out, S, lds, sc, nt if sc is not None else 0,
+                                  nrm, stream)
+        if out == L.F32:
+            clocks = Clocks(0)
+            time.sleep(0.3)
+        reps = 3
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            L.symnmf_build_dependence(Y, T, n, n, 1, out, S, lds, sc,
+                                      nt if sc is not None else 0, nrm, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[out] = e0.elapsed_time(e1) / reps
+        if out == L.F32:
+            ck = clocks.stop()
+        del S, sc
+        torch.cuda.empty_cache()
+    Tp = (T + 31) // 32 * 32
+    ms = times[L.F32]
+    # executed tensor work: the 128 x 256 tiles on or above the diagonal,
+    # 3 tf32 products over Tp each
+    nib, njb = (n + 127) // 128, (n + 255) // 256
+    tiles = sum(min(nib, 2 * jb + 2) for jb in range(njb))
+    tf32_flops = 3 * 2.0 * tiles * 128 * 256 * Tp
+    achieved = tf32_flops / (ms * 1e-3) / 1e12
+    d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = float(d.get("bf16_tflops", 1900.0))
+    peak = bf16 * (1.1 / 2.25)   # tf32 dense = bf16 dense x the nominal ratio
+    cpu = None
+    if args.cpu_baseline:
+        from oracle import dependence_oracle as DO
+        m = 4000
+        Ys = Y[:, :m].double().cpu().numpy()
+        t0 = time.perf_counter()
+        it = 0
+        while True:
+            DO.dependence(Ys, True)
+            it += 1
+            el = time.perf_counter() - t0
+            if el >= min(args.cpu_budget, 10.0) and it >= 1:
+                break
+        cpu = {"value": it * m * m / el / 1e9, "unit": "G entries of S per s",
+               "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{it} FP64 oracle builds of a {m}-variable slice (T = {T}, {el:.1f} s)"}
+    return {
+        "metric": "dependence matrix build: entries of S per second (|corr|, n = 1e5, T = 500)",
+        "value": n * n / (ms * 1e-3) / 1e9, "unit": "G entries of S per s", "n_gpus": 1,
+        "steps": 3, "warmup": 1, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 in, tf32 hi/lo products, f32 out",
+        "data": "synthetic (seeded 50-factor model)",
+        "config": {"workload": f"abs_corr_n{n}_T{T}", "n": n, "T": T,
+                   "ms_bf16_out": times[L.BF16], "ms_fp8_out": times[L.FP8E4M3],
+                   "S_write_gbs_f32": n * n * 4 / (ms * 1e-3) / 1e9},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "measured bf16 x nominal tf32/bf16 ratio (1.1 / 2.25)",
+                     "kernel": "dep_gemm (3 tf32 products per pair, upper-triangle tiles)",
+                     "flops_per_launch": tf32_flops, "tiles": tiles},
+        "cpu_baseline": cpu,
+        "clocks": ck,
+        "gpu_launches": 3 * 4,
+        "status": "ok",
+    }
+
+
 def run_reference(args, rank):
     """The FP64 CPU oracle on the same workload, bounded per step."""
     if rank != 0:
@@ -777,6 +880,9 @@ def main():
     ap.add_argument("--restarts", type=int, default=4)
     ap.add_argument("--tune-iters", dest="tune_iters", type=int, default=10)
     ap.add_argument("--batch-cap", dest="batch_cap", type=int, default=3000)
+    ap.add_argument("--dependence", action="store_true",
+                    help="dependence matrix build, |corr| n=1e5 T=500 (own JSON line)")
+    ap.add_argument("--dep-n", dest="dep_n", type=int, default=100000)
     ap.add_argument("--kmeans", action="store_true",
                     help="spherical K-means on the n=20000 TPDM matrix, K=32 (own JSON line)")
     ap.add_argument("--km-storage", dest="km_storage", default="f32", choices=["f32", "bf16"])
@@ -796,6 +902,9 @@ def main():
         return
     if args.kmeans:
         print(json.dumps(run_kmeans(args)), flush=True)
+        return
+    if args.dependence:
+        print(json.dumps(run_dependence(args)), flush=True)
         return
     if args.impl == "reference":
         out = run_reference(args, rank)

@@ -19,7 +19,10 @@
 //               normalises, clamps to [0, 1], writes 1 on the diagonal and
 //               stores S as FP32, BF16 (round to nearest) or E4M3 with one
 //               power-of-two scale per 128 x 128 tile, plus the CTA's FP64
-//               sum of squares (FP8: of the values before quantisation)
+//               sum of squares (FP8: of the values before quantisation).
+//               Only 128 x 128 tiles on or above the diagonal are computed;
+//               each one above it is also stored transposed, so S is
+//               exactly symmetric and the tensor work is halved
 //   dep_sum     fixed-order FP64 sum of the CTA partials -> ||S||^2
 // Every mbarrier wait is bounded (2 s); on expiry the CTA records an error
 // code, drains its own copies, frees its tensor memory and returns.
@@ -131,6 +134,11 @@ __global__ void __launch_bounds__(kDepThreads, 1)
   const int ib = first + local % gsize;
   const int jb = local / gsize;
 
+  // both 128-column tiles below the diagonal: their mirrors are computed
+  if (2 * jb + 1 < ib) {
+    if (threadIdx.x == 0) a.sq[blockIdx.x] = 0.0;
+    return;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kDepStages; ++s) {
@@ -202,13 +210,25 @@ __global__ void __launch_bounds__(kDepThreads, 1)
       mma_commit(accf);
     }
   } else {
-    // epilogue: thread row r of the tile, 256 columns
+    // epilogue: thread row r of the tile, 256 columns = the 128-column
+    // tiles jt = 2 jb and 2 jb + 1.  Only the upper triangle is computed:
+    // a tile with jt > ib is stored and mirrored to (jt, ib) (lane = row,
+    // so the mirrored stores of a warp are 32 consecutive entries of one
+    // row); in a tile with jt == ib the entries j >= i are stored and those
+    // with j > i mirrored; jt < ib is left to its mirror.  Every stored
+    // pair S_ij, S_ji is one accumulator value, so S is exactly symmetric.
     const int q = warp & 3, r = q * 32 + lane, et = threadIdx.x - 64;
     const int64_t i = (int64_t)ib * 128 + r;
     const bool vrow = i < a.n;
     const float inv_i = vrow ? (float)a.inv_d[i] : 0.f;
     const uint32_t trow = tbase + ((uint32_t)(q * 32) << 16);
     const int64_t j0 = (int64_t)jb * 256;
+    int mode[2];  // 0 skip, 1 store, 2 store and mirror
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int jt = 2 * jb + h;
+      mode[h] = ((int64_t)jt * 128 >= a.n || jt < ib) ? 0 : (jt == ib ? 1 : 2);
+    }
     const bool ok = warp_wait_idle(accf, 0, abort_flag);
     if (!ok && lane == 0) {
       set_err(a.err, 33);
@@ -222,17 +242,26 @@ __global__ void __launch_bounds__(kDepThreads, 1)
       if (j == i) return 1.f;
       return fminf(1.f, fabsf(__uint_as_float(bits)) * inv_i * invj[c]);
     };
+    // how many stored entries the value of column c stands for (0, 1, 2)
+    auto wgt = [&](int md, int c) -> float {
+      const int64_t j = j0 + c;
+      if (md == 2) return 2.f;
+      return j > i ? 2.f : (j == i ? 1.f : 0.f);
+    };
     double sq = 0.0;
     if (a.out == 2) {
       // per 128 x 128 half: amax, then the tile scale, then the codes
       float amax[2] = {0.f, 0.f};
       for (int c0 = 0; c0 < 256 && ok; c0 += 32) {
+        if (!mode[c0 >> 7]) continue;
         uint32_t x[32];
 #pragma unroll
         for (int u = 0; u < 4; ++u) tmem_ld8_nw(trow + c0 + 8 * u, x, 8 * u);
         tmem_wait_ld_all(x);
+        const int md = mode[c0 >> 7];
 #pragma unroll
-        for (int u = 0; u < 32; ++u) amax[c0 >> 7] = fmaxf(amax[c0 >> 7], sval(x[u], c0 + u));
+        for (int u = 0; u < 32; ++u)
+          if (wgt(md, c0 + u) > 0.f) amax[c0 >> 7] = fmaxf(amax[c0 >> 7], sval(x[u], c0 + u));
       }
 #pragma unroll
       for (int h = 0; h < 2; ++h)
@@ -253,12 +282,15 @@ __global__ void __launch_bounds__(kDepThreads, 1)
         inv_dsc[h] = 1.f / dsc[h];
       }
       dep_bar();
-      if (et < 2) {
-        const int64_t tc = (int64_t)jb * 2 + et;
-        if (tc * 128 < a.n) a.scales[(int64_t)ib * a.ld_scales + tc] = dsc[et];
+      if (et < 2 && mode[et]) {
+        const int64_t jt = (int64_t)jb * 2 + et;
+        a.scales[(int64_t)ib * a.ld_scales + jt] = dsc[et];
+        if (mode[et] == 2) a.scales[jt * a.ld_scales + ib] = dsc[et];
       }
-      uint8_t *Srow = reinterpret_cast<uint8_t *>(a.S) + i * a.lds;
+      uint8_t *S8 = reinterpret_cast<uint8_t *>(a.S);
       for (int c0 = 0; c0 < 256 && ok; c0 += 32) {
+        const int md = mode[c0 >> 7];
+        if (!md) continue;
         uint32_t x[32];
 #pragma unroll
         for (int u = 0; u < 4; ++u) tmem_ld8_nw(trow + c0 + 8 * u, x, 8 * u);
@@ -269,25 +301,30 @@ __global__ void __launch_bounds__(kDepThreads, 1)
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
           const float v = sval(x[u], c0 + u);
-          part = fmaf(v, v, part);
+          part = fmaf(wgt(md, c0 + u) * v, v, part);
           const uint32_t code = e4m3_bits(v * isc);
           if ((u & 3) == 0) w[u >> 2] = 0u;
           w[u >> 2] |= code << (8 * (u & 3));
         }
         sq += (double)part;
-        if (vrow) {
-          if (j0 + c0 + 32 <= a.n) {
-            uint4 *dst = reinterpret_cast<uint4 *>(Srow + j0 + c0);
-            dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-            dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
-          } else {
-            for (int u = 0; u < 32 && j0 + c0 + u < a.n; ++u)
-              Srow[j0 + c0 + u] = (uint8_t)(w[u >> 2] >> (8 * (u & 3)));
-          }
+        if (!vrow) continue;
+        uint8_t *Srow = S8 + i * a.lds;
+        if (md == 2 && j0 + c0 + 32 <= a.n) {
+          uint4 *dst = reinterpret_cast<uint4 *>(Srow + j0 + c0);
+          dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        } else {
+          for (int u = 0; u < 32 && j0 + c0 + u < a.n; ++u)
+            if (md == 2 || j0 + c0 + u >= i) Srow[j0 + c0 + u] = (uint8_t)(w[u >> 2] >> (8 * (u & 3)));
         }
+        for (int u = 0; u < 32 && j0 + c0 + u < a.n; ++u)
+          if (md == 2 || j0 + c0 + u > i)
+            S8[(j0 + c0 + u) * a.lds + i] = (uint8_t)(w[u >> 2] >> (8 * (u & 3)));
       }
     } else {
       for (int c0 = 0; c0 < 256 && ok; c0 += 32) {
+        const int md = mode[c0 >> 7];
+        if (!md) continue;
         uint32_t x[32];
 #pragma unroll
         for (int u = 0; u < 4; ++u) tmem_ld8_nw(trow + c0 + 8 * u, x, 8 * u);
@@ -299,23 +336,30 @@ __global__ void __launch_bounds__(kDepThreads, 1)
           float s = sval(x[u], c0 + u);
           if (a.out == 1) s = __bfloat162float(__float2bfloat16_rn(s));
           v[u] = s;
-          part = fmaf(s, s, part);
+          part = fmaf(wgt(md, c0 + u) * s, s, part);
         }
         sq += (double)part;
         if (!vrow) continue;
-        const bool whole = j0 + c0 + 32 <= a.n;
+        const bool whole = md == 2 && j0 + c0 + 32 <= a.n;
         if (a.out == 0) {
-          float *Srow = reinterpret_cast<float *>(a.S) + i * a.lds + j0 + c0;
+          float *S32 = reinterpret_cast<float *>(a.S);
+          float *Srow = S32 + i * a.lds + j0 + c0;
           if (whole) {
 #pragma unroll
             for (int u = 0; u < 8; ++u)
               reinterpret_cast<float4 *>(Srow)[u] =
                   make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
           } else {
-            for (int u = 0; u < 32 && j0 + c0 + u < a.n; ++u) Srow[u] = v[u];
+            for (int u = 0; u < 32 && j0 + c0 + u < a.n; ++u)
+              if (md == 2 || j0 + c0 + u >= i) Srow[u] = v[u];
           }
+#pragma unroll
+          for (int u = 0; u < 32; ++u)
+            if (j0 + c0 + u < a.n && (md == 2 || j0 + c0 + u > i))
+              S32[(j0 + c0 + u) * a.lds + i] = v[u];
         } else {
-          uint16_t *Srow = reinterpret_cast<uint16_t *>(a.S) + i * a.lds + j0 + c0;
+          uint16_t *S16 = reinterpret_cast<uint16_t *>(a.S);
+          uint16_t *Srow = S16 + i * a.lds + j0 + c0;
           if (whole) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -327,8 +371,13 @@ __global__ void __launch_bounds__(kDepThreads, 1)
               reinterpret_cast<uint4 *>(Srow)[u] = make_uint4(p[0], p[1], p[2], p[3]);
             }
           } else {
-            for (int u = 0; u < 32 && j0 + c0 + u < a.n; ++u) Srow[u] = bf16_bits(v[u]);
+            for (int u = 0; u < 32 && j0 + c0 + u < a.n; ++u)
+              if (md == 2 || j0 + c0 + u >= i) Srow[u] = bf16_bits(v[u]);
           }
+#pragma unroll
+          for (int u = 0; u < 32; ++u)
+            if (j0 + c0 + u < a.n && (md == 2 || j0 + c0 + u > i))
+              S16[(j0 + c0 + u) * a.lds + i] = bf16_bits(v[u]);
         }
       }
     }

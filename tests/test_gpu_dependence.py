@@ -78,6 +78,7 @@ def test_dependence_fp32(L, T, n, center):
     assert err <= tol(T), (err, tol(T))
     assert np.all(np.diag(got) == 1.0)
     assert np.all(got >= 0.0) and np.all(got <= 1.0)
+    assert np.array_equal(got, got.T)
     assert abs(nrm - float(np.sum(got * got))) <= NRM_REL * nrm
 
 
@@ -104,6 +105,7 @@ def test_dependence_fp8_codes_and_scales(L):
     q_ref, sc_ref = O.quantize_fp8(ref)
     assert np.array_equal(sc.double().cpu().numpy(), sc_ref)
     codes = S.cpu().view(torch.float8_e4m3fn).double().numpy()
+    assert np.array_equal(codes, codes.T)
     mism = codes != q_ref
     if np.any(mism):
         # only where the exact value sits within the FP32-level error of a
