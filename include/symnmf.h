@@ -313,6 +313,21 @@ int symnmf_objective_noalloc(const void *S, int64_t n, int64_t lds, int32_t dtyp
                              const float *scales, int64_t ld_scales, const float *H, int32_t k,
                              double normS2, double *f, void *stream);
 
+/* Rolling windows: rebind the handle to another matrix S of the same n and
+ * storage type (device, row pitch lds >= n; FP8 also takes its tile scales,
+ * else scales may be NULL) without reallocating.  The handle first waits
+ * for its stream, so the previous matrix may be overwritten after the call
+ * returns.  H, its MMA copy and its Gram are kept as the warm start of the
+ * new problem; the optimizer state, the snapshot, the gradient buffer, the
+ * controller and the trace start afresh, and ||S||^2 (and the K-means row
+ * norms, if computed) are recomputed for the new matrix.  The paper names
+ * rolling-window solves as future work (Sec. 8); this is the library's
+ * warm-start primitive for them.
+ * Errors: INVALID for a null S, lds < n, or FP8 without scales or with
+ * ld_scales < ceil(n/128); CUDA as for the other calls. */
+int symnmf_set_matrix(symnmf_t h, const void *S, int64_t lds, const float *scales,
+                      int64_t ld_scales);
+
 /* ------------------------------------------------- dependence matrix */
 
 /* The solver's input from data (Sec. 3, "Correlation matrices" and the

@@ -879,6 +879,39 @@ int symnmf_quantize_fp8(const void *src, int32_t src_dtype, int64_t rows, int64_
   return e == cudaSuccess ? SYMNMF_OK : SYMNMF_ERR_CUDA;
 }
 
+int symnmf_set_matrix(symnmf_t h, const void *S, int64_t lds, const float *scales,
+                      int64_t ld_scales) {
+  if (!h || !S || lds < h->n) return SYMNMF_ERR_INVALID;
+  if (h->dtype == SYMNMF_FP8E4M3 && (!scales || ld_scales < h->ntiles)) return SYMNMF_ERR_INVALID;
+  // every launch that reads the old matrix has finished
+  CK(cudaStreamSynchronize(h->stream));
+  h->S = S;
+  h->lds = lds;
+  h->tc_layout_ok = ((uintptr_t)S % 16 == 0) && ((lds * (int64_t)esize(h->dtype)) % 16 == 0);
+  if (h->dtype == SYMNMF_FP8E4M3) {
+    h->scales = scales;
+    h->ld_scales = ld_scales;
+  }
+  // H (and its MMA copy and Gram) is kept as the warm start; the optimizer
+  // state, the snapshot, the gradient, the controller and the trace start
+  // afresh for the new problem
+  const size_t bytes = sizeof(float) * (size_t)h->ntiles * kTileRows * h->kp;
+  CK(cudaMemsetAsync(h->A, 0, bytes, h->stream));
+  CK(cudaMemsetAsync(h->M, 0, bytes, h->stream));
+  CK(cudaMemsetAsync(h->mu, 0, bytes, h->stream));
+  CK(cudaMemsetAsync(h->g, 0, bytes, h->stream));
+  reset_ctrl(&h->ctrl);
+  h->trace.clear();
+  h->copied_upto = 0;
+  h->last_check = -1;
+  std::memset(&h->last_check_rec, 0, sizeof(h->last_check_rec));
+  if (h->km_rn) {
+    CK(launch_row_norms(h->S, h->n, h->lds, h->dtype, h->scales, h->ld_scales, h->km_rn,
+                        h->stream));
+  }
+  return compute_norm(h);
+}
+
 int symnmf_set_norm(symnmf_t h, double normS2) {
   if (!h || !(normS2 > 0) || !std::isfinite(normS2)) return SYMNMF_ERR_INVALID;
   h->normS2 = normS2;

@@ -1,0 +1,120 @@
+"""Rolling windows (Sec. 8 names streaming SymNMF over rolling windows as
+the next step): symnmf_set_matrix rebinds a handle to the next window's S
+and keeps H as the warm start, with the solver state fresh.  The oracle
+takes the same warm start (the GPU's H after the previous window) on the
+same stored S, so the window's trajectory is compared like a cold run."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import symnmf_oracle as O
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+OBJ_ABS = 1e-6
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2607_24518_gb300 import build
+    build.build()
+    from paper_2607_24518_gb300 import symnmf
+    return symnmf
+
+
+def _window_stream(n, T, steps, stride, seed):
+    rng = np.random.default_rng(seed)
+    k = max(2, n // 64)
+    A = rng.uniform(0.0, 1.0, size=(n, k)) * (rng.random((n, k)) < 0.3)
+    A[:, 0] = rng.uniform(0.4, 0.8, size=n)
+    Tt = T + (steps - 1) * stride
+    return (rng.standard_normal((Tt, k)) @ A.T + rng.standard_normal((Tt, n))).astype(np.float32)
+
+
+def _build(L, Y, n, lds):
+    S = torch.empty(n, lds, dtype=torch.float32, device=DEV)
+    L.symnmf_build_dependence(torch.tensor(Y, device=DEV), Y.shape[0], n, n, 1, L.F32, S, lds)
+    return S
+
+
+def test_set_matrix_matches_a_fresh_handle(L):
+    """After set_matrix the gradient and objective are those of a new handle
+    on the new S with the same H (bit for bit: the same kernels run)."""
+    n, k, T = 700, 8, 200
+    Y = _window_stream(n, T, 2, 50, seed=1)
+    lds = (n + 3) // 4 * 4
+    S1, S2 = _build(L, Y[:T], n, lds), _build(L, Y[50:50 + T], n, lds)
+    H0 = torch.rand(n, k, device=DEV, generator=torch.Generator(DEV).manual_seed(0)) * 0.2
+    h = L.symnmf_create_ld(S1, n, lds, k, L.F32)
+    h2 = L.symnmf_create_ld(S2, n, lds, k, L.F32)
+    try:
+        L.symnmf_set_H(h, H0)
+        L.symnmf_step(h, L.symnmf_hparams_default(L.ADAGRAD, eta=0.1), 7)
+        H = torch.empty(n, k, device=DEV)
+        L.symnmf_get_H(h, H)
+        L.symnmf_set_matrix(h, S2, lds)
+        L.symnmf_set_H(h2, H)
+        G1, G2 = torch.empty(n, k, device=DEV), torch.empty(n, k, device=DEV)
+        L.symnmf_grad(h, G1)
+        L.symnmf_grad(h2, G2)
+        f1, _ = L.symnmf_objective(h)
+        f2, _ = L.symnmf_objective(h2)
+        torch.cuda.synchronize()
+        assert torch.equal(G1, G2) and f1 == f2
+        assert L.symnmf_get_norm(h) == L.symnmf_get_norm(h2)
+        A = torch.empty(n, k, device=DEV)
+        L.symnmf_get_buffer(h, L.BUF_ACC, A)
+        torch.cuda.synchronize()
+        assert float(A.abs().max()) == 0.0
+        assert L.symnmf_get_ctrl(h).t == 0 and len(L.symnmf_get_trace(h)) == 0
+    finally:
+        L.symnmf_destroy(h)
+        L.symnmf_destroy(h2)
+
+
+def test_warm_started_window_matches_oracle(L):
+    """Window 1: 80 AdaGrad iterations; window 2 (stride 40): 80 more from
+    the warm start; the second window's E trajectory and final H match the
+    oracle run from the same warm start on the same stored S."""
+    n, k, T = 640, 8, 300
+    Y = _window_stream(n, T, 2, 40, seed=2)
+    lds = n
+    S1, S2 = _build(L, Y[:T], n, lds), _build(L, Y[40:40 + T], n, lds)
+    H0 = np.random.default_rng(3).uniform(0.0, 0.1, size=(n, k)).astype(np.float32)
+    hp = L.symnmf_hparams_default(L.ADAGRAD, eta=0.1)
+    h = L.symnmf_create(S1, n, k, L.F32)
+    try:
+        L.symnmf_set_H(h, torch.tensor(H0, device=DEV))
+        L.symnmf_step(h, hp, 80)
+        Hw = torch.empty(n, k, device=DEV)
+        L.symnmf_get_H(h, Hw)
+        L.symnmf_set_matrix(h, S2, lds)
+        L.symnmf_step(h, hp, 80)
+        tr = L.symnmf_get_trace(h)
+        Hg = torch.empty(n, k, device=DEV)
+        L.symnmf_get_H(h, Hg)
+        torch.cuda.synchronize()
+    finally:
+        L.symnmf_destroy(h)
+    ohp = O.HParams.paper(O.ADAGRAD)
+    ohp.eta = 0.1
+    s = O.Solver(S2.double().cpu().numpy(), Hw.double().cpu().numpy(), ohp)
+    s.run(80)
+    assert len(tr) == 80 and tr[0].t == 0
+    Eg = np.array([r.E for r in tr])
+    Er = np.array([r.E for r in s.records])
+    assert np.max(np.abs(Eg - Er)) < OBJ_ABS
+    assert O.rel_err(Hg.double().cpu().numpy(), s.H) < 1e-4
+
+
+def test_set_matrix_invalid(L):
+    n, k = 300, 4
+    S = torch.eye(n, device=DEV)
+    h = L.symnmf_create(S, n, k, L.F32)
+    try:
+        for args in ((None, n), (S, n - 1)):
+            with pytest.raises(L.SymNMFError) as e:
+                L.symnmf_set_matrix(h, *args)
+            assert e.value.status == L.ERR_INVALID
+    finally:
+        L.symnmf_destroy(h)
