@@ -534,12 +534,14 @@ def run_large_fp8(args):
 
 def run_batch(args):
     """Batching workload: 64 instances (n ~ U{2000..30000}, k in {8,16,32,64},
-    even = correlation, odd = TPDM), BF16 S, 4 random restarts each (256
-    handles, each on its own stream, the 4 restarts sharing S), Piecewise
-    AdaGrad (eta 1, c 10, c_r 10).  The library's autotuner picks the CTA
-    caps (its trial iterations are part of the solves); then the batch runs
-    to the AND rule.  Reports aggregate iterations/s and per-instance time
-    to tolerance (first restart to converge)."""
+    even = correlation, odd = TPDM), BF16 S, 4 random restarts each, Piecewise
+    AdaGrad (eta 1, c 10, c_r 10).  Where 4 k <= 64 the restarts are
+    concatenated along N in one handle (symnmf_set_restarts: one stream of S
+    feeds all four); the other instances run one handle per restart, each
+    handle on its own stream.  The library's autotuner picks the CTA caps
+    (its trial iterations are part of the solves); then the batch runs to
+    the AND rule.  Reports aggregate restart-iterations/s and per-instance
+    time to tolerance (first handle of the instance to converge)."""
     import numpy as np
     import torch
     import gen
@@ -550,7 +552,7 @@ def run_batch(args):
     torch.cuda.set_device(dev)
     specs = gen.batch_specs(args.batch_count)
     t_gen = time.perf_counter()
-    mats, handles, hps, owner, streams = [], [], [], [], []
+    mats, handles, hps, owner, streams, mult = [], [], [], [], [], []
     for i, sp in enumerate(specs):
         n, k = sp["n"], sp["k"]
         ld = -(-n // 8) * 8  # 16-byte row pitch for the tensor-core path
@@ -563,7 +565,22 @@ def run_batch(args):
         S = inst.S
         mats.append(S)
         mean = float(S[: min(n, 4096), :n].double().mean())
-        for r in range(args.restarts):
+        R = args.restarts
+        if args.joint and R * k <= 64:
+            st = torch.cuda.Stream(device=dev)
+            h = L.symnmf_create_ld(S, n, ld, R * k, L.BF16)
+            L.symnmf_set_stream(h, st)
+            L.symnmf_set_restarts(h, R)
+            H0 = np.concatenate([gen.init_scaled(mean, n, k, seed=sp["seed"], stream=r)
+                                 for r in range(R)], axis=1)
+            L.symnmf_set_H(h, torch.tensor(H0, dtype=torch.float32, device=dev))
+            handles.append(h)
+            streams.append(st)
+            hps.append(L.symnmf_hparams_default(L.PIECEWISE_ADAGRAD, eta=1.0, c=10.0, c_r=10.0))
+            owner.append(i)
+            mult.append(R)
+            continue
+        for r in range(R):
             st = torch.cuda.Stream(device=dev)
             h = L.symnmf_create_ld(S, n, ld, k, L.BF16)
             L.symnmf_set_stream(h, st)
@@ -574,6 +591,7 @@ def run_batch(args):
             streams.append(st)
             hps.append(L.symnmf_hparams_default(L.PIECEWISE_ADAGRAD, eta=1.0, c=10.0, c_r=10.0))
             owner.append(i)
+            mult.append(1)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     t0 = time.perf_counter()
@@ -594,7 +612,7 @@ def run_batch(args):
             break
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    total_iters = sum(iters_done)
+    total_iters = sum(it * m for it, m in zip(iters_done, mult))
     per_inst = []
     for i, sp in enumerate(specs):
         js = [j for j in range(len(handles)) if owner[j] == i]
@@ -612,6 +630,7 @@ def run_batch(args):
             "data": "synthetic (seeded correlation / TPDM generators, seeds 0-%d)" % (len(specs) - 1),
             "config": {"workload": "batch_%dx%d_bf16_piecewise" % (len(specs), args.restarts),
                        "instances": len(specs), "restarts": args.restarts,
+                       "handles": len(handles), "restarts_along_n": bool(args.joint),
                        "sum_n2": int(sum(sp["n"] ** 2 for sp in specs)),
                        "autotune_iters_per_candidate": args.tune_iters, "iteration_cap": args.batch_cap},
             "wall_s": wall, "total_iters": total_iters,
@@ -955,6 +974,8 @@ def main():
                     help="64 instances x 4 restarts, BF16, Piecewise AdaGrad (own JSON line)")
     ap.add_argument("--batch-count", dest="batch_count", type=int, default=64)
     ap.add_argument("--restarts", type=int, default=4)
+    ap.add_argument("--separate-restarts", dest="joint", action="store_false",
+                    help="one handle per restart even where 4 k <= 64")
     ap.add_argument("--tune-iters", dest="tune_iters", type=int, default=10)
     ap.add_argument("--batch-cap", dest="batch_cap", type=int, default=3000)
     ap.add_argument("--rolling", action="store_true",

@@ -313,6 +313,21 @@ int symnmf_objective_noalloc(const void *S, int64_t n, int64_t lds, int32_t dtyp
                              const float *scales, int64_t ld_scales, const float *H, int32_t k,
                              double normS2, double *f, void *stream);
 
+/* Independent restarts concatenated along N: a handle of rank k with
+ * restarts = R (k divisible by R) runs R solves of rank k / R on the same S
+ * from one stream of S per iteration.  Column block r of H (columns
+ * r k/R .. (r+1) k/R - 1) is restart r.  The Gram H^T H is kept block
+ * diagonal (the entries between different blocks are set to 0 when it is
+ * reduced), so H Gram gives each block its own H_r (H_r^T H_r) and every
+ * update (AdaGrad, RMSprop, ADMM's k x k inverse) acts on each restart
+ * alone; the gradient, objective, KKT measure and stopping rule are those
+ * of the concatenated problem: f = sum_r f_r, E = f / (R ||S||^2) (the
+ * restarts' mean E), ||grad_proj|| over all blocks, divided by n k.  The
+ * Piecewise reset's median is taken over all blocks together.  Call before
+ * stepping; the current H's Gram is recomputed.  Default 1.
+ * Errors: INVALID for restarts < 1 or k not divisible by restarts. */
+int symnmf_set_restarts(symnmf_t h, int32_t restarts);
+
 /* Rolling windows: rebind the handle to another matrix S of the same n and
  * storage type (device, row pitch lds >= n; FP8 also takes its tile scales,
  * else scales may be NULL) without reallocating.  The handle first waits

@@ -93,6 +93,7 @@ struct symnmf_ctx {
   double prof_bytes = 0.0;
   int64_t prof_kernels = 0;  // kernels launched by the solver loop while profiling
   int ctas = 0;              // CTA cap of the tensor-core launches (0: all SMs)
+  int restarts = 1;          // independent restarts concatenated along N
   // spherical K-means scratch, allocated by the first symnmf_spkmeans
   double *km_rn = nullptr;      // ||s_i||
   int *km_lab = nullptr;        // two label buffers of n
@@ -199,7 +200,10 @@ ReduceArgs reduce_args(symnmf_t h, const double *slots, const float *gram_part, 
   r.ntiles = h->ntiles;
   r.k = h->k;
   r.n = h->n;
-  r.normS2 = h->normS2;
+  // R restarts: f and E of the concatenated problem, sum_r f_r and its
+  // mean E (the Gram is block diagonal, so the cross terms vanish)
+  r.normS2 = h->normS2 * h->restarts;
+  r.kb = h->restarts > 1 ? h->k / h->restarts : 0;
   r.t = t;
   r.full = full;
   r.gram64_cur = h->gram64[h->cur];
@@ -513,7 +517,8 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t, bool need_g) 
       e.n1 = (int)tI.size();
     } else {
       CK(launch_gram_subset(h->gram_part[cur], h->kp, dI, (int)tI.size(), dJ, (int)tJ.size(),
-                            h->gramI, h->gramJ, h->stream));
+                            h->gramI, h->gramJ, h->restarts > 1 ? h->k / h->restarts : 0,
+                            h->stream));
       count_kernels(h, 1);
       PartLayout l1, l2;
       if ((rc = prod(h, dI, (int)tI.size(), dJ, (int)tJ.size(), h->P, &l1))) return rc;
@@ -910,6 +915,13 @@ int symnmf_set_matrix(symnmf_t h, const void *S, int64_t lds, const float *scale
                         h->stream));
   }
   return compute_norm(h);
+}
+
+int symnmf_set_restarts(symnmf_t h, int32_t restarts) {
+  if (!h || restarts < 1 || h->k % restarts != 0) return SYMNMF_ERR_INVALID;
+  h->restarts = restarts;
+  // the Gram of the current H under the new block structure
+  return refresh_derived(h);
 }
 
 int symnmf_set_norm(symnmf_t h, double normS2) {

@@ -347,6 +347,8 @@ __global__ void __launch_bounds__(128) reduce_iter_kernel(ReduceArgs a) {
       s += ordered_sum32(a.lvl1 + (int64_t)g0 * stride + e, stride, c2);
     }
     if (e >= 4 && gram) {
+      // restarts concatenated along N: only the diagonal kb x kb blocks
+      if (a.kb > 0 && (e - 4) / KP / a.kb != (e - 4) % KP / a.kb) s = 0.0;
       a.gram64_next[e - 4] = s;
       a.gram32_next[e - 4] = (float)s;
     }
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(128) reduce_iter_kernel(ReduceArgs a) {
 template <int KP>
 __global__ void __launch_bounds__(256) gram_subset_kernel(const float *gram_part, const int *l1,
                                                           int n1, const int *l2, int n2,
-                                                          float *o1, float *o2) {
+                                                          float *o1, float *o2, int kb) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= KP * KP) return;
   const int *l = blockIdx.y == 0 ? l1 : l2;
@@ -383,6 +385,7 @@ __global__ void __launch_bounds__(256) gram_subset_kernel(const float *gram_part
   float *o = blockIdx.y == 0 ? o1 : o2;
   double s = 0.0;
   for (int i = 0; i < m; ++i) s += (double)gram_part[(int64_t)l[i] * KP * KP + e];
+  if (kb > 0 && e / KP / kb != e % KP / kb) s = 0.0;
   o[e] = (float)s;
 }
 
@@ -618,9 +621,9 @@ cudaError_t launch_reduce_iter(const ReduceArgs &a, int kp, cudaStream_t s) {
 }
 
 cudaError_t launch_gram_subset(const float *gram_part, int kp, const int *l1, int n1,
-                               const int *l2, int n2, float *o1, float *o2, cudaStream_t s) {
+                               const int *l2, int n2, float *o1, float *o2, int kb, cudaStream_t s) {
   dim3 grid((kp * kp + 255) / 256, 2);
-  KP_SWITCH(kp, gram_subset_kernel<KPV><<<grid, 256, 0, s>>>(gram_part, l1, n1, l2, n2, o1, o2));
+  KP_SWITCH(kp, gram_subset_kernel<KPV><<<grid, 256, 0, s>>>(gram_part, l1, n1, l2, n2, o1, o2, kb));
   return cudaGetLastError();
 }
 

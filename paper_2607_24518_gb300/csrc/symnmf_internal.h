@@ -139,6 +139,8 @@ struct ReduceArgs {
   DevRecord *rec;            // record destination or nullptr
   double *lvl1;              // ceil(ntiles/32) x (4 + kp^2) scratch
   int *counters;             // >= ceil((4 + kp^2)/128) counters, zero between launches
+  int kb;                    // restarts along N: Gram entries whose columns lie in
+                             // different blocks of kb columns are set to 0 (0: none)
 };
 
 constexpr int kSlotStride = 4;
@@ -168,7 +170,7 @@ cudaError_t launch_prepare_tiles(const float *H, int64_t n, int k, int kp, void 
 cudaError_t launch_reduce_iter(const ReduceArgs &a, int kp, cudaStream_t s);
 // Gram of a subset of tiles (lists of tile indices) -> FP32 kp x kp, two lists
 cudaError_t launch_gram_subset(const float *gram_part, int kp, const int *list1, int n1,
-                               const int *list2, int n2, float *out1, float *out2,
+                               const int *list2, int n2, float *out1, float *out2, int kb,
                                cudaStream_t s);
 cudaError_t launch_norm_s2(const void *S, int64_t n, int64_t lds, int dtype, const float *scales,
                            int64_t ld_scales, double *partials, int nparts, double *out,

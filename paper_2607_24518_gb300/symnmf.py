@@ -78,6 +78,7 @@ def _load():
         "symnmf_set_tile_scales": [vp, vp, i64],
         "symnmf_set_norm": [vp, dbl],
         "symnmf_set_matrix": [vp, vp, i64, vp, i64],
+        "symnmf_set_restarts": [vp, i32],
         "symnmf_objective_noalloc": [vp, i64, i64, i32, vp, i64, vp, i32, dbl, vp, vp],
         "symnmf_quantize_fp8": [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, vp],
         "symnmf_get_norm": [vp, P(dbl)],
@@ -135,7 +136,7 @@ DECLARED = [
     "symnmf_state_bytes", "symnmf_get_state", "symnmf_set_state", "symnmf_last_error",
     "symnmf_status_string", "symnmf_splitmix64", "symnmf_sample_blocks",
     "symnmf_controller_check", "symnmf_objective_noalloc", "symnmf_spkmeans",
-    "symnmf_build_dependence", "symnmf_set_matrix",
+    "symnmf_build_dependence", "symnmf_set_matrix", "symnmf_set_restarts",
 ]
 
 NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -233,6 +234,11 @@ def symnmf_spkmeans(h, labels0, labels, max_iter, tol=1e-4, trace=True):
     _check(LIB.symnmf_spkmeans(h, _ptr(labels0), _ptr(labels), max_iter, float(tol), Jt,
                                C.byref(st)), h)
     return st, (list(Jt)[:st.iters] if trace else None)
+
+
+def symnmf_set_restarts(h, restarts):
+    """Run the k columns of H as `restarts` independent blocks (one S stream)."""
+    return _check(LIB.symnmf_set_restarts(h, restarts), h)
 
 
 def symnmf_set_matrix(h, S, lds, scales=None, ld_scales=0):

@@ -1,0 +1,78 @@
+"""Restarts concatenated along N: one handle of rank R k with restarts = R
+against R handles of rank k started from the matching column blocks.
+With the block-diagonal Gram every column block sees exactly the
+arithmetic of its own solve (the other blocks contribute exact zeros), so
+the blocks of H agree with the separate runs; the concatenated record's E
+is the mean of the separate E values."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2607_24518_gb300 import build
+    build.build()
+    from paper_2607_24518_gb300 import symnmf
+    return symnmf
+
+
+def _get(L, h, n, k):
+    out = torch.empty(n, k, device=DEV)
+    L.symnmf_get_H(h, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("method,iters", [(0, 40), (5, 15), (4, 24)])
+def test_joint_restarts_match_separate_solves(L, method, iters):
+    n, k, R = 704, 8, 4
+    inst = gen.tpdm_groups(n=n, groups=8, T=3000, q=0.05, seed=1)
+    S = torch.tensor(inst.S, dtype=torch.float32, device=DEV)
+    rng = np.random.default_rng(2)
+    H0 = rng.uniform(0.0, np.sqrt(float(inst.S.mean()) / k), size=(n, R * k)).astype(np.float32)
+    over = dict(eta=0.1) if method != 5 else dict(rho=50.0)
+    if method == 4:
+        over.update(phi0=0.3, snapshot_period=3)
+    hp = L.symnmf_hparams_default(method, **over)
+    hj = L.symnmf_create(S, n, R * k, L.F32)
+    hs = [L.symnmf_create(S, n, k, L.F32) for _ in range(R)]
+    try:
+        L.symnmf_set_restarts(hj, R)
+        L.symnmf_set_H(hj, torch.tensor(H0, device=DEV))
+        L.symnmf_step(hj, hp, iters)
+        Hj = _get(L, hj, n, R * k)
+        Ej = np.array([r.E for r in L.symnmf_get_trace(hj)])
+        Es = []
+        for r, h in enumerate(hs):
+            L.symnmf_set_H(h, torch.tensor(np.ascontiguousarray(H0[:, r * k:(r + 1) * k]), device=DEV))
+            L.symnmf_step(h, hp, iters)
+            Hr = _get(L, h, n, k)
+            blk = Hj[:, r * k:(r + 1) * k]
+            assert np.max(np.abs(blk - Hr)) <= 1e-6 * max(1.0, float(np.abs(Hr).max())), r
+            Es.append([rec.E for rec in L.symnmf_get_trace(h)])
+    finally:
+        L.symnmf_destroy(hj)
+        for h in hs:
+            L.symnmf_destroy(h)
+    Em = np.mean(np.array(Es), axis=0)
+    full = ~np.isnan(Ej)
+    assert np.max(np.abs(Ej[full] - Em[full])) < 1e-6
+
+
+def test_restarts_invalid(L):
+    n = 256
+    S = torch.eye(n, device=DEV)
+    h = L.symnmf_create(S, n, 8, L.F32)
+    try:
+        for R in (0, 3, 16):
+            with pytest.raises(L.SymNMFError) as e:
+                L.symnmf_set_restarts(h, R)
+            assert e.value.status == L.ERR_INVALID
+    finally:
+        L.symnmf_destroy(h)
