@@ -820,7 +820,7 @@ def run_dependence(args):
                "cores": cpu_threads(), "kind": "oracle",
                "sample": f"{it} FP64 oracle builds of a {m}-variable slice (T = {T}, {el:.1f} s)"}
     return {
-        "metric": "dependence matrix build: entries of S per second (|corr|, n = 1e5, T = 500)",
+        "metric": f"dependence matrix build: entries of S per second (|corr|, n = {n}, T = {T})",
         "value": n * n / (ms * 1e-3) / 1e9, "unit": "G entries of S per s", "n_gpus": 1,
         "steps": 3, "warmup": 1, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 in, tf32 hi/lo products, f32 out",
