@@ -13,33 +13,41 @@
 //   warps 2-9   epilogue, two threads per tile row (half the columns each):
 //               (tcgen05.ld), P = acc_hi + acc_lo, and for a finished tile
 //               runs the whole per-row update: g = 4 (H Gram_t - P), the
-//               AdaGrad / RMSprop step with the max(0, .) projection into the
-//               other H buffer, the hi/lo MMA copy of the new rows, and the
-//               tile partials tr = sum H * P, ||grad_proj||^2, sum(G), NaN
-//               count and the Gram partial H'^T H'
+//               AdaGrad / RMSprop / ADMM step with the max(0, .) projection
+//               into the other H buffer, the MMA copy of the new rows, and
+//               the tile partials tr = sum H * P, ||grad_proj||^2, sum(G),
+//               NaN count and the Gram partial H'^T H'
 //   warps 10-13 folders: fold each accumulator chain into FP32 registers and
 //               hand a finished tile segment's P over; with FP32 storage
-//               they also convert the staged S rows, see below
+//               they also convert the staged S rows, see below; with FP8
+//               storage they apply the per-unit scale of S when folding
 // Storage types:
 //   BF16  kind::f16, A = S straight from shared memory, B = [H_hi | H_lo]
 //         in bf16 (H enters with about 16 significant bits)
 //   FP32  error-compensated TF32 (after Ootomo & Yokota, IJHPCA 2022):
 //         kind::tf32 reads the staged FP32 S tile straight from shared
 //         memory and uses its 19 high bits, i.e. S_hi = S with the 13 low
-//         mantissa bits cleared; the converter warps form
-//         S_lo = round_tf32(S - S_hi) and store it in tensor memory, where a
-//         second MMA reads it as its A operand.  With B = [H_hi | H_lo] in
-//         tf32 the k-slice accumulates S_hi [H_hi | H_lo] into one
-//         accumulator and S_lo H_hi into a second one, leaving only
-//         S_lo H_lo (relative 2^-22) and the rounding of the lo parts
+//         mantissa bits cleared, against B = [H_hi | H_lo] in tf32; the
+//         converter warps form S_lo = S - S_hi (exact) and store it in
+//         tensor memory, where a second MMA reads it as its A operand: for
+//         kp <= 32 rounded to bf16 against a bf16 copy of H (kind::f16),
+//         otherwise rounded to tf32 against H_hi (kind::tf32).  What is
+//         left out is S_lo H_lo (relative 2^-21) and the rounding of the
+//         lo parts
+//   FP8   kind::f8f6f4 on the E4M3 codes of S against H as two E4M3 pieces
+//         per entry at a power-of-two factor d per 128-row tile,
+//         H ~ d (hi + lo / 16); S's tile scale over d is applied per unit
+//         when the folders fold
 // Work: the row-major list of (row tile, 128-column tile) units is split
 // into equal contiguous ranges, one per CTA (stream-K), so every SM streams
 // the same number of S bytes.  A tile whose units span several CTAs is
 // finished by the last of them to arrive (per-tile counter): the others
 // leave their FP32 partial in slot (cta + tile); the finisher adds the
 // slots in CTA order, so results do not depend on timing.  Finished tiles
-// feed the fixed-order FP64 cross-tile reduction (epi_common.cuh), whose
-// last CTA writes the Gram of H_{t+1} and the iteration record.
+// leave per-tile FP64 scalars and FP32 Gram partials; the reduction kernel
+// that follows (reduce_iter_kernel in k_epilogue.cu, overlapped with the
+// next step by programmatic dependent launch) sums them across tiles in a
+// fixed order into the Gram of H_{t+1} and the iteration record.
 // Launches over row / column lists (sampled iterations) only write the
 // partial slots; the stand-alone epilogue kernel consumes them.
 //

@@ -169,3 +169,30 @@ def test_kmeans_invalid_arguments(L):
             assert e.value.status == L.ERR_INVALID
     finally:
         L.symnmf_destroy(h)
+
+
+def test_kmeans_fp8_storage(L):
+    """FP8 storage: the operands enter the product as two E4M3 pieces
+    (error up to 2^-8 of an entry), so labels are checked for validity:
+    every label's oracle cosine (on the dequantised S) is within 2^-6 of
+    the best, and J within 2^-6 per row."""
+    from oracle import symnmf_oracle as O
+    n, Kc = 1024, 16
+    S_t, _ = _tpdm(n, Kc, seed=12)
+    S64q = S_t.double().cpu().numpy()
+    q_ref, sc_ref = O.quantize_fp8(S64q)
+    nt = (n + 127) // 128
+    q = torch.tensor(q_ref, dtype=torch.float32).to(torch.float8_e4m3fn).view(torch.uint8).to(DEV)
+    sc = torch.tensor(sc_ref, dtype=torch.float32, device=DEV)
+    S64 = O.dequantize_fp8(q_ref, sc_ref)
+    h = L.symnmf_create(q, n, Kc, L.FP8E4M3)
+    try:
+        L.symnmf_set_tile_scales(h, sc, nt)
+        lab0 = _labels(n, Kc, seed=13)
+        got, st, Jt = _run(L, h, lab0, n, 1)
+    finally:
+        L.symnmf_destroy(h)
+    ref, J, cos = K.lloyd_step(S64, lab0, Kc)
+    rows = np.arange(n)
+    assert np.all(cos[rows, got] >= cos[rows, ref] - 2.0 ** -6)
+    assert abs(Jt[0] - J) <= 2.0 ** -6 * n

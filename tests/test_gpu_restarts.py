@@ -76,3 +76,27 @@ def test_restarts_invalid(L):
             assert e.value.status == L.ERR_INVALID
     finally:
         L.symnmf_destroy(h)
+
+
+def test_joint_restarts_bf16_k64(L):
+    """BF16 storage, four restarts of rank 16 in one rank-64 handle."""
+    n, k, R = 1024, 16, 4
+    inst = gen.tpdm_groups(n=n, groups=16, T=4000, q=0.05, seed=3)
+    S = torch.tensor(inst.S, dtype=torch.bfloat16, device=DEV)
+    H0 = np.random.default_rng(4).uniform(0.0, 0.05, size=(n, R * k)).astype(np.float32)
+    hp = L.symnmf_hparams_default(L.ADAGRAD, eta=0.1)
+    hj = L.symnmf_create(S, n, R * k, L.BF16)
+    h1 = L.symnmf_create(S, n, k, L.BF16)
+    try:
+        L.symnmf_set_restarts(hj, R)
+        L.symnmf_set_H(hj, torch.tensor(H0, device=DEV))
+        L.symnmf_step(hj, hp, 20)
+        Hj = _get(L, hj, n, R * k)
+        for r in (0, 3):
+            L.symnmf_set_H(h1, torch.tensor(np.ascontiguousarray(H0[:, r * k:(r + 1) * k]), device=DEV))
+            L.symnmf_step(h1, hp, 20)
+            Hr = _get(L, h1, n, k)
+            assert np.max(np.abs(Hj[:, r * k:(r + 1) * k] - Hr)) <= 1e-6 * max(1.0, float(np.abs(Hr).max()))
+    finally:
+        L.symnmf_destroy(hj)
+        L.symnmf_destroy(h1)

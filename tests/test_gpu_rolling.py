@@ -118,3 +118,30 @@ def test_set_matrix_invalid(L):
             assert e.value.status == L.ERR_INVALID
     finally:
         L.symnmf_destroy(h)
+
+
+def test_set_matrix_fp8_takes_the_new_scales(L):
+    """FP8 storage: the rebound handle's ||S||^2 is that of a fresh handle
+    on the new codes and scales."""
+    from oracle import symnmf_oracle as O
+    n, k, T = 512, 8, 200
+    Y = _window_stream(n, T, 2, 60, seed=4)
+    nt = (n + 127) // 128
+    qs = []
+    for w in range(2):
+        S = _build(L, Y[w * 60:w * 60 + T], n, n).double().cpu().numpy()
+        q_ref, sc_ref = O.quantize_fp8(S)
+        q = torch.tensor(q_ref, dtype=torch.float32).to(torch.float8_e4m3fn).view(torch.uint8).to(DEV)
+        qs.append((q, torch.tensor(sc_ref, dtype=torch.float32, device=DEV)))
+    h = L.symnmf_create(qs[0][0], n, k, L.FP8E4M3)
+    h2 = L.symnmf_create(qs[1][0], n, k, L.FP8E4M3)
+    try:
+        L.symnmf_set_tile_scales(h, qs[0][1], nt)
+        L.symnmf_set_tile_scales(h2, qs[1][1], nt)
+        L.symnmf_set_matrix(h, qs[1][0], n, qs[1][1], nt)
+        assert L.symnmf_get_norm(h) == L.symnmf_get_norm(h2)
+        with pytest.raises(L.SymNMFError):
+            L.symnmf_set_matrix(h, qs[0][0], n)   # FP8 without scales
+    finally:
+        L.symnmf_destroy(h)
+        L.symnmf_destroy(h2)
