@@ -55,6 +55,31 @@ def test_argument_errors_without_gpu(L):
     assert e.value.status == L.ERR_INVALID
 
 
+def test_next_row_argument_errors_without_gpu(L):
+    """The dependence builder, K-means, rolling-window and restart entry
+    points reject bad arguments before any CUDA call."""
+    Y, S = 4096, 8192  # never dereferenced: validation fails first
+    bad = [
+        (None, 10, 64, 64, 1, L.F32, S, 64),        # null Y
+        (Y, 10, 64, 63, 1, L.F32, S, 64),           # ldy < n
+        (Y, 1, 64, 64, 1, L.F32, S, 64),            # T < 2 with centring
+        (Y, 0, 64, 64, 0, L.F32, S, 64),            # T < 1
+        (Y, 10, 64, 64, 1, 9, S, 64),               # unknown output type
+        (Y, 10, 64, 64, 1, L.F32, S, 63),           # lds < n
+        (Y, 10, 64, 64, 1, L.F32, S + 4, 64),       # S not 16-byte aligned
+        (Y, 10, 65, 65, 1, L.F32, S, 65),           # FP32 pitch not a multiple of 16 bytes
+        (Y, 10, 64, 64, 1, L.FP8E4M3, S, 64),       # FP8 without scales
+    ]
+    for args in bad:
+        with pytest.raises(L.SymNMFError) as e:
+            L.symnmf_build_dependence(*args)
+        assert e.value.status == L.ERR_INVALID, args
+    for fn, args in ((L.LIB.symnmf_spkmeans, (None, None, None, 1, 1e-4, None, None)),
+                     (L.LIB.symnmf_set_matrix, (None, None, 64, None, 0)),
+                     (L.LIB.symnmf_set_restarts, (None, 2))):
+        assert fn(*args) == L.ERR_INVALID
+
+
 def test_status_strings(L):
     assert L.symnmf_status_string(L.OK) == "ok"
     assert L.symnmf_status_string(L.ERR_TIMEOUT) == "device wait timed out"
