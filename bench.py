@@ -186,6 +186,65 @@ def oracle_rate(S64, H0, method, eta, budget_s=15.0, min_iters=2, max_iters=None
     return it / el, it, el
 
 
+def oracle_rate_one_thread(name, budget_s=10.0):
+    """The same oracle timing on one host thread: a child process with the
+    BLAS thread counts set to 1 before numpy loads regenerates the workload
+    on the CPU and times the oracle's iterations."""
+    import subprocess
+    kind, n, k, dt, method, eta = WORKLOADS[name]
+    if kind != "tpdm" or dt != "f32":
+        return None
+    code = (
+        "import sys, time, json\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import numpy as np, gen\n"
+        "from oracle import symnmf_oracle as O\n"
+        f"S = np.asarray(gen.tpdm_groups(n={n}, groups=32, T=5000, q=0.05, seed=0).S, dtype=np.float64)\n"
+        f"H0 = gen.init_scaled(float(S.mean()), {n}, {k}, seed=0)\n"
+        f"hp = O.HParams.paper({method})\n"
+        + (f"hp.eta = {eta}\n" if eta is not None else "")
+        + "hp.tau_g = 1e-30\n"
+        "s = O.Solver(S, H0, hp)\n"
+        "s.step()\n"
+        "t0 = time.perf_counter(); it = 0\n"
+        "while True:\n"
+        "    s.step(); it += 1; el = time.perf_counter() - t0\n"
+        f"    if it >= 2 and el >= {budget_s}: break\n"
+        "print(json.dumps({'rate': it / el, 'iters': it, 'seconds': el}))\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=600)
+        d = json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, never fatal to the bench line
+        return {"error": str(e)[:200]}
+    return {"value": d["rate"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{d['iters']} FP64 oracle iterations of the same workload on one thread "
+                      f"({d['seconds']:.1f} s; workload regenerated on the CPU)"}
+
+
+def oracle_row_rate(S_rows, H, rows, n, budget_s=10.0):
+    """Oracle iterations/s extrapolated from its gradient on a sample of
+    rows of S: a full iteration costs n / len(rows) times as much (the
+    update and the O(n k^2) terms are negligible at these sizes)."""
+    from oracle import symnmf_oracle as O
+    O.gradient_rows(S_rows, H, rows)
+    t0 = time.perf_counter()
+    it = 0
+    while True:
+        O.gradient_rows(S_rows, H, rows)
+        it += 1
+        el = time.perf_counter() - t0
+        if it >= 2 and el >= budget_s:
+            break
+    per_iter = el / it * (n / len(rows))
+    return {"value": 1.0 / per_iter, "unit": "iters/s (extrapolated)", "cores": cpu_threads(),
+            "kind": "oracle",
+            "sample": f"{it} FP64 oracle gradients of {len(rows)} rows of S ({el:.1f} s), "
+                      f"extrapolated to a full iteration (x {n / len(rows):.0f})"}
+
+
 def aggregate_ranks(ms, iters, world, device):
     """Replicas: the slowest rank's time and the iterations of all ranks
     (one value per rank; no data-path collective exists)."""
@@ -327,6 +386,9 @@ def run_native(args, rank, world, local_rank):
             cpu = {"value": rate, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
                    "sample": f"{it} FP64 oracle iterations of the same workload ({el:.1f} s, "
                              "numpy float64 on the host cores)"}
+            one = oracle_rate_one_thread(args.workload, budget_s=min(args.cpu_budget, 10.0))
+            if one is not None:
+                cpu["one_thread"] = one
         out = {
             "metric": METRIC, "value": total_iters / (ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / max(1, iters),
@@ -414,6 +476,11 @@ def run_time_to_tol(args):
         runs[name] = r
     L.symnmf_destroy(h32)
     sp = runs["fp32"]["seconds"] / runs["bf16"]["seconds"]
+    cpu = None
+    if args.cpu_baseline:
+        rows = np.arange(1024)
+        cpu = oracle_row_rate(S32[:1024].double().cpu().numpy(), H0.double().cpu().numpy(), rows,
+                              n, budget_s=min(args.cpu_budget, 10.0))
     return {"metric": "time-to-tol at n=1e5 BF16 vs FP32 (relative objective 1e-3)",
             "value": runs["bf16"]["seconds"], "unit": "s", "higher_is_better": False,
             "speedup_bf16_vs_fp32": sp, "n_gpus": 1, "data": "synthetic (seeded correlation generator)",
@@ -421,7 +488,7 @@ def run_time_to_tol(args):
             "config": {"workload": "corr_n%d_k32_adagrad_time_to_tol" % n, "n": n, "k": k,
                        "method": "adagrad", "eta": hp.eta, "tol": tol,
                        "E_star_rule": "E of an FP32 run stopped by the AND rule (or the cap)"},
-            "reference_run": ref, "E_star": Estar, "runs": runs,
+            "reference_run": ref, "E_star": Estar, "runs": runs, "cpu_baseline": cpu,
             "generation_seconds": t_gen}
 
 
@@ -512,6 +579,10 @@ def run_large_fp8(args):
     L.symnmf_set_impl(h, 1)
     f_simt, _ = L.symnmf_objective(h)
     L.symnmf_destroy(h)
+    cpu = oracle_row_rate(S_rows, H64, rows, n, budget_s=min(args.cpu_budget, 10.0)) \
+        if args.cpu_baseline else None
+    if cpu:
+        cpu["note"] = "a full-gradient iteration; a block step reads phi S (phi = 0.75)"
     iters = int(st.iter) - args.warmup
     return {"metric": "Block-SVRG AdaptGrow iters/s at n=3e5 FP8", "value": iters / (ms / 1e3),
             "unit": "iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -529,6 +600,7 @@ def run_large_fp8(args):
             "check": {"grad_rel_err_sampled_rows": grad_err, "rows": [int(t) for t in tiles],
                       "bound_two_piece_H": 2.0 ** -8,
                       "objective_tc_vs_fp32_simt_rel_normS2": abs(f_tc - f_simt) / norm_q},
+            "cpu_baseline": cpu,
             "clocks": ck, "generation_seconds": t_gen, "status": L.symnmf_status_string(status)}
 
 
