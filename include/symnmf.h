@@ -322,11 +322,21 @@ int symnmf_objective_noalloc(const void *S, int64_t n, int64_t lds, int32_t dtyp
  * update (AdaGrad, RMSprop, ADMM's k x k inverse) acts on each restart
  * alone; the gradient, objective, KKT measure and stopping rule are those
  * of the concatenated problem: f = sum_r f_r, E = f / (R ||S||^2) (the
- * restarts' mean E), ||grad_proj|| over all blocks, divided by n k.  The
+ * restarts' mean E), ||grad_proj|| over all blocks, divided by n k.  At
+ * every check each restart also gets its own E_r and KKT measure (from the
+ * gradient the step wrote: f_r = ||S||^2 - ||Gram_rr||^2 + sum(H_r .* g_r) / 2)
+ * and its own AND rule (Eq. 11); the handle stops (SYMNMF_CONVERGED) when
+ * the concatenated problem or any restart meets it, with H_t kept.  The
  * Piecewise reset's median is taken over all blocks together.  Call before
  * stepping; the current H's Gram is recomputed.  Default 1.
- * Errors: INVALID for restarts < 1 or k not divisible by restarts. */
+ * Errors: INVALID for restarts < 1 or > 8 or k not divisible by restarts;
+ * OOM when the check scratch cannot be allocated. */
 int symnmf_set_restarts(symnmf_t h, int32_t restarts);
+/* E, KKT measure and converged flag of each restart at the last check (host
+ * arrays of count >= restarts entries, any may be NULL); with one restart
+ * the handle's own. */
+int symnmf_get_restart_stats(symnmf_t h, int32_t count, double *E, double *kkt,
+                             int32_t *converged);
 
 /* Rolling windows: rebind the handle to another matrix S of the same n and
  * storage type (device, row pitch lds >= n; FP8 also takes its tile scales,

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/symnmf.h"
+#include "restart_stats.h"
 #include "symnmf_internal.h"
 
 using namespace symnmf;
@@ -94,6 +95,15 @@ struct symnmf_ctx {
   int64_t prof_kernels = 0;  // kernels launched by the solver loop while profiling
   int ctas = 0;              // CTA cap of the tensor-core launches (0: all SMs)
   int restarts = 1;          // independent restarts concatenated along N
+  // per-restart checks (restarts > 1): AND rule state and the last check
+  struct RestartCtl {
+    double E0 = NAN, E_prev = NAN;
+    bool have_prev = false;
+  };
+  std::vector<RestartCtl> rctl;
+  std::vector<double> rE, rkkt;
+  std::vector<int32_t> rconv;
+  double *rs_part = nullptr, *rs_out = nullptr, *rs_host = nullptr;  // host: pinned
   // spherical K-means scratch, allocated by the first symnmf_spkmeans
   double *km_rn = nullptr;      // ||s_i||
   int *km_lab = nullptr;        // two label buffers of n
@@ -157,10 +167,11 @@ void free_all(symnmf_t h) {
                   (void *)h->hist, (void *)h->sel, (void *)h->dmed, (void *)h->dsum,
                   (void *)h->norm_parts, (void *)h->dev_err, (void *)h->counters, (void *)h->tile_cnt,
                   (void *)h->lvl1, (void *)h->km_rn, (void *)h->km_lab, (void *)h->km_colsq,
-                  (void *)h->km_inv, (void *)h->km_slots, (void *)h->km_out})
+                  (void *)h->km_inv, (void *)h->km_slots, (void *)h->km_out, (void *)h->rs_part,
+                  (void *)h->rs_out})
     cudaFree(p);
   for (void *p : {(void *)h->hlists, (void *)h->hring, (void *)h->hsum, (void *)h->hmed,
-                  (void *)h->host_err, (void *)h->km_hout})
+                  (void *)h->host_err, (void *)h->km_hout, (void *)h->rs_host})
     if (p) cudaFreeHost(p);
   for (int i = 0; i < kStages; ++i)
     if (h->stage_ev[i]) cudaEventDestroy(h->stage_ev[i]);
@@ -661,6 +672,55 @@ int iterate_launch(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &ph
 
 // second half: the check (Eq. 11 and the method's control); returns OK,
 // CONVERGED or an error
+void reset_restart_checks(symnmf_t h) {
+  h->rctl.assign(h->restarts, symnmf_ctx::RestartCtl{});
+  h->rE.assign(h->restarts, NAN);
+  h->rkkt.assign(h->restarts, NAN);
+  h->rconv.assign(h->restarts, 0);
+}
+
+// Per-restart AND rule at check t (restarts > 1): H_t is in the other H
+// buffer (the step has flipped cur) and g holds its gradient; the Gram of
+// H_t is block diagonal.  f_r = ||S||^2 - ||Gram_rr||^2 + sum(H_r .* g_r) / 2,
+// E_r = f_r / ||S||^2, kkt_r = ||grad_proj,r|| / (n kb).  Sets *any when a
+// restart meets Eq. 11 (E0 and the stagnation test per restart, as for a
+// handle of its own).
+int restart_checks(symnmf_t h, const symnmf_hparams *hp, int64_t t, bool *any) {
+  *any = false;
+  const int R = h->restarts, kp = h->kp, kb = h->k / R;
+  const int prev = 1 - h->cur;
+  CK(launch_restart_stats(h->H[prev], h->g, h->n, h->k, kp, R, h->rs_part, h->rs_out, h->stream));
+  CK(cudaMemcpyAsync(h->rs_host, h->rs_out, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(h->rs_host + 2 * R, h->gram64[prev], sizeof(double) * kp * kp,
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  count_kernels(h, 2);
+  const double *G = h->rs_host + 2 * R;
+  const double tau_g = hp->tau_g > 0 ? hp->tau_g : 1e-4 * std::max(1.0, 1e4 / (double)h->n);
+  for (int r = 0; r < R; ++r) {
+    double g2 = 0.0;
+    for (int c = r * kb; c < (r + 1) * kb; ++c)
+      for (int d = r * kb; d < (r + 1) * kb; ++d) g2 += G[c * kp + d] * G[c * kp + d];
+    const double f = h->normS2 - g2 + 0.5 * h->rs_host[2 * r];
+    const double E = f / h->normS2;
+    const double kkt = std::sqrt(h->rs_host[2 * r + 1]) / ((double)h->n * (double)kb);
+    symnmf_ctx::RestartCtl &c = h->rctl[r];
+    if (t == 0 || !(c.E0 == c.E0)) c.E0 = E;
+    const double ratio = c.have_prev ? (c.E_prev - E) / c.E0 : NAN;
+    const bool stag = c.have_prev && t >= hp->warmup && ratio < hp->tau_stag;
+    c.E_prev = E;
+    c.have_prev = true;
+    h->rE[r] = E;
+    h->rkkt[r] = kkt;
+    if (E < hp->tau_E && kkt < tau_g && stag) {
+      h->rconv[r] = 1;
+      *any = true;
+    }
+  }
+  return SYMNMF_OK;
+}
+
 int iterate_finish(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &phis) {
   const int64_t t = h->ctrl.t;
   int rc;
@@ -681,6 +741,16 @@ int iterate_finish(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &ph
     };
     ctrl_check(&h->ctrl, hp, h->n, t, rec.E, rec.kkt, rec.sumA, med, &o);
     if (mrc) return mrc;
+    if (h->restarts > 1) {
+      // a concatenated handle stops when any of its restarts converges
+      bool any = false;
+      if ((rc = restart_checks(h, hp, t, &any))) return rc;
+      if (any && !o.converged) {
+        o.converged = true;
+        o.reset = false;
+        h->ctrl.converged = 1;
+      }
+    }
     rec.check = 1;
     rec.stag_ratio = o.ratio;
     rec.converged = o.converged ? 1 : 0;
@@ -884,6 +954,18 @@ int symnmf_quantize_fp8(const void *src, int32_t src_dtype, int64_t rows, int64_
   return e == cudaSuccess ? SYMNMF_OK : SYMNMF_ERR_CUDA;
 }
 
+int symnmf_get_restart_stats(symnmf_t h, int32_t count, double *E, double *kkt,
+                             int32_t *converged) {
+  if (!h || count < h->restarts) return SYMNMF_ERR_INVALID;
+  for (int r = 0; r < h->restarts; ++r) {
+    const bool have = h->restarts > 1 && r < (int)h->rE.size();
+    if (E) E[r] = have ? h->rE[r] : h->last_check_rec.E;
+    if (kkt) kkt[r] = have ? h->rkkt[r] : h->last_check_rec.kkt;
+    if (converged) converged[r] = have ? h->rconv[r] : h->ctrl.converged;
+  }
+  return SYMNMF_OK;
+}
+
 int symnmf_set_matrix(symnmf_t h, const void *S, int64_t lds, const float *scales,
                       int64_t ld_scales) {
   if (!h || !S || lds < h->n) return SYMNMF_ERR_INVALID;
@@ -906,6 +988,7 @@ int symnmf_set_matrix(symnmf_t h, const void *S, int64_t lds, const float *scale
   CK(cudaMemsetAsync(h->mu, 0, bytes, h->stream));
   CK(cudaMemsetAsync(h->g, 0, bytes, h->stream));
   reset_ctrl(&h->ctrl);
+  reset_restart_checks(h);
   h->trace.clear();
   h->copied_upto = 0;
   h->last_check = -1;
@@ -918,8 +1001,19 @@ int symnmf_set_matrix(symnmf_t h, const void *S, int64_t lds, const float *scale
 }
 
 int symnmf_set_restarts(symnmf_t h, int32_t restarts) {
-  if (!h || restarts < 1 || h->k % restarts != 0) return SYMNMF_ERR_INVALID;
+  if (!h || restarts < 1 || restarts > 8 || h->k % restarts != 0) return SYMNMF_ERR_INVALID;
+  if (restarts > 1 && !h->rs_part) {
+    cudaError_t e = dalloc(&h->rs_part, (size_t)h->ntiles * 16);
+    if (e == cudaSuccess) e = dalloc(&h->rs_out, 16);
+    if (e == cudaSuccess)
+      e = cudaMallocHost((void **)&h->rs_host, sizeof(double) * (16 + 64 * 64));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, SYMNMF_ERR_OOM, "restart check scratch");
+    }
+  }
   h->restarts = restarts;
+  reset_restart_checks(h);
   // the Gram of the current H under the new block structure
   return refresh_derived(h);
 }
@@ -965,6 +1059,7 @@ int symnmf_set_H(symnmf_t h, const float *H) {
   CK(cudaMemsetAsync(h->counters, 0, sizeof(int) * 64, h->stream));
   CK(cudaMemsetAsync(h->tile_cnt, 0, sizeof(int) * h->ntiles, h->stream));
   reset_ctrl(&h->ctrl);
+  reset_restart_checks(h);
   h->trace.clear();
   h->copied_upto = 0;
   h->last_check = -1;

@@ -79,6 +79,7 @@ def _load():
         "symnmf_set_norm": [vp, dbl],
         "symnmf_set_matrix": [vp, vp, i64, vp, i64],
         "symnmf_set_restarts": [vp, i32],
+        "symnmf_get_restart_stats": [vp, i32, P(dbl), P(dbl), P(i32)],
         "symnmf_objective_noalloc": [vp, i64, i64, i32, vp, i64, vp, i32, dbl, vp, vp],
         "symnmf_quantize_fp8": [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, vp],
         "symnmf_get_norm": [vp, P(dbl)],
@@ -137,6 +138,7 @@ DECLARED = [
     "symnmf_status_string", "symnmf_splitmix64", "symnmf_sample_blocks",
     "symnmf_controller_check", "symnmf_objective_noalloc", "symnmf_spkmeans",
     "symnmf_build_dependence", "symnmf_set_matrix", "symnmf_set_restarts",
+    "symnmf_get_restart_stats",
 ]
 
 NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -239,6 +241,15 @@ def symnmf_spkmeans(h, labels0, labels, max_iter, tol=1e-4, trace=True):
 def symnmf_set_restarts(h, restarts):
     """Run the k columns of H as `restarts` independent blocks (one S stream)."""
     return _check(LIB.symnmf_set_restarts(h, restarts), h)
+
+
+def symnmf_get_restart_stats(h, count):
+    """Per-restart (E, kkt, converged) lists at the last check."""
+    E = (C.c_double * count)()
+    kkt = (C.c_double * count)()
+    cv = (C.c_int32 * count)()
+    _check(LIB.symnmf_get_restart_stats(h, count, E, kkt, cv), h)
+    return list(E), list(kkt), list(cv)
 
 
 def symnmf_set_matrix(h, S, lds, scales=None, ld_scales=0):

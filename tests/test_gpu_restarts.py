@@ -100,3 +100,68 @@ def test_joint_restarts_bf16_k64(L):
     finally:
         L.symnmf_destroy(hj)
         L.symnmf_destroy(h1)
+
+
+def test_restart_checks_match_separate_records(L):
+    """At each check every restart's E_r and KKT measure equal the records
+    of its separate solve.  E_r is formed from the gradient the step wrote
+    (f_r = ||S||^2 - ||Gram_rr||^2 + sum H_r .* g_r / 2), the separate record
+    by the trace form; both carry the FP32 gradient's error, a few units of
+    1e-6 relative to ||S||^2."""
+    n, k, R = 704, 8, 4
+    inst = gen.tpdm_groups(n=n, groups=8, T=3000, q=0.05, seed=5)
+    S = torch.tensor(inst.S, dtype=torch.float32, device=DEV)
+    H0 = np.random.default_rng(6).uniform(0.0, np.sqrt(float(inst.S.mean()) / k),
+                                          size=(n, R * k)).astype(np.float32)
+    hp = L.symnmf_hparams_default(L.ADAGRAD, eta=0.1)
+    hj = L.symnmf_create(S, n, R * k, L.F32)
+    hs = [L.symnmf_create(S, n, k, L.F32) for _ in range(R)]
+    try:
+        L.symnmf_set_restarts(hj, R)
+        L.symnmf_set_H(hj, torch.tensor(H0, device=DEV))
+        got = []
+        for steps in (1, 10, 10, 10):           # checks at t = 0, 10, 20, 30
+            L.symnmf_step(hj, hp, steps)
+            got.append(L.symnmf_get_restart_stats(hj, R))
+        for r, h in enumerate(hs):
+            L.symnmf_set_H(h, torch.tensor(np.ascontiguousarray(H0[:, r * k:(r + 1) * k]), device=DEV))
+            L.symnmf_step(h, hp, 31)
+            tr = L.symnmf_get_trace(h)
+            for c, t in enumerate((0, 10, 20, 30)):
+                E, kkt, cv = got[c]
+                assert abs(E[r] - tr[t].E) < 5e-6, (r, t, E[r], tr[t].E)
+                assert abs(kkt[r] - tr[t].kkt) <= 1e-4 * tr[t].kkt, (r, t, kkt[r], tr[t].kkt)
+                assert cv[r] == 0
+    finally:
+        L.symnmf_destroy(hj)
+        for h in hs:
+            L.symnmf_destroy(h)
+
+
+def test_joint_handle_stops_with_its_first_converged_restart(L):
+    """Restart 0 starts next to an exact solution of S = W W^T, restart 1
+    far from it: the concatenated handle stops at the check where restart 0's
+    own solve stops, and reports which restart converged."""
+    n, k = 400, 6
+    W, S64 = gen.planted_exact(n, k, seed=2)
+    S = torch.tensor(S64, dtype=torch.float32, device=DEV)
+    rng = np.random.default_rng(0)
+    H_near = (W + rng.uniform(0, 0.05, W.shape)).astype(np.float32)
+    H_far = rng.uniform(0, 0.05, W.shape).astype(np.float32)
+    hp = L.symnmf_hparams_default(L.ADAGRAD, eta=0.05)
+    h1 = L.symnmf_create(S, n, k, L.F32)
+    hj = L.symnmf_create(S, n, 2 * k, L.F32)
+    try:
+        L.symnmf_set_H(h1, torch.tensor(H_near, device=DEV))
+        st1, s1 = L.symnmf_step(h1, hp, 3000)
+        assert st1 == L.CONVERGED
+        L.symnmf_set_restarts(hj, 2)
+        L.symnmf_set_H(hj, torch.tensor(np.concatenate([H_near, H_far], axis=1), device=DEV))
+        stj, sj = L.symnmf_step(hj, hp, 3000)
+        E, kkt, cv = L.symnmf_get_restart_stats(hj, 2)
+    finally:
+        L.symnmf_destroy(h1)
+        L.symnmf_destroy(hj)
+    assert stj == L.CONVERGED and cv == [1, 0]
+    assert sj.iter == s1.iter
+    assert E[0] < 1e-3
