@@ -425,6 +425,15 @@ typedef struct {
 int symnmf_spkmeans(symnmf_t h, const int32_t *labels0, int32_t *labels, int32_t max_iter,
                     double tol, double *J_trace, symnmf_kmeans_stats *stats);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): one
+ * thread waits, with the bounded mbarrier wait the tensor-core kernels use,
+ * on a barrier that nothing completes, for limit_s seconds (0 < limit_s <=
+ * 10), on the legacy default stream, then the call synchronises the device.
+ * Returns SYMNMF_ERR_TIMEOUT when the wait gave up and recorded its error
+ * code (the expected outcome; the context stays usable), SYMNMF_OK if it
+ * did not, INVALID for a limit out of range, CUDA for a failed launch. */
+int symnmf_selftest_wait_timeout(double limit_s);
+
 const char *symnmf_last_error(symnmf_t h);
 const char *symnmf_status_string(int32_t status);
 

@@ -80,6 +80,7 @@ def _load():
         "symnmf_set_matrix": [vp, vp, i64, vp, i64],
         "symnmf_set_restarts": [vp, i32],
         "symnmf_get_restart_stats": [vp, i32, P(dbl), P(dbl), P(i32)],
+        "symnmf_selftest_wait_timeout": [dbl],
         "symnmf_objective_noalloc": [vp, i64, i64, i32, vp, i64, vp, i32, dbl, vp, vp],
         "symnmf_quantize_fp8": [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, vp],
         "symnmf_get_norm": [vp, P(dbl)],
@@ -138,7 +139,7 @@ DECLARED = [
     "symnmf_status_string", "symnmf_splitmix64", "symnmf_sample_blocks",
     "symnmf_controller_check", "symnmf_objective_noalloc", "symnmf_spkmeans",
     "symnmf_build_dependence", "symnmf_set_matrix", "symnmf_set_restarts",
-    "symnmf_get_restart_stats",
+    "symnmf_get_restart_stats", "symnmf_selftest_wait_timeout",
 ]
 
 NOALLOC_SCRATCH_BYTES = 8 << 20

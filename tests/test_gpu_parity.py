@@ -378,3 +378,19 @@ def test_batch_step_caps_and_autotune(L):
     finally:
         for h in hs:
             L.symnmf_destroy(h)
+
+
+def test_bounded_wait_times_out_and_the_context_survives(L):
+    """A device wait on a barrier that nothing completes gives up after its
+    limit (0.2 s) and reaches the host as SYMNMF_ERR_TIMEOUT; a solve on
+    the same context afterwards is unaffected."""
+    assert L.LIB.symnmf_selftest_wait_timeout(0.2) == L.ERR_TIMEOUT
+    assert L.LIB.symnmf_selftest_wait_timeout(0.0) == L.ERR_INVALID
+    n, k = 300, 4
+    S_t, S64, H0_t, H64 = problem(n, k, seed=8)
+    with Handle(L, S_t, n, k, L.F32) as hd:
+        L.symnmf_set_H(hd.h, H0_t)
+        G = torch.empty(n, k, dtype=torch.float32, device=DEV)
+        L.symnmf_grad(hd.h, G)
+        torch.cuda.synchronize()
+        assert O.rel_err(G.double().cpu().numpy(), O.gradient(S64, H64)) < REL_FP32
