@@ -156,3 +156,25 @@ def test_controller_replay_matches_oracle(L, method):
             assert bool(c.cooldown) == co.cooldown and bool(c.resets_enabled) == co.resets_enabled
             if out.converged:
                 break
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """With the compiled library absent the binding raises ImportError: the
+    product path has no CPU fallback."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "paper_2607_24518_gb300"
+    pkg.mkdir()
+    src = os.path.join(ROOT, "paper_2607_24518_gb300")
+    for f in ("__init__.py", "symnmf.py"):
+        shutil.copy(os.path.join(src, f), pkg / f)
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "try:\n"
+            "    import paper_2607_24518_gb300.symnmf\n"
+            "except ImportError as e:\n"
+            "    print('ImportError:', e)\n"
+            "    sys.exit(0)\n"
+            "sys.exit(1)\n") % str(tmp_path)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "not built" in r.stdout, r.stdout + r.stderr
