@@ -328,7 +328,9 @@ int symnmf_objective_noalloc(const void *S, int64_t n, int64_t lds, int32_t dtyp
  * and its own AND rule (Eq. 11); the handle stops (SYMNMF_CONVERGED) when
  * the concatenated problem or any restart meets it, with H_t kept.  The
  * Piecewise reset's median is taken over all blocks together.  Call before
- * stepping; the current H's Gram is recomputed.  Default 1.
+ * stepping; the current H's Gram is recomputed.  Default 1.  The per-restart
+ * check state (each restart's E0 and previous E) is not part of the
+ * checkpoint blob: after symnmf_set_state it starts again at the next check.
  * Errors: INVALID for restarts < 1 or > 8 or k not divisible by restarts;
  * OOM when the check scratch cannot be allocated. */
 int symnmf_set_restarts(symnmf_t h, int32_t restarts);
