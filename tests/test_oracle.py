@@ -496,11 +496,13 @@ def test_gradient_rows_is_the_full_gradient_restricted():
 
 def test_hparams_match_the_printed_anchors():
     """Golden values: tests/golden/hparams_anchors.txt (appendix, Family 3;
-    Sec. 5.1 for Piecewise AdaGrad)."""
-    names = {"adagrad": O.ADAGRAD, "rmsprop": O.RMSPROP, "piecewise": O.PIECEWISE}
+    Sec. 5.1 for Piecewise AdaGrad; Sec. 5.2 and the Phase-2 configuration
+    table for ADMM's penalty)."""
+    names = {"adagrad": O.ADAGRAD, "rmsprop": O.RMSPROP, "piecewise": O.PIECEWISE,
+             "admm": O.ADMM}
     path = os.path.join(os.path.dirname(__file__), "golden", "hparams_anchors.txt")
     rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
-    assert len(rows) == 6
+    assert len(rows) == 7
     for method, param, value in rows:
         assert getattr(O.HParams.paper(names[method]), param) == float(value)
 
