@@ -14,6 +14,17 @@ Under torchrun each rank solves its own copy of the workload on its own
 GPU (replicas only: the solve has no data-parallel exchange on one box);
 the value is the sum of iterations over ranks divided by the slowest rank's
 time.  ``--impl reference`` times the FP64 CPU oracle on the host cores.
+
+Further workloads, one JSON line each:
+  --workload NAME   the other n=20000 / n=1e5 step workloads (BF16, FP8,
+                    RMSprop, ADMM, correlation)
+  --time-to-tol     n=1e5 correlation, BF16 vs FP32 time to a relative
+                    objective of 1e-3
+  --large-fp8       n=3e5 k=64 TPDM in FP8, Block-SVRG AdaptGrow
+  --batch           64 instances x 4 restarts, BF16, Piecewise AdaGrad
+  --kmeans          spherical K-means on the n=20000 TPDM matrix, K=32
+  --dependence      the |corr| build of n=1e5 variables over 500 observations
+  --rolling         10 windows: GPU |corr| build + warm-started solves
 """
 from __future__ import annotations
 
