@@ -163,6 +163,50 @@ def test_first_rmsprop_step_closed_form():
     assert np.allclose(s.H, np.maximum(H0 - m1, 0.0), rtol=1e-13, atol=1e-15)
 
 
+def _gradient_by_loops(S, H):
+    """g_ic = 4 (sum_d H_id (H^T H)_dc - sum_j S_ij H_jc), entry by entry."""
+    n, k = H.shape
+    gram = [[sum(H[j, c] * H[j, d] for j in range(n)) for d in range(k)] for c in range(k)]
+    g = np.zeros_like(H)
+    for i in range(n):
+        for c in range(k):
+            hg = sum(H[i, d] * gram[d][c] for d in range(k))
+            sh = sum(S[i, j] * H[j, c] for j in range(n))
+            g[i, c] = 4 * (hg - sh)
+    return g
+
+
+def test_rmsprop_three_steps_by_hand():
+    """RMSprop (appendix, Family 3) written out entry by entry for three
+    steps, so the momentum carry mu * m_{t-1} and the EMA of g^2 are both
+    exercised (m_0 = v_0 = 0 hides them in the first step):
+        v_t = a v_{t-1} + (1 - a) g_t^2
+        m_t = mu m_{t-1} + eta g_t / (sqrt(v_t) + eps)
+        H_{t+1} = [H_t - m_t]_+"""
+    S, H0 = _small_problem(16, 2, seed=19)
+    hp = O.HParams.paper(O.RMSPROP)
+    hp.eta = 0.02                 # small enough that no entry is clamped to 0
+    s = O.Solver(S, H0, hp)
+    H = H0.copy()
+    v = np.zeros_like(H)
+    m = np.zeros_like(H)
+    n, k = H.shape
+    for step in range(3):
+        s.step()
+        g = _gradient_by_loops(S, H)
+        for i in range(n):
+            for c in range(k):
+                v[i, c] = hp.alpha * v[i, c] + (1.0 - hp.alpha) * g[i, c] ** 2
+                m[i, c] = hp.mu * m[i, c] + hp.eta * g[i, c] / (math.sqrt(v[i, c]) + hp.eps)
+                H[i, c] = max(H[i, c] - m[i, c], 0.0)
+        assert np.allclose(s.A, v, rtol=1e-12, atol=1e-15), step
+        assert np.allclose(s.M, m, rtol=1e-12, atol=1e-15), step
+        assert np.allclose(s.H, H, rtol=1e-12, atol=1e-15), step
+    # the carried momentum is a real part of step 3 (not a vanishing term)
+    assert np.max(np.abs(hp.mu * m)) > 1e-3 * np.max(np.abs(H))
+    assert np.all(H > 0)
+
+
 def test_second_adagrad_step_by_hand():
     """Two steps written out with plain loops over entries."""
     S, H0 = _small_problem(20, 2, seed=10)
@@ -234,6 +278,63 @@ def test_block_gradient_pieces_by_loops():
             for j in I:
                 exp[i] += 2 * (H0[j] @ H0[i] - S[j, i]) * H0[j]
     assert np.allclose(g, exp, rtol=1e-12, atol=1e-12)
+
+
+def test_row_gradient_partial_fraction_by_loops():
+    """Row-Stochastic SVRG at |I| < n (Sec. 5.1; appendix): sampled rows get
+    the exact row gradient 4 (h_i (H^T H) - S_i H), every other row keeps
+    the snapshot mu_i.  The row set is a union of whole blocks, drawn as
+    ceil(frac n) rows rounded up to blocks."""
+    S, H0 = _small_problem(48, 2, seed=20)
+    hp = O.HParams.paper(O.ROW_SVRG)
+    hp.row_frac, hp.block_rows = 0.4, 8
+    s = O.Solver(S, H0, hp)
+    s.mu = np.random.default_rng(1).random(H0.shape) - 0.5
+    g = s.row_gradient(t=7)
+    I = set(s.last_I.tolist())
+    # ceil(0.4 * 48) = 20 rows -> 3 blocks of 8 = 24 rows, whole blocks
+    assert len(I) == 24 and s.last_J is None
+    assert all({b * 8 + r for r in range(8)} <= I for b in {i // 8 for i in I})
+    full = _gradient_by_loops(S, H0)
+    for i in range(48):
+        want = full[i] if i in I else s.mu[i]
+        assert np.allclose(g[i], want, rtol=1e-12, atol=1e-13), i
+    # the two parts really differ, so a wrong branch cannot pass by accident
+    assert min(np.abs(full[i] - s.mu[i]).max() for i in range(48)) > 1e-6
+
+
+def test_full_pass_schedule_and_snapshot_refresh():
+    """Stochastic methods take a full pass at t % s == 0 or t % delta == 0
+    (and Block-SVRG whenever phi = 1); that pass evaluates f, E and the KKT
+    norm at H_t and refreshes the snapshot mu = grad f(H_t).  Sampled
+    iterations leave mu unchanged and report no objective."""
+    S, H0 = _small_problem(48, 2, seed=21)
+    for method, extra in [(O.ROW_SVRG, {"row_frac": 0.5}), (O.BLOCK_SVRG, {"phi0": 0.25})]:
+        hp = O.HParams.paper(method)
+        hp.eta, hp.block_rows, hp.snapshot_period, hp.check_interval = 0.05, 8, 3, 10
+        hp.tau_g = 1e-12                   # no convergence, phi never grows here
+        for a, b in extra.items():
+            setattr(hp, a, b)
+        s = O.Solver(S, H0, hp)
+        normS2 = float(np.sum(S * S))
+        for t in range(32):
+            H_t, mu_prev = s.H.copy(), s.mu.copy()
+            rec = s.step()
+            assert rec.t == t
+            assert rec.full == (t % 3 == 0 or t % 10 == 0), (method, t)
+            if rec.full:
+                assert np.allclose(s.mu, _gradient_by_loops(S, H_t), rtol=1e-12, atol=1e-13)
+                f = float(np.sum((S - H_t @ H_t.T) ** 2))
+                assert math.isclose(rec.E, f / normS2, rel_tol=1e-10)
+            else:
+                assert np.array_equal(s.mu, mu_prev)
+                assert rec.E != rec.E          # NaN: no objective on a sampled step
+        assert s.ctrl.phi == hp.phi0 if method == O.BLOCK_SVRG else True
+    # Block-SVRG at phi = 1 is full at every iteration
+    hp = O.HParams.paper(O.BLOCK_SVRG)
+    hp.phi0, hp.snapshot_period = 1.0, 3
+    s = O.Solver(S, H0, hp)
+    assert all(s.step().full for _ in range(7))
 
 
 def test_stochastic_methods_at_full_fraction_equal_adagrad():
