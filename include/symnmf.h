@@ -131,6 +131,8 @@ typedef struct symnmf_record {
   int32_t full, check, reset, converged;
   int32_t nonfinite;       /* NaN/Inf gradient entries seen                     */
   int32_t reserved;
+  double median_g2;        /* Piecewise: lower median of the n*k values g_t^2 (FP32,
+                              radix-selected) when this check evaluated it, else NaN */
 } symnmf_record;
 
 typedef struct symnmf_stats {
@@ -273,9 +275,10 @@ int symnmf_set_state(symnmf_t h, const void *buf, size_t bytes);
 /* Size of the fixed device scratch of symnmf_objective_noalloc (8 MiB). */
 #define SYMNMF_NOALLOC_SCRATCH_BYTES (8u << 20)
 
-/* f (device, one double) = normS2 - 2 tr(H^T S H) + ||H^T H||_F^2 (Eq. 2)
- * for a caller's S and H, with no handle and no device allocation.  The
- * paper has no counterpart; this library adds it for callers that cannot
+/* f (device, one double) = normS2 - 2 tr(H^T S H) + ||H^T H||_F^2, the
+ * objective ||S - H H^T||_F^2 without the n x n residual, for a caller's S
+ * and H, with no handle and no device allocation.  The paper has no
+ * counterpart; this library adds it for callers that cannot
  * allocate at the moment they need an objective: a monitor thread that
  * must not stall a running solve (cudaMalloc and cudaFree can synchronise
  * the device), a process whose device memory is fully reserved by another
@@ -297,9 +300,14 @@ int symnmf_set_state(symnmf_t h, const void *buf, size_t bytes);
  * SYMNMF_ERR_UNSUPPORTED and launches nothing.
  * Zero state: no part of the scratch has to start at zero; every slot the
  * last kernel reads is written earlier in the same call.
- * Set-up: the first call on each device looks up that device's scratch
- * address (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture begins.
+ * Set-up: the first call on each device does that device's set-up, with
+ * that device current: looking up the scratch address (cudaGetSymbolAddress)
+ * loads this library's module on the device, which creates the scratch
+ * array and may synchronise the device, and the call then loads every
+ * kernel it can launch (with lazy module loading each would otherwise load
+ * at its first launch, inside a later call).  So make the first call at
+ * set-up time, before any stream capture begins and before the code that
+ * must not allocate runs; from then on a call only launches kernels.
  * Concurrency: all calls on one device share the one scratch, so calls
  * whose kernels can overlap in time (different streams, or host threads
  * without an order between them) race and give wrong values; order them,
@@ -312,6 +320,14 @@ int symnmf_set_state(symnmf_t h, const void *buf, size_t bytes);
 int symnmf_objective_noalloc(const void *S, int64_t n, int64_t lds, int32_t dtype,
                              const float *scales, int64_t ld_scales, const float *H, int32_t k,
                              double normS2, double *f, void *stream);
+/* Host-only check of symnmf_objective_noalloc's arguments, with no CUDA
+ * call: returns the status that entry point returns for these sizes before
+ * it launches anything (OK, INVALID or UNSUPPORTED; have_scales says
+ * whether a scales pointer would be passed) and, when need is not NULL,
+ * the scratch bytes such a call uses (also set when the size is beyond the
+ * limit).  Lets a caller size its problems ahead of time. */
+int symnmf_objective_noalloc_check(int64_t n, int64_t lds, int32_t dtype, int32_t have_scales,
+                                   int64_t ld_scales, int32_t k, size_t *need);
 
 /* Independent restarts concatenated along N: a handle of rank k with
  * restarts = R (k divisible by R) runs R solves of rank k / R on the same S

@@ -274,6 +274,7 @@ int64_t sample_count(double frac, int64_t n, int64_t block_rows) {
 struct CheckOut {
   bool converged = false, reset = false, grow = false;
   double ratio = NAN;
+  double median = NAN;  // median(g_t^2) when the check evaluated it
 };
 
 template <class MedianFn>
@@ -293,6 +294,7 @@ void ctrl_check(symnmf_ctrl *c, const symnmf_hparams *hp, int64_t n, int64_t t, 
     if (c->cooldown && sumA >= 2.0 * c->sumA_post) c->cooldown = 0;
     if (!c->cooldown && c->resets_enabled && stag && kkt > hp->c_r * tau_g) {
       const double med = median();
+      o->median = med;
       if (med > hp->eps) {
         if (c->resets > 0 && !(E < c->E_at_reset - hp->tau_stag * c->E0)) {
           c->resets_enabled = 0;
@@ -571,6 +573,7 @@ symnmf_record to_record(const DevRecord &d, double phi) {
   r.nonfinite = d.nonfinite;
   r.stag_ratio = NAN;
   r.phi = phi;
+  r.median_g2 = NAN;
   return r;
 }
 
@@ -752,6 +755,7 @@ int iterate_finish(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &ph
       }
     }
     rec.check = 1;
+    rec.median_g2 = o.median;
     rec.stag_ratio = o.ratio;
     rec.converged = o.converged ? 1 : 0;
     rec.reset = o.reset ? 1 : 0;

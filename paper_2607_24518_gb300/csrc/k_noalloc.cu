@@ -197,35 +197,100 @@ cudaError_t launch_dt(const ObjArgs &a, int kp, cudaStream_t s) {
 std::mutex g_addr_mu;
 void *g_addr[kMaxDevices] = {};
 
+// Load every kernel this entry point launches on the current device.  With
+// lazy module loading each kernel would otherwise be loaded at its first
+// launch, i.e. inside some later call, which may allocate and synchronise.
+template <int DT>
+cudaError_t preload_dt() {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tr_share_kernel<DT, 8>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tr_share_kernel<DT, 16>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tr_share_kernel<DT, 32>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tr_share_kernel<DT, 64>);
+  return e;
+}
+template <int KP>
+cudaError_t preload_kp() {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, gram_tile_kernel<KP>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, finish_kernel<KP>);
+  return e;
+}
+cudaError_t preload_kernels() {
+  cudaError_t e = preload_dt<0>();
+  if (e == cudaSuccess) e = preload_dt<1>();
+  if (e == cudaSuccess) e = preload_dt<2>();
+  if (e == cudaSuccess) e = preload_kp<8>();
+  if (e == cudaSuccess) e = preload_kp<16>();
+  if (e == cudaSuccess) e = preload_kp<32>();
+  if (e == cudaSuccess) e = preload_kp<64>();
+  return e;
+}
+
+// Argument and size check of the entry point, host arithmetic only.  On OK
+// *need is the scratch the call uses and *kp the padded rank.
+int noalloc_validate(bool have_S, int64_t n, int64_t lds, int32_t dtype, bool have_scales,
+                     int64_t ld_scales, bool have_H, int32_t k, bool have_f, size_t *need,
+                     int *kp_out) {
+  if (!have_S || !have_H || !have_f || n < 1 || lds < n || k < 1 || k > 64)
+    return SYMNMF_ERR_INVALID;
+  if (dtype != SYMNMF_F32 && dtype != SYMNMF_BF16 && dtype != SYMNMF_FP8E4M3)
+    return SYMNMF_ERR_INVALID;
+  const int64_t ntiles = (n + kTileRows - 1) / kTileRows;
+  if (dtype == SYMNMF_FP8E4M3 && (!have_scales || ld_scales < ntiles)) return SYMNMF_ERR_INVALID;
+  const int kp = k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64;
+  // scratch: ntiles * kSplit FP64 tr partials, then (256-byte aligned)
+  // ntiles * kp * kp FP32 Gram partials
+  const size_t tr_bytes = ((size_t)ntiles * kSplit * sizeof(double) + 255) & ~(size_t)255;
+  *need = tr_bytes + (size_t)ntiles * kp * kp * sizeof(float);
+  *kp_out = kp;
+  if (ntiles > 65535 || *need > (size_t)SYMNMF_NOALLOC_SCRATCH_BYTES) return SYMNMF_ERR_UNSUPPORTED;
+  return SYMNMF_OK;
+}
+
 }  // namespace
 }  // namespace symnmf
 
 using namespace symnmf;
 
+extern "C" int symnmf_objective_noalloc_check(int64_t n, int64_t lds, int32_t dtype,
+                                              int32_t have_scales, int64_t ld_scales, int32_t k,
+                                              size_t *need) {
+  size_t bytes = 0;
+  int kp = 0;
+  const int st = noalloc_validate(true, n, lds, dtype, have_scales != 0, ld_scales, true, k, true,
+                                  &bytes, &kp);
+  if (need) *need = bytes;
+  return st;
+}
+
 extern "C" int symnmf_objective_noalloc(const void *S, int64_t n, int64_t lds, int32_t dtype,
                                         const float *scales, int64_t ld_scales, const float *H,
                                         int32_t k, double normS2, double *f, void *stream) {
-  if (!S || !H || !f || n < 1 || lds < n || k < 1 || k > 64) return SYMNMF_ERR_INVALID;
-  if (dtype != SYMNMF_F32 && dtype != SYMNMF_BF16 && dtype != SYMNMF_FP8E4M3)
-    return SYMNMF_ERR_INVALID;
+  size_t need = 0;
+  int kp = 0;
+  const int st = noalloc_validate(S != nullptr, n, lds, dtype, scales != nullptr, ld_scales,
+                                  H != nullptr, k, f != nullptr, &need, &kp);
+  if (st != SYMNMF_OK) return st;
   const int64_t ntiles = (n + kTileRows - 1) / kTileRows;
-  if (dtype == SYMNMF_FP8E4M3 && (!scales || ld_scales < ntiles)) return SYMNMF_ERR_INVALID;
-  const int kp = k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64;
-  // scratch: ntiles * kSplit FP64 tr partials, then (256-byte aligned)
-  // ntiles * kp * kp FP32 Gram partials
   const size_t tr_bytes = ((size_t)ntiles * kSplit * sizeof(double) + 255) & ~(size_t)255;
-  const size_t need = tr_bytes + (size_t)ntiles * kp * kp * sizeof(float);
-  if (ntiles > 65535 || need > (size_t)SYMNMF_NOALLOC_SCRATCH_BYTES) return SYMNMF_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SYMNMF_ERR_CUDA;
   void *base = nullptr;
   {
     // first call on a device: look up that device's copy of the scratch
+    // (this loads the library's module there, creating the array) and load
+    // every kernel of this entry point, so later calls only launch
     std::lock_guard<std::mutex> lock(g_addr_mu);
-    if (!g_addr[dev] && cudaGetSymbolAddress(&g_addr[dev], g_noalloc_scratch) != cudaSuccess) {
-      g_addr[dev] = nullptr;
-      cudaGetLastError();
-      return SYMNMF_ERR_CUDA;
+    if (!g_addr[dev]) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess ||
+          preload_kernels() != cudaSuccess) {
+        cudaGetLastError();
+        return SYMNMF_ERR_CUDA;
+      }
+      g_addr[dev] = p;
     }
     base = g_addr[dev];
   }

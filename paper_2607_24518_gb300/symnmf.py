@@ -44,7 +44,8 @@ class symnmf_record(C.Structure):
     _fields_ = [("t", C.c_int64), ("f", C.c_double), ("E", C.c_double), ("kkt", C.c_double),
                 ("stag_ratio", C.c_double), ("phi", C.c_double), ("sumA", C.c_double),
                 ("full", C.c_int32), ("check", C.c_int32), ("reset", C.c_int32),
-                ("converged", C.c_int32), ("nonfinite", C.c_int32), ("reserved", C.c_int32)]
+                ("converged", C.c_int32), ("nonfinite", C.c_int32), ("reserved", C.c_int32),
+                ("median_g2", C.c_double)]
 
 
 class symnmf_stats(C.Structure):
@@ -82,6 +83,7 @@ def _load():
         "symnmf_get_restart_stats": [vp, i32, P(dbl), P(dbl), P(i32)],
         "symnmf_selftest_wait_timeout": [dbl],
         "symnmf_objective_noalloc": [vp, i64, i64, i32, vp, i64, vp, i32, dbl, vp, vp],
+        "symnmf_objective_noalloc_check": [i64, i64, i32, i32, i64, i32, P(C.c_size_t)],
         "symnmf_quantize_fp8": [vp, i32, i64, i64, i64, vp, i64, vp, i64, vp, vp],
         "symnmf_get_norm": [vp, P(dbl)],
         "symnmf_set_impl": [vp, i32],
@@ -137,7 +139,8 @@ DECLARED = [
     "symnmf_batch_autotune",
     "symnmf_state_bytes", "symnmf_get_state", "symnmf_set_state", "symnmf_last_error",
     "symnmf_status_string", "symnmf_splitmix64", "symnmf_sample_blocks",
-    "symnmf_controller_check", "symnmf_objective_noalloc", "symnmf_spkmeans",
+    "symnmf_controller_check", "symnmf_objective_noalloc", "symnmf_objective_noalloc_check",
+    "symnmf_spkmeans",
     "symnmf_build_dependence", "symnmf_set_matrix", "symnmf_set_restarts",
     "symnmf_get_restart_stats", "symnmf_selftest_wait_timeout",
 ]
@@ -218,6 +221,15 @@ def symnmf_objective_noalloc(S, n, lds, dtype, scales, ld_scales, H, k, normS2, 
         raise SymNMFError(st, "n=%d, k=%d needs %d bytes of scratch, above the fixed %d"
                           % (n, k, noalloc_scratch_need(n, k), NOALLOC_SCRATCH_BYTES))
     return _check(st)
+
+
+def symnmf_objective_noalloc_check(n, lds, dtype, have_scales, ld_scales, k):
+    """(status, scratch bytes) of symnmf_objective_noalloc for these sizes,
+    computed on the host without any CUDA call."""
+    need = C.c_size_t()
+    st = LIB.symnmf_objective_noalloc_check(n, lds, dtype, int(bool(have_scales)), ld_scales, k,
+                                            C.byref(need))
+    return st, need.value
 
 
 def symnmf_build_dependence(Y, T, n, ldy, center, out_dtype, S, lds, scales=None, ld_scales=0,

@@ -178,3 +178,27 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
             "sys.exit(1)\n") % str(tmp_path)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and "not built" in r.stdout, r.stdout + r.stderr
+
+
+def test_noalloc_size_check_on_the_host(L):
+    """symnmf_objective_noalloc's argument and size check, run on the host
+    with no CUDA call: the documented largest n per padded rank fit, one
+    more 128-row tile does not, and the scratch bytes follow
+    ceil(n/128) * 8 * 8 (256-byte aligned) + ceil(n/128) * 4 * kp^2."""
+    limits = {8: 3355392, 16: 986880, 32: 258048, 64: 65280}
+    for k, nmax in [(3, 3355392), (8, 3355392), (9, 986880), (16, 986880), (17, 258048),
+                    (32, 258048), (33, 65280), (64, 65280)]:
+        st, need = L.symnmf_objective_noalloc_check(nmax, nmax, L.F32, 0, 0, k)
+        assert st == 0 and need <= L.NOALLOC_SCRATCH_BYTES, (k, nmax)
+        assert need == L.noalloc_scratch_need(nmax, k)
+        st, need = L.symnmf_objective_noalloc_check(nmax + 128, nmax + 128, L.F32, 0, 0, k)
+        assert st == L.ERR_UNSUPPORTED and need > L.NOALLOC_SCRATCH_BYTES, (k, nmax)
+    assert sorted(limits) == [8, 16, 32, 64]
+    nt = -(-1031 // 128)
+    assert L.symnmf_objective_noalloc_check(1031, 1068, L.FP8E4M3, 1, nt, 33) == \
+        (0, (nt * 64 + 255) // 256 * 256 + nt * 4 * 64 * 64)
+    assert L.symnmf_objective_noalloc_check(1, 1, L.BF16, 0, 0, 1)[0] == 0
+    for args in [(0, 1, L.F32, 0, 0, 4), (16, 15, L.F32, 0, 0, 4), (16, 16, L.F32, 0, 0, 65),
+                 (16, 16, L.F32, 0, 0, 0), (16, 16, 7, 0, 0, 4), (16, 16, L.FP8E4M3, 0, 1, 4),
+                 (300, 300, L.FP8E4M3, 1, 2, 4)]:
+        assert L.symnmf_objective_noalloc_check(*args)[0] == L.ERR_INVALID, args

@@ -597,7 +597,7 @@ def test_gradient_rows_is_the_full_gradient_restricted():
 
 def test_hparams_match_the_printed_anchors():
     """Golden values: tests/golden/hparams_anchors.txt (appendix, Family 3;
-    Sec. 5.1 for Piecewise AdaGrad; Sec. 5.2 and the Phase-2 configuration
+    Sec. 5.1 for Piecewise AdaGrad; Sec. 5.1 and the Phase-2 configuration
     table for ADMM's penalty)."""
     names = {"adagrad": O.ADAGRAD, "rmsprop": O.RMSPROP, "piecewise": O.PIECEWISE,
              "admm": O.ADMM}
