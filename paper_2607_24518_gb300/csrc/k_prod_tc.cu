@@ -72,9 +72,7 @@ using namespace tc;
 struct TcArgs {
   int64_t W;             // units = n_rows_list * n_cols_list
   int G;                 // CTAs
-  int R;                 // leading row positions shared stream-K style
-  int D;                 // row positions owned whole by each CTA after those
-  int thr;               // fused: boundary shift limit in units (see sk_start)
+  int R;                 // row positions (tiles of 128 rows)
   int n_cols;
   const int *row_list;
   const int *col_list;
@@ -111,14 +109,20 @@ struct Cfg {
   static constexpr int FOLD = F32 ? 1 : SPU;
   // accumulator columns per part read before one wait when folding
   static constexpr int FOLD_CW = F32 ? 8 : (KP == 64 ? 16 : 32);
-  static constexpr uint32_t EPI_FLOATS = 128 * (KP + 1) + KP * KP;
+  // the epilogue's H tile; the Gram of H_t is read from global memory (L1)
+  static constexpr uint32_t EPI_FLOATS = 128 * (KP + 1);
   // + FP8: a ring of 256 unit scales after the epilogue scratch
   static constexpr uint32_t EPI_BYTES = EPI_FLOATS * 4 + 512 + (F8 ? 1024 : 0);
   static constexpr uint32_t BAR_BYTES = 512;
   static constexpr uint32_t BUDGET = 232448u - 1024u - BAR_BYTES - EPI_BYTES;
   static constexpr int STAGES = (BUDGET / STAGE) < 8u ? (int)(BUDGET / STAGE) : 8;
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + BAR_BYTES + EPI_BYTES;
-  static constexpr int THREADS = 448;  // 14 warps: TMA, MMA, 8 epilogue, 4 folder
+  // MMA issuing threads (warps 1 and 14).  One thread issues a tcgen05.mma
+  // about every 60 SM cycles at best, so a skinny-N stream of S is bounded
+  // by the issuer unless the chains are split between two of them.
+  static constexpr int NISSUE = 2;
+  // 16 warps: TMA, MMA, 8 epilogue, 4 folder, second MMA, spare
+  static constexpr int THREADS = 512;
   // FP32: TMEM columns of one S_lo buffer, number of S_lo buffers, width
   // of the separate S_lo H accumulator (0: shared with the main one)
   // (SLO16: one bf16 S_lo buffer of 32 columns per ring stage, so a
@@ -135,52 +139,54 @@ struct Cfg {
   static_assert(TMEM_NEED <= 512, "tensor memory budget exceeded");
 };
 
-// The units of CTA b: first its stream-K share [b W_R / G, (b+1) W_R / G)
-// of the R shared row positions (W_R = R n_cols), then its D whole row
-// positions R + b D .. R + b D + D - 1.  Every CTA streams the same number
-// of units and, when D > 0, ends on a tile it owns alone.
-// Within an owned tile CTA b visits the columns from rot = b n_cols / G
-// onwards (wrapping), so the CTAs do not all read the same column of S and
-// the same slice of the MMA copy of H at the same moment.
+// The units of CTA b are its stream-K share [b W / G, (b+1) W / G) of the
+// row-major unit list (W = R n_cols), so every CTA streams the same number
+// of units.  A share is made of pieces: the part of its first row
+// position, whole row positions, the part of its last row position.  A
+// fused step streams its longest piece last (ties: the last one) and the
+// rest before it, so every CTA finishes at most one row position at the
+// end of its stream, and any other row position it finishes is complete
+// with at least half of its share still to stream: the two CTAs sharing a
+// row position never both keep their part of it for last.  The two
+// segments are the two contiguous ranges in streaming order.  Without the
+// fused epilogue the order does not matter and segment 0 is the share.
 struct Segs {
   int64_t lo[2], hi[2];
-  int rot;
 };
-// First shared unit of CTA b (b = G: the end).  The even split b W_R / G is
-// moved down to a tile boundary when CTA b-1 would otherwise hold a whole
-// tile and then fewer than `thr` units of the next one: that tile's
-// epilogue and the next one's would both fall after CTA b-1's stream, while
-// CTA b absorbs the few units at the cost of a few units of streaming.
-__device__ __forceinline__ int64_t sk_start(const TcArgs &a, int b, int64_t WR) {
-  const int64_t x = (int64_t)b * WR / a.G;
-  if (!a.fused || b <= 0 || b >= a.G) return x;
-  const int64_t prev = (int64_t)(b - 1) * WR / a.G;
-  const int64_t B = x / a.n_cols * a.n_cols;
-  if (x > B && x - B < a.thr && B - a.n_cols >= prev) return B;
-  return x;
+__device__ __forceinline__ int64_t sk_start(const TcArgs &a, int b, int64_t W) {
+  return (int64_t)b * W / a.G;
 }
-// CTA holding shared unit u
-__device__ __forceinline__ int64_t sk_owner(const TcArgs &a, int64_t u, int64_t WR) {
-  int64_t b = sk_cta(u, WR, a.G);
-  if (b + 1 < a.G && u >= sk_start(a, (int)b + 1, WR)) ++b;
-  return b;
+// CTA holding unit u
+__device__ __forceinline__ int64_t sk_owner(const TcArgs &a, int64_t u, int64_t W) {
+  return sk_cta(u, W, a.G);
 }
 __device__ __forceinline__ Segs cta_segments(const TcArgs &a, int b) {
-  const int64_t WR = (int64_t)a.R * a.n_cols;
+  const int64_t W = (int64_t)a.R * a.n_cols;
+  const int64_t lo = sk_start(a, b, W), hi = sk_start(a, b + 1, W);
   Segs s;
-  s.lo[0] = sk_start(a, b, WR);
-  s.hi[0] = sk_start(a, b + 1, WR);
-  s.lo[1] = ((int64_t)a.R + (int64_t)b * a.D) * a.n_cols;
-  s.hi[1] = s.lo[1] + (int64_t)a.D * a.n_cols;
-  s.rot = (int)((int64_t)b * a.n_cols / a.G);
+  s.lo[0] = lo;
+  s.hi[0] = hi;
+  s.lo[1] = s.hi[1] = lo;
+  if (!a.fused || hi <= lo) return s;
+  int64_t mid = (hi - 1) / a.n_cols * a.n_cols;  // start of the last row position
+  if (mid <= lo) return s;                      // one piece
+  const int64_t l = hi - mid;                   // last piece
+  const int64_t f = (lo / a.n_cols + 1) * a.n_cols - lo;  // first piece
+  const bool whole_rows = (mid - lo - f) > 0;
+  if (l >= f && (!whole_rows || l >= a.n_cols)) {
+    s.hi[0] = mid;                              // the last piece goes last
+    s.lo[1] = mid;
+    s.hi[1] = hi;
+  } else {
+    s.lo[0] = mid;                              // the last piece first, then
+    s.lo[1] = lo;                               // the first piece and whole rows
+    s.hi[1] = mid;
+  }
   return s;
 }
-// column position visited for unit L of segment si
-__device__ __forceinline__ int unit_col(const TcArgs &a, const Segs &sg, int64_t L, int si) {
-  const int ci = (int)(L % a.n_cols);
-  if (si == 0) return ci;
-  const int r = ci + sg.rot;
-  return r >= a.n_cols ? r - a.n_cols : r;
+// column position visited for unit L
+__device__ __forceinline__ int unit_col(const TcArgs &a, int64_t L) {
+  return (int)(L % a.n_cols);
 }
 
 // ------------------------------------------------------------------ epilogue
@@ -254,7 +260,7 @@ __device__ __forceinline__ void tile_prep(const EpiArgs &e, int tp, float *Hs, c
     const float4 *gr = reinterpret_cast<const float4 *>(Gs + d * KP + cb);
 #pragma unroll
     for (int c4 = 0; c4 < KH / 4; ++c4) {
-      const float4 gv = gr[c4];
+      const float4 gv = __ldg(gr + c4);
       hg[4 * c4 + 0] = fmaf(hv, gv.x, hg[4 * c4 + 0]);
       hg[4 * c4 + 1] = fmaf(hv, gv.y, hg[4 * c4 + 1]);
       hg[4 * c4 + 2] = fmaf(hv, gv.z, hg[4 * c4 + 2]);
@@ -564,7 +570,7 @@ struct Hand {
 // Epilogue warps 2-5: one thread per tile row.
 template <int DT, int KP>
 __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_base, float *Hs,
-                              float *Gs, double *scratch, const Hand &hd,
+                              double *scratch, const Hand &hd,
                               volatile int *abort_flag, const Segs &sg) {
   using C = Cfg<DT, KP>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -574,10 +580,11 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
   const int half = (warp - 2) >> 2;       // column half owned
   if (!a.fused) return;
   // the Gram of H_t and the tile slots belong to the preceding reduction
-  // kernel, which may still run (programmatic dependent launch)
+  // kernel, which may still run (programmatic dependent launch).  The Gram
+  // is read from global memory: its next writer is the reduction kernel
+  // that follows this step, which starts only after this grid completes.
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  for (int i = et; i < KP * KP; i += 256) Gs[i] = e.gram[i];
-  epi_bar();
+  const float *Gs = e.gram;
   constexpr int KH = Own<KP>::KH;
   constexpr int HW = Own<KP>::HW;
   float hg[KH], av[HW], mv[HW];
@@ -592,13 +599,13 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     }
   }
   int pb = 0;
-  uint32_t pph[2] = {0u, 0u};
+  uint32_t pph = 0u;  // bit b: parity of P buffer b
   for (int si = 0; si < 2; ++si)
   for (int64_t L = sg.lo[si], L1 = sg.hi[si]; L < L1;) {
     const int tp = (int)(L / a.n_cols);
     const int64_t tile_end = (int64_t)(tp + 1) * a.n_cols;
     L = L1 < tile_end ? L1 : tile_end;
-    if (!warp_wait_idle(&hd.pfull[pb], pph[pb], abort_flag)) {
+    if (!warp_wait_idle(&hd.pfull[pb], (pph >> pb) & 1u, abort_flag)) {
       if (lane == 0) {
         set_err(a.err, 6);
         *abort_flag = 1;
@@ -622,7 +629,7 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&hd.pempty[pb]);
-    pph[pb] ^= 1;
+    pph ^= 1u << pb;
     pb ^= 1;
     if (epi == 2) {
       // shared row position: its partials in slots cta + tp, CTA order
@@ -689,7 +696,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
 #pragma unroll
   for (int c = 0; c < KP; ++c) p[c] = 0.f;
   int acc = 0, pb = 0;
-  uint32_t tph[2] = {0u, 0u}, pph[2] = {0u, 0u};
+  uint32_t tph = 0u, pph = 0u;  // bit i: parity of accumulator / P buffer i
   bool ok = true;
 
   auto fail = [&](int code) {
@@ -704,7 +711,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
   // finishes the tile), 1 (P in TMEM buffer pb, stored from p), 2 (the
   // epilogue warps add the partial slots)
   auto handoff = [&](int epi) {
-    if (!warp_wait_idle(&hd.pempty[pb], pph[pb] ^ 1, abort_flag)) {
+    if (!warp_wait_idle(&hd.pempty[pb], ((pph >> pb) & 1u) ^ 1u, abort_flag)) {
       fail(7);
       return;
     }
@@ -724,7 +731,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&hd.pfull[pb]);
-    pph[pb] ^= 1;
+    pph ^= 1u << pb;
     pb ^= 1;
   };
   // A partial left for another CTA is published (fence, arrival count)
@@ -764,9 +771,13 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       }
       epi = (b0 == b1);
     }
-    // the tile's first CTA, when every other CTA sharing the tile has
-    // already left its partial: finish here without storing its own
-    if (!epi && a.fused && b == b0) {
+    // when every other CTA sharing the tile has already left its partial,
+    // the tile is finished here without storing this CTA's own.  The sum
+    // stays in CTA order: for the first sharer its own partial comes first;
+    // for the second, own + s_b0 equals s_b0 + own exactly (floating-point
+    // addition commutes) and the later partials follow in order.  A CTA
+    // further down the order leaves its partial like any other.
+    if (!epi && a.fused && b - b0 <= 1) {
       if (ft == 0) {
         const int arrived = *reinterpret_cast<volatile int *>(&a.tile_cnt[tp]);
         const int last = (arrived == (int)(b1 - b0));
@@ -776,8 +787,8 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       fold_bar();
       if (*reinterpret_cast<volatile int *>(sflag)) {
         __threadfence();
-        // partials added in CTA order after this CTA's own (b == b0)
-        for (int64_t bb = b0 + 1; bb <= b1; ++bb) {
+        for (int64_t bb = b0; bb <= b1; ++bb) {
+          if (bb == b) continue;
           const float4 *src =
               reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP);
 #pragma unroll
@@ -821,12 +832,14 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     if (i >= nunits) return 1.f;
     const int si = i < len0 ? 0 : 1;
     const int64_t u = i < len0 ? sg.lo[0] + i : sg.lo[1] + (i - len0);
-    const int tp = (int)(u / a.n_cols), ci = unit_col(a, sg, u, si);
+    const int tp = (int)(u / a.n_cols), ci = unit_col(a, u);
     const int rt = a.row_list ? a.row_list[tp] : tp;
     const int ct = a.col_list ? a.col_list[ci] : ci;
     return __ldg(a.sS + (int64_t)rt * a.ld_sS + ct) * __ldg(a.deq + ct);
   };
   int64_t fcount = 0;  // units folded so far
+  int fold_si = -1;     // segment of the last fold, and the end of its tile row
+  int64_t tile_end = 0;
   float pre = 1.f;     // this thread's entry of the block two ahead
   if constexpr (C::F8) {
     sring[ft] = scale_of(ft);
@@ -846,7 +859,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       }
       ++fcount;
     }
-    if (!warp_wait(&tfull[acc], tph[acc], abort_flag)) {
+    if (!warp_wait(&tfull[acc], (tph >> acc) & 1u, abort_flag)) {
       fail(5);
       return;
     }
@@ -882,12 +895,18 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&tempty[acc]);
-    tph[acc] ^= 1;
+    tph ^= 1u << acc;
     acc ^= 1;
     const int64_t cend = (f + 1) * C::FOLD;
     if (cend % C::SPU == 0) {
       const int64_t u = cend / C::SPU - 1;  // unit just completed
-      if (u + 1 == Lhi || (u + 1) % a.n_cols == 0) finish_segment((int)(u / a.n_cols));
+      // end of the current tile row, stepped rather than divided per unit
+      if (si != fold_si) {
+        fold_si = si;
+        tile_end = (u / a.n_cols + 1) * a.n_cols;
+      }
+      if (u + 1 == Lhi || u + 1 == tile_end) finish_segment((int)(u / a.n_cols));
+      if (u + 1 == tile_end) tile_end += a.n_cols;
     }
     if (pend_tp >= 0 && --pend_cd <= 0 && ok) publish_pending();
   };
@@ -974,6 +993,119 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
   if (ok && pend_tp >= 0) publish_pending();
 }
 
+// MMA issuer `who` of NISSUE: issues the accumulator chains c with
+// c % NISSUE == who (chain c covers the CTA's stages [c FOLD, (c+1) FOLD)
+// and accumulates into buffer c % 2), commits each stage to its ring slot's
+// empty barrier and each finished chain to tfull.  The loop keeps its ring
+// position, phases and accumulator parities in registers and advances the
+// shared-memory descriptors by constant offsets: the issue rate of a single
+// thread bounds the stream.  On return *consumed holds the first stage this
+// issuer did not finish (the CTA's stage count when it finished all).
+template <int DT, int KP>
+__device__ __noinline__ void mma_role(const TcArgs &a, const Segs &sg, uint8_t *smem, uint32_t tmem_base,
+                         uint64_t *full, uint64_t *empty, uint64_t *afull, uint64_t *aempty,
+                         uint64_t *tfull, uint64_t *tempty, uint64_t *drain, int *consumed,
+                         volatile int *abort_flag, int who) {
+  using C = Cfg<DT, KP>;
+  constexpr int STAGES = C::STAGES;
+  constexpr int N = C::N;
+  constexpr int FOLD = C::FOLD;
+  constexpr uint32_t idesc =
+      C::F32 ? idesc_tf32(128, N) : C::F8 ? idesc_e4m3(128, N) : idesc_bf16(128, N);
+  // descriptor units are 16 bytes; stage, atom and 32-byte K-slice offsets
+  constexpr uint64_t kStageD = C::STAGE >> 4, kAtomD = kAtomBytes >> 4, kBAtomD = C::B_ATOM >> 4;
+  const uint64_t ad_base = sdesc(smem_u32(smem));
+  const int64_t nst = (sg.hi[0] - sg.lo[0] + sg.hi[1] - sg.lo[1]) * C::SPU;
+  const int64_t nchain = nst / FOLD;
+  int stage = 0;
+  uint32_t phase = 0, tph = 0;  // tph bit i: parity of accumulator i
+  int64_t g = 0;                // CTA stage index of `stage`
+  bool ok = true;
+  for (int64_t c = 0; c < nchain && ok; ++c) {
+    if ((int)(c % C::NISSUE) != who) {  // the other issuer's chain
+      g += FOLD;
+      stage += FOLD;
+      while (stage >= STAGES) {
+        stage -= STAGES;
+        phase ^= 1u;
+      }
+      continue;
+    }
+    const int acc = (int)(c & 1);
+    if (!mbar_wait(&tempty[acc], ((tph >> acc) & 1u) ^ 1u, abort_flag)) {
+      set_err(a.err, 2);
+      ok = false;
+      break;
+    }
+    const uint32_t d = tmem_base + C::ACC0 + (uint32_t)acc * C::ACCW;
+#pragma unroll
+    for (int t = 0; t < FOLD; ++t, ++g) {
+      if (!mbar_wait(&full[stage], phase, abort_flag)) {
+        set_err(a.err, 3);
+        ok = false;
+        break;
+      }
+      fence_after();
+      const uint64_t ad = ad_base + (uint64_t)stage * kStageD;
+      const uint64_t bd = ad + (C::A_BYTES >> 4);
+      const uint32_t first = (t == 0) ? 0u : 1u;
+#pragma unroll
+      for (int j = 0; j < C::KSL; ++j) {
+        const uint64_t off = (uint64_t)(j & 3) * 2u;  // 32-byte K slice within a 128-byte row
+        const uint64_t adj = ad + (uint64_t)(j >> 2) * kAtomD + off;
+        const uint64_t bdj = bd + (uint64_t)(j >> 2) * kBAtomD + off;
+        const uint32_t accum = (j == 0) ? first : 1u;
+        if constexpr (C::F32) mma_tf32_ss(d, adj, bdj, idesc, accum);
+        else if constexpr (C::F8) mma_e4m3(d, adj, bdj, idesc, accum);
+        else mma_bf16(d, adj, bdj, idesc, accum);
+      }
+      if constexpr (C::F32) {
+        // S_lo H once the converter warps have stored S_lo in TMEM: as
+        // kind::f16 against bf16(H) (kp <= 32), else as tf32 against H_hi
+        // into the H_lo part
+        const int ab = C::SLO16 ? stage : (int)(g % C::NABUF);
+        const uint32_t aparity = C::SLO16 ? phase : (uint32_t)((g / C::NABUF) & 1);
+        if (!mbar_wait(&afull[ab], aparity, abort_flag)) {
+          set_err(a.err, 3);
+          ok = false;
+          break;
+        }
+        fence_after();
+        if constexpr (C::SLO16) {
+          constexpr uint32_t idesc16 = idesc_bf16(128, C::N2);
+          const uint64_t bd2 = bd + (C::B_BYTES >> 4);
+#pragma unroll
+          for (int j = 0; j < C::APS * 2; ++j) {
+            const uint32_t alo = tmem_base + (uint32_t)ab * C::ABUF + (uint32_t)j * 8u;
+            mma_bf16_ta(d + N, alo, bd2 + (uint64_t)j * 2u, idesc16, (j == 0) ? first : 1u);
+          }
+        } else {
+          constexpr uint32_t idesc_lo = idesc_tf32(128, KP >= 16 ? KP : N);
+#pragma unroll
+          for (int j = 0; j < C::KSL; ++j) {
+            const uint64_t bdj = bd + (uint64_t)(j >> 2) * kBAtomD + (uint64_t)(j & 3) * 2u;
+            const uint32_t alo = tmem_base + (uint32_t)ab * C::ABUF + (uint32_t)j * 8u;
+            mma_tf32_ta(d + (KP >= 16 ? KP : 0), alo, bdj, idesc_lo, 1u);
+          }
+          mma_commit(&aempty[ab]);
+        }
+      }
+      mma_commit(&empty[stage]);
+      if (++stage == STAGES) {
+        stage = 0;
+        phase ^= 1u;
+      }
+    }
+    if (!ok) break;
+    mma_commit(&tfull[acc]);
+    tph ^= 1u << acc;
+  }
+  if (!ok) *abort_flag = 1;
+  consumed[who] = (int)g;
+  mma_commit(&drain[who]);
+  if (!mbar_wait(&drain[who], 0, abort_flag, 100000000ull) && !*abort_flag) set_err(a.err, 4);
+}
+
 // -------------------------------------------------------------------- kernel
 template <int DT, int KP>
 __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
@@ -995,17 +1127,15 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
   uint64_t *tempty = tfull + 2;
   uint64_t *pfull = tempty + 2;
   uint64_t *pempty = pfull + 2;
-  uint64_t *drain = pempty + 2;
-  uint32_t *holder = reinterpret_cast<uint32_t *>(drain + 1);
+  uint64_t *drain = pempty + 2;  // one per MMA issuer
+  uint32_t *holder = reinterpret_cast<uint32_t *>(drain + 2);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(holder + 1);
-  int *consumed = const_cast<int *>(abort_flag) + 1;
-  int *sflag = consumed + 1;
+  int *consumed = const_cast<int *>(abort_flag) + 1;  // one per MMA issuer
+  int *sflag = consumed + 2;
   volatile int *pflag = sflag + 1;  // two entries
   float *Hs = reinterpret_cast<float *>(smem + STAGES * C::STAGE + C::BAR_BYTES);
-  float *Gs = reinterpret_cast<float *>(
-      (reinterpret_cast<uintptr_t>(Hs + 128 * (KP + 1)) + 15) & ~uintptr_t(15));
   double *scratch = reinterpret_cast<double *>(
-      (reinterpret_cast<uintptr_t>(Gs + KP * KP) + 15) & ~uintptr_t(15));
+      (reinterpret_cast<uintptr_t>(Hs + 128 * (KP + 1)) + 15) & ~uintptr_t(15));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -1021,9 +1151,10 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
       mbar_init(&pfull[i], 4);
       mbar_init(&pempty[i], 8);
     }
-    mbar_init(drain, 1);
+    mbar_init(&drain[0], 1);
+    mbar_init(&drain[1], 1);
     *abort_flag = 0;
-    *consumed = 0;
+    consumed[0] = consumed[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(holder, C::TMEM_COLS);
@@ -1041,156 +1172,74 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
       if constexpr (C::SLO16)
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB2)) : "memory");
+      // unit coordinates are stepped, not divided: one thread issues every
+      // copy, and a 64-bit division per stage would bound the stream
       int stage = 0;
       uint32_t phase = 0;
       bool stop = false;
-      for (int si = 0; si < 2 && !stop; ++si)
-      for (int64_t c = sg.lo[si] * C::SPU; c < sg.hi[si] * C::SPU; ++c) {
-        const int64_t L = c / C::SPU;
-        const int kc = (int)(c % C::SPU);
-        const int tp = (int)(L / a.n_cols), ci = unit_col(a, sg, L, si);
-        const int rt = a.row_list ? a.row_list[tp] : tp;
-        const int ct = a.col_list ? a.col_list[ci] : ci;
-        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) {
-          set_err(a.err, 1);
-          *abort_flag = 1;
-          stop = true;
-          break;
-        }
-        uint8_t *sa = smem + stage * C::STAGE;
-        uint8_t *sb = sa + C::A_BYTES;
-        const int x0 = ct * 128 + kc * (C::APS * C::ATOM_COLS);
-        mbar_expect_tx(&full[stage], C::STAGE);
+      for (int si = 0; si < 2 && !stop; ++si) {
+        if (sg.hi[si] <= sg.lo[si]) continue;
+        int tp = (int)(sg.lo[si] / a.n_cols);
+        int ci = unit_col(a, sg.lo[si]);
+        int cpos = (int)(sg.lo[si] - (int64_t)tp * a.n_cols);
+        int rt = a.row_list ? a.row_list[tp] : tp;
+        for (int64_t L = sg.lo[si]; L < sg.hi[si] && !stop; ++L) {
+          const int ct = a.col_list ? a.col_list[ci] : ci;
+#pragma unroll 1
+          for (int kc = 0; kc < C::SPU; ++kc) {
+            if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) {
+              set_err(a.err, 1);
+              *abort_flag = 1;
+              stop = true;
+              break;
+            }
+            uint8_t *sa = smem + stage * C::STAGE;
+            uint8_t *sb = sa + C::A_BYTES;
+            const int x0 = ct * 128 + kc * (C::APS * C::ATOM_COLS);
+            mbar_expect_tx(&full[stage], C::STAGE);
 #pragma unroll
-        for (int at = 0; at < C::APS; ++at) {
-          tma_load_2d(sa + at * kAtomBytes, &mapS, &full[stage], x0 + at * C::ATOM_COLS, rt * 128);
-          tma_load_2d(sb + at * C::B_ATOM, &mapB, &full[stage], x0 + at * C::ATOM_COLS, 0);
-        }
-        if constexpr (C::SLO16)  // bf16 H^T rows for the stage's 64 columns
-          tma_load_2d(sb + C::B_BYTES, &mapB2, &full[stage], x0, 0);
-        ++issued;
-        if (++stage == STAGES) {
-          stage = 0;
-          phase ^= 1;
+            for (int at = 0; at < C::APS; ++at) {
+              tma_load_2d(sa + at * kAtomBytes, &mapS, &full[stage], x0 + at * C::ATOM_COLS, rt * 128);
+              tma_load_2d(sb + at * C::B_ATOM, &mapB, &full[stage], x0 + at * C::ATOM_COLS, 0);
+            }
+            if constexpr (C::SLO16)  // bf16 H^T rows for the stage's 64 columns
+              tma_load_2d(sb + C::B_BYTES, &mapB2, &full[stage], x0, 0);
+            ++issued;
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+          // next unit: the column steps by one (mod n_cols) and the row
+          // position advances at the end of each tile row
+          if (++ci == a.n_cols) ci = 0;
+          if (++cpos == a.n_cols && L + 1 < sg.hi[si]) {
+            cpos = 0;
+            ++tp;
+            rt = a.row_list ? a.row_list[tp] : tp;
+          }
         }
       }
     }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      int acc = 0;
-      uint32_t tph[2] = {0u, 0u};
-      uint32_t aph[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-      constexpr uint32_t idesc =
-          F32 ? idesc_tf32(128, N) : C::F8 ? idesc_e4m3(128, N) : idesc_bf16(128, N);
-      int done = 0;
-      bool stop = false;
-      for (int si = 0; si < 2 && !stop; ++si)
-      for (int64_t c = sg.lo[si] * C::SPU; c < sg.hi[si] * C::SPU; ++c) {
-        const bool seg_start = (c % C::FOLD) == 0;
-        const bool seg_end = (c % C::FOLD) == C::FOLD - 1;
-        const int ab = C::SLO16 ? stage : done % C::NABUF;
-        if (seg_start && !mbar_wait(&tempty[acc], tph[acc] ^ 1, abort_flag)) {
-          set_err(a.err, 2);
-          *abort_flag = 1;
-          stop = true;
-          break;
-        }
-        if (!mbar_wait(&full[stage], phase, abort_flag)) {
-          set_err(a.err, 3);
-          *abort_flag = 1;
-          stop = true;
-          break;
-        }
-        fence_after();
-        const uint32_t sa = smem_u32(smem + stage * C::STAGE);
-        const uint32_t sb = sa + C::A_BYTES;
-        const uint32_t d = tmem_base + C::ACC0 + (uint32_t)acc * C::ACCW;
-        if constexpr (F32) {
-          // S_hi [H_hi | H_lo] straight from the staged tile, then, once the
-          // converters have stored S_lo in TMEM, S_lo H: as kind::f16 against
-          // bf16(H) (kp <= 32), else as tf32 against H_hi into the H_lo part
-          constexpr uint32_t idesc_lo = idesc_tf32(128, KP >= 16 ? KP : N);
-#pragma unroll
-          for (int j = 0; j < C::KSL; ++j) {
-            const uint32_t within = (uint32_t)(j & 3) * 32u;
-            const uint64_t bd = sdesc(sb + (uint32_t)(j >> 2) * C::B_ATOM + within);
-            const uint64_t ad = sdesc(sa + (uint32_t)(j >> 2) * kAtomBytes + within);
-            mma_tf32_ss(d, ad, bd, idesc, (seg_start && j == 0) ? 0u : 1u);
-          }
-          if (!mbar_wait(&afull[ab], aph[ab], abort_flag)) {
-            set_err(a.err, 3);
-            *abort_flag = 1;
-            stop = true;
-            break;
-          }
-          fence_after();
-          if constexpr (C::SLO16) {
-            // bf16 S_lo (TMEM, 8 columns per k-step of 16) against bf16(H)
-            constexpr uint32_t idesc16 = idesc_bf16(128, C::N2);
-            const uint32_t sb2 = sb + C::B_BYTES;
-#pragma unroll
-            for (int j = 0; j < C::APS * 2; ++j) {
-              const uint64_t bd = sdesc(sb2 + (uint32_t)j * 32u);
-              const uint32_t alo = tmem_base + (uint32_t)ab * C::ABUF + (uint32_t)j * 8u;
-              mma_bf16_ta(d + N, alo, bd, idesc16, (seg_start && j == 0) ? 0u : 1u);
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < C::KSL; ++j) {
-              const uint32_t within = (uint32_t)(j & 3) * 32u;
-              const uint64_t bd = sdesc(sb + (uint32_t)(j >> 2) * C::B_ATOM + within);
-              const uint32_t alo = tmem_base + (uint32_t)ab * C::ABUF + (uint32_t)j * 8u;
-              mma_tf32_ta(d + (KP >= 16 ? KP : 0), alo, bd, idesc_lo, 1u);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < C::KSL; ++j) {
-            const uint32_t within = (uint32_t)(j & 3) * 32u;
-            const uint64_t bd = sdesc(sb + (uint32_t)(j >> 2) * C::B_ATOM + within);
-            const uint64_t ad = sdesc(sa + (uint32_t)(j >> 2) * kAtomBytes + within);
-            if constexpr (C::F8)
-              mma_e4m3(d, ad, bd, idesc, (seg_start && j == 0) ? 0u : 1u);
-            else
-              mma_bf16(d, ad, bd, idesc, (seg_start && j == 0) ? 0u : 1u);
-          }
-        }
-        mma_commit(&empty[stage]);
-        if (F32) {
-          if (!C::SLO16) mma_commit(&aempty[ab]);
-          aph[ab] ^= 1;
-        }
-        ++done;
-        if (seg_end) {
-          mma_commit(&tfull[acc]);
-          tph[acc] ^= 1;
-          acc ^= 1;
-        }
-        if (++stage == STAGES) {
-          stage = 0;
-          phase ^= 1;
-        }
-      }
-      *consumed = done;
-      mma_commit(drain);
-      if (!mbar_wait(drain, 0, abort_flag, 100000000ull) && !*abort_flag) set_err(a.err, 4);
-    }
-  } else if (warp >= 10) {
+  } else if (warp == 1 || (C::NISSUE == 2 && warp == 14)) {
+    if (lane == 0)
+      mma_role<DT, KP>(a, sg, smem, tmem_base, full, empty, afull, aempty, tfull, tempty, drain,
+                       consumed, abort_flag, warp == 1 ? 0 : 1);
+  } else if (warp >= 10 && warp < 14) {
     const Hand hd{pfull, pempty, pflag};
     folder_role<DT, KP>(a, tmem_base, smem, full, empty, afull, aempty, tfull, tempty, hd, sflag,
                         abort_flag, sg, b, reinterpret_cast<float *>(scratch + 64));
-  } else {
+  } else if (warp >= 2 && warp < 10) {
     const Hand hd{pfull, pempty, pflag};
-    epilogue_role<DT, KP>(a, e, tmem_base, Hs, Gs, scratch, hd, abort_flag, sg);
+    epilogue_role<DT, KP>(a, e, tmem_base, Hs, scratch, hd, abort_flag, sg);
   }
   __syncthreads();
   if (warp == 0 && lane == 0 && *abort_flag) {
     // drain TMA copies that were issued but never consumed (bounded)
-    int stage = *consumed % STAGES;
-    uint32_t phase = (uint32_t)((*consumed / STAGES) & 1);
-    for (int i = *consumed; i < issued; ++i) {
+    const int from = C::NISSUE == 2 ? min(consumed[0], consumed[1]) : consumed[0];
+    int stage = from % STAGES;
+    uint32_t phase = (uint32_t)((from / STAGES) & 1);
+    for (int i = from; i < issued; ++i) {
       int dummy = 0;
       mbar_wait(&full[stage], phase, reinterpret_cast<volatile int *>(&dummy), 100000000ull);
       if (++stage == STAGES) {
@@ -1292,14 +1341,10 @@ cudaError_t launch_step_tc(const ProdArgs &a, const EpiArgs *epi, int *tile_cnt,
   ta.err = err;
   ta.fused = (epi != nullptr) ? 1 : 0;
   ta.tile_cnt = tile_cnt;
-  // all row positions shared stream-K style (D = 0).  Owning whole tiles
-  // (D = n_rows / G) makes the R leftover tiles' last arrivers add ~G / R
-  // partials each while HBM is saturated, which measured slower.
-  ta.D = 0;
-  ta.R = a.n_rows_list - ta.D * ta.G;
-  // about half an epilogue's worth of streaming: 128 x 128 units of 64 KB
-  // (FP32), 32 KB (BF16), 16 KB (FP8) at a CTA's share of HBM bandwidth
-  ta.thr = a.dtype == 0 ? 4 : a.dtype == 1 ? 9 : 18;
+  // every row position shared stream-K style (owning whole tiles makes the
+  // leftover tiles' last arrivers add ~G / R partials each while HBM is
+  // saturated, which measured slower)
+  ta.R = a.n_rows_list;
   ta.sS = a.scales;
   ta.ld_sS = a.ld_scales;
   *G_out = ta.G;

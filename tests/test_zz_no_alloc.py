@@ -5,6 +5,8 @@ Both evaluate Eq. 2 with FP64 cross-tile sums; they differ in how S H is
 formed (FP32 FMA here, the tensor-core or SIMT product there), so they
 agree to the FP32 product error: |df| <= 1e-6 ||S||^2, the bound the
 objective tests use.  Two calls in a row must give identical bits."""
+import gc
+
 import numpy as np
 import pytest
 import torch
@@ -88,11 +90,13 @@ def test_noalloc_leaves_device_memory_untouched(L):
     after it."""
     S, lds, dt, sc, ldsc, H = _inputs(L, 1031, 33, "fp8", seed=3)
     f = torch.zeros(2, dtype=torch.float64, device=DEV)
-    L.symnmf_objective_noalloc(S, 1031, lds, dt, sc, ldsc, H, 33, 1.0, f[0:])
+    f1 = f[1:]
+    L.symnmf_objective_noalloc(S, 1031, lds, dt, sc, ldsc, H, 33, 1.0, f)
     torch.cuda.synchronize()
+    gc.collect()            # no Python temporary is freed between the readings
     before = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(),
               torch.cuda.mem_get_info()[0])
-    L.symnmf_objective_noalloc(S, 1031, lds, dt, sc, ldsc, H, 33, 1.0, f[1:])
+    L.symnmf_objective_noalloc(S, 1031, lds, dt, sc, ldsc, H, 33, 1.0, f1)
     torch.cuda.synchronize()
     after = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(),
              torch.cuda.mem_get_info()[0])
