@@ -590,11 +590,12 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
   float hg[KH], av[HW], mv[HW];
   // The tile holding this CTA's last unit is, in practice, finished here
   // (the next CTA streams the rest of it first): prepare it while idle.
-  int prepared = -1;
+  int prepared = -1, final_tp = -1;
   if constexpr (KH == HW) {
     const int last_si = (sg.hi[1] > sg.lo[1]) ? 1 : 0;
     if (sg.hi[last_si] > sg.lo[last_si]) {
-      prepared = (int)((sg.hi[last_si] - 1) / a.n_cols);
+      final_tp = (int)((sg.hi[last_si] - 1) / a.n_cols);
+      prepared = final_tp;
       tile_prep<DT, KP>(e, prepared, Hs, Gs, row, half, hg, av, mv);
     }
   }
@@ -672,6 +673,12 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
       }
       prepared = -1;
       tile_finish<DT, KP>(e, tp, p, hg, av, mv, Hs, scratch, et, row, half);
+      // a tile finished mid-stream: prepare the final one again while the
+      // stream goes on (tile_finish ends on a barrier, Hs is free)
+      if (final_tp >= 0 && tp != final_tp) {
+        prepared = final_tp;
+        tile_prep<DT, KP>(e, prepared, Hs, Gs, row, half, hg, av, mv);
+      }
     }
   }
 }

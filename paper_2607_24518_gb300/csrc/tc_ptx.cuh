@@ -43,8 +43,6 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// try_wait that lets the hardware suspend the thread for up to ns
-// nanoseconds (it resumes early when the phase completes)
 // non-blocking test of the phase with the given parity
 __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
@@ -56,6 +54,8 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait that lets the hardware suspend the thread for up to ns
+// nanoseconds (it resumes early when the phase completes)
 __device__ __forceinline__ bool mbar_try_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
   uint32_t ok;
   asm volatile(
@@ -77,13 +77,16 @@ __device__ __forceinline__ bool mbar_wait_idle(uint64_t *bar, uint32_t parity,
     if (gtimer() - t0 > kWaitNs) return false;
   }
 }
-// bounded wait; false on timeout or when another role has aborted
+// bounded wait; false on timeout or when another role has aborted.  After
+// a first plain test the thread sleeps in try_wait (it resumes as soon as
+// the phase completes): a polling thread would take issue slots from the
+// warps sharing its scheduler
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                           uint64_t limit_ns = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   while (true) {
-    if (mbar_try(bar, parity)) return true;
+    if (mbar_try_sleep(bar, parity, 2000u)) return true;
     if (*abort_flag) return false;
     if (gtimer() - t0 > limit_ns) return false;
   }
