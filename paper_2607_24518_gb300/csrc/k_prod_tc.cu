@@ -133,7 +133,12 @@ struct Cfg {
   static constexpr uint32_t ACC0 = F32 ? NABUF * ABUF : 0u;
   static constexpr uint32_t ACCW = N + NL;                // columns per accumulator buffer
   static constexpr uint32_t PB0 = ACC0 + 2 * ACCW;        // double-buffered P rows
-  static constexpr uint32_t TMEM_NEED = PB0 + 2 * KP;
+  // kp = 64: the folders keep the running sum of a tile segment in tensor
+  // memory (PA) instead of 64 registers per thread, which the 128-register
+  // budget of a 16-warp CTA cannot hold next to a fold's loads
+  static constexpr bool PTMEM = (KP == 64);
+  static constexpr uint32_t PA0 = PB0 + 2 * KP;
+  static constexpr uint32_t TMEM_NEED = PA0 + (PTMEM ? KP : 0);
   static constexpr uint32_t TMEM_COLS = TMEM_NEED <= 32 ? 32 : TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
   static_assert(STAGES >= 2, "shared memory ring too small");
   static_assert(TMEM_NEED <= 512, "tensor memory budget exceeded");
@@ -699,9 +704,12 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
   const int row = q * 32 + lane;
   const int ft = (warp - 10) * 32 + lane;
   const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-  float p[KP];
+  constexpr int NP = C::PTMEM ? 1 : KP;  // register sum (PTMEM: unused)
+  float p[NP];
 #pragma unroll
-  for (int c = 0; c < KP; ++c) p[c] = 0.f;
+  for (int c = 0; c < NP; ++c) p[c] = 0.f;
+  bool pa_first = true;                   // PTMEM: the next fold starts PA
+  const uint32_t tpa = tmem_base + lane_off + C::PA0;
   int acc = 0, pb = 0;
   uint32_t tph = 0u, pph = 0u;  // bit i: parity of accumulator / P buffer i
   bool ok = true;
@@ -725,12 +733,23 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     fence_after();
     if (epi == 1) {
       const uint32_t tb = tmem_base + lane_off + C::PB0 + (uint32_t)(pb * KP);
+      if constexpr (C::PTMEM) {
 #pragma unroll
-      for (int cc = 0; cc < KP; cc += 8) {
-        float v[8];
+        for (int cc = 0; cc < KP; cc += 16) {
+          uint32_t x[16];
+          tmem_ld8_nw(tpa + cc, x, 0);
+          tmem_ld8_nw(tpa + cc + 8, x, 8);
+          tmem_wait_ld_all(x);
+          tmem_st16(tb + cc, x);
+        }
+      } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = p[cc + j];
-        tmem_st8(tb + cc, v);
+        for (int cc = 0; cc < KP; cc += 8) {
+          float v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = p[cc + j];
+          tmem_st8(tb + cc, v);
+        }
       }
       tmem_wait_st();
     }
@@ -794,17 +813,43 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       fold_bar();
       if (*reinterpret_cast<volatile int *>(sflag)) {
         __threadfence();
-        for (int64_t bb = b0; bb <= b1; ++bb) {
-          if (bb == b) continue;
-          const float4 *src =
-              reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP);
+        if constexpr (C::PTMEM) {
+          // PA += the other partials, 16 columns at a time
+#pragma unroll 1
+          for (int cc = 0; cc < KP; cc += 16) {
+            uint32_t x[16];
+            tmem_ld8_nw(tpa + cc, x, 0);
+            tmem_ld8_nw(tpa + cc + 8, x, 8);
+            tmem_wait_ld_all(x);
+            for (int64_t bb = b0; bb <= b1; ++bb) {
+              if (bb == b) continue;
+              const float4 *src =
+                  reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP + cc);
 #pragma unroll
-          for (int c4 = 0; c4 < KP / 4; ++c4) {
-            const float4 v = __ldcg(src + c4);
-            p[4 * c4 + 0] += v.x;
-            p[4 * c4 + 1] += v.y;
-            p[4 * c4 + 2] += v.z;
-            p[4 * c4 + 3] += v.w;
+              for (int c4 = 0; c4 < 4; ++c4) {
+                const float4 v = __ldcg(src + c4);
+                x[4 * c4 + 0] = __float_as_uint(__uint_as_float(x[4 * c4 + 0]) + v.x);
+                x[4 * c4 + 1] = __float_as_uint(__uint_as_float(x[4 * c4 + 1]) + v.y);
+                x[4 * c4 + 2] = __float_as_uint(__uint_as_float(x[4 * c4 + 2]) + v.z);
+                x[4 * c4 + 3] = __float_as_uint(__uint_as_float(x[4 * c4 + 3]) + v.w);
+              }
+            }
+            tmem_st16(tpa + cc, x);
+          }
+          tmem_wait_st();
+        } else {
+          for (int64_t bb = b0; bb <= b1; ++bb) {
+            if (bb == b) continue;
+            const float4 *src =
+                reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP);
+#pragma unroll
+            for (int c4 = 0; c4 < KP / 4; ++c4) {
+              const float4 v = __ldcg(src + c4);
+              p[4 * c4 + 0] += v.x;
+              p[4 * c4 + 1] += v.y;
+              p[4 * c4 + 2] += v.z;
+              p[4 * c4 + 3] += v.w;
+            }
           }
         }
         epi = 1;
@@ -813,9 +858,24 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     }
     if (!epi) {
       float *dst = a.out + ((int64_t)(b + tp) * 128 + row) * KP;
+      if constexpr (C::PTMEM) {
 #pragma unroll
-      for (int cc = 0; cc < KP; cc += 4)
-        reinterpret_cast<float4 *>(dst + cc)[0] = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
+        for (int cc = 0; cc < KP; cc += 16) {
+          uint32_t x[16];
+          tmem_ld8_nw(tpa + cc, x, 0);
+          tmem_ld8_nw(tpa + cc + 8, x, 8);
+          tmem_wait_ld_all(x);
+#pragma unroll
+          for (int c4 = 0; c4 < 4; ++c4)
+            reinterpret_cast<float4 *>(dst + cc)[c4] =
+                make_float4(__uint_as_float(x[4 * c4]), __uint_as_float(x[4 * c4 + 1]),
+                            __uint_as_float(x[4 * c4 + 2]), __uint_as_float(x[4 * c4 + 3]));
+        }
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < KP; cc += 4)
+          reinterpret_cast<float4 *>(dst + cc)[0] = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
+      }
       if (a.fused) {
         pend_tp = tp;
         pend_b0 = b0;
@@ -826,7 +886,8 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       handoff(epi);
     }
 #pragma unroll
-    for (int c = 0; c < KP; ++c) p[c] = 0.f;
+    for (int c = 0; c < NP; ++c) p[c] = 0.f;
+    pa_first = true;
   };
   // fold accumulator chain f (stage-sized chunks [f FOLD, (f+1) FOLD))
   // FP8: the scale of each unit (S tile scale over the H tile factor) comes
@@ -876,6 +937,36 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     // loads are in flight before its one wait
     constexpr int NPART = 2 + (C::NL > 0 ? 1 : 0);
     constexpr int CW = (KP < C::FOLD_CW) ? KP : C::FOLD_CW;
+    if constexpr (C::PTMEM) {
+      // PA = (pa_first ? 0 : PA) + this chain, 16 columns per round
+#pragma unroll
+      for (int cc = 0; cc < KP; cc += 16) {
+        uint32_t x[(NPART + 1) * 16];
+#pragma unroll
+        for (int u = 0; u < 16; u += 8) {
+          tmem_ld8_nw(tb + cc + u, x, u);
+          tmem_ld8_nw(tb + KP + cc + u, x, 16 + u);
+          if constexpr (C::NL > 0) tmem_ld8_nw(tb + C::N + cc + u, x, 32 + u);
+          if (!pa_first) tmem_ld8_nw(tpa + cc + u, x, NPART * 16 + u);
+        }
+        tmem_wait_ld_all(x);
+        uint32_t o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float v;
+          if constexpr (C::F8) {
+            v = fmaf(__uint_as_float(x[16 + j]), 0.0625f, __uint_as_float(x[j])) * sc;
+          } else {
+            v = __uint_as_float(x[j]) + __uint_as_float(x[16 + j]);
+          }
+          if constexpr (C::NL > 0) v += __uint_as_float(x[32 + j]);
+          o[j] = __float_as_uint(pa_first ? v : __uint_as_float(x[NPART * 16 + j]) + v);
+        }
+        tmem_st16(tpa + cc, o);
+      }
+      tmem_wait_st();
+      pa_first = false;
+    } else
 #pragma unroll
     for (int cc = 0; cc < KP; cc += CW) {
       uint32_t x[NPART * CW];
