@@ -87,6 +87,41 @@ __device__ __forceinline__ float part_sum(const float *P, int nsplit, int skG, i
   return v;
 }
 
+// Row order of every Gram partial (H_tile^T H_tile over a 128-row tile):
+// entry (c, d) is (s_0 + s_1) + (s_2 + s_3), s_g the FMA chain over the rows
+// r = 4 i + g, i = 0..31 in order, starting from zero.  gram_entry forms it
+// from a tile in shared memory; gram_quad_sum adds the four s_g held by the
+// lanes 4 q + g of a quad (every lane of the quad gets the same bits).
+template <int KP>
+__device__ __forceinline__ float gram_entry(const float (*Hn)[KP + 1], int c, int d) {
+  float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+  for (int i = 0; i < kTileRows / 4; ++i)
+#pragma unroll
+    for (int g = 0; g < 4; ++g) s[g] = fmaf(Hn[4 * i + g][c], Hn[4 * i + g][d], s[g]);
+  return (s[0] + s[1]) + (s[2] + s[3]);
+}
+__device__ __forceinline__ float gram_quad_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  return v;
+}
+
+// (hi, lo) += (hi, lo) of lane ^ o for non-overlapping float pairs: the
+// high parts by Knuth's TwoSum (exact: s + err = a + b), the low parts and
+// err added and renormalised by Fast2Sum.  Relative error near 2^-44; both
+// lanes of the pair get the same bits.
+__device__ __forceinline__ void ff_xor_add(float &hi, float &lo, int o) {
+  const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+  const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+  const float s = __fadd_rn(hi, bh);
+  const float v = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(bh, v));
+  const float t = __fadd_rn(__fadd_rn(lo, bl), err);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
 // Sum, in index order, `count` (<= 32) values at base[i * stride]; every
 // load is issued before the ordered additions.
 template <typename T>

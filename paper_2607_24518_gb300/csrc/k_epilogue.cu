@@ -91,13 +91,8 @@ __device__ void tile_tail(const float (*Hn)[KP + 1], int64_t r0, void *Bt, int b
     }
   }
   if (gram_part) {
-    for (int q = tid; q < KP * KP; q += blockDim.x) {
-      const int c = q / KP, d = q % KP;
-      float s = 0.f;
-#pragma unroll 8
-      for (int r = 0; r < kTileRows; ++r) s = fmaf(Hn[r][c], Hn[r][d], s);
-      gram_part[(int64_t)tile * KP * KP + q] = s;
-    }
+    for (int q = tid; q < KP * KP; q += blockDim.x)
+      gram_part[(int64_t)tile * KP * KP + q] = gram_entry<KP>(Hn, q / KP, q % KP);
   }
 }
 

@@ -146,11 +146,15 @@ __global__ void __launch_bounds__(256) gram_tile_kernel(ObjArgs a) {
   }
   __syncthreads();
   for (int q = threadIdx.x; q < KP * KP; q += blockDim.x) {
+    // rows r = 4 i + g in four FMA chains, added (s0 + s1) + (s2 + s3): the
+    // row order of the solver's Gram partials
     const int c = q / KP, d = q % KP;
-    float s = 0.f;
-#pragma unroll 8
-    for (int r = 0; r < kTileRows; ++r) s = fmaf(Hn[r][c], Hn[r][d], s);
-    a.gram_part[(int64_t)tile * KP * KP + q] = s;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int i = 0; i < kTileRows / 4; ++i)
+#pragma unroll
+      for (int g = 0; g < 4; ++g) s[g] = fmaf(Hn[4 * i + g][c], Hn[4 * i + g][d], s[g]);
+    a.gram_part[(int64_t)tile * KP * KP + q] = (s[0] + s[1]) + (s[2] + s[3]);
   }
 }
 

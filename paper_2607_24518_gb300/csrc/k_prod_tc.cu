@@ -195,12 +195,12 @@ __device__ __forceinline__ int unit_col(const TcArgs &a, int64_t L) {
 }
 
 // ------------------------------------------------------------------ epilogue
-// Register-block shape of the per-thread share of the kp x kp Gram partial
+// The kp x kp Gram partial as an 8 x 8 grid of B x B blocks, one per quad
+// of the 256 epilogue threads
 template <int KP>
 struct GramBlk {
-  static constexpr int BR = KP == 64 ? 4 : KP == 32 ? 2 : 1;
-  static constexpr int BC = KP == 64 ? 4 : KP == 32 ? 2 : 1;
-  static constexpr int NBLK = (KP / BR) * (KP / BC);  // <= 256
+  static constexpr int B = KP / 8;
+  static constexpr int BP = B == 8 ? 2 : B;  // block rows summed per pass
 };
 
 // Per-tile update for the thread's row (row = tile row, et = index among the
@@ -490,41 +490,57 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
   }
   epi_bar();  // Hs holds the tile of H_{t+1}
   if (e.update && e.gram_part) {
+    // Each lane quad sums one B x B block of the 8 x 8 block grid in the
+    // Gram row order (gram_quad_sum); a warp holds 2 x 4 blocks so that
+    // its loads from Hs hit distinct banks.
     using GB = GramBlk<KP>;
-    if (et < GB::NBLK) {
-      const int cb = et / (KP / GB::BC), db = et % (KP / GB::BC);
-      const int c0 = cb * GB::BR, d0 = db * GB::BC;
-      float acc[GB::BR][GB::BC];
+    constexpr int B = GB::B, BP = GB::BP;
+    const int g = et & 3, bl = (et >> 2) & 7, wq = et >> 5;
+    const int c0 = (2 * (wq >> 1) + (bl >> 2)) * B;
+    const int d0 = (4 * (wq & 1) + (bl & 3)) * B;
+    float *gp = e.gram_part + (int64_t)tp * KP * KP;
+#pragma unroll 1
+    for (int cp = c0; cp < c0 + B; cp += BP) {  // BP block rows per pass
+      float acc[BP][B];
 #pragma unroll
-      for (int i = 0; i < GB::BR; ++i)
+      for (int i = 0; i < BP; ++i)
 #pragma unroll
-        for (int j = 0; j < GB::BC; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < B; ++j) acc[i][j] = 0.f;
 #pragma unroll 4
-      for (int r = 0; r < 128; ++r) {
-        const float *hr = Hs + r * (KP + 1);
-        float x[GB::BR], y[GB::BC];
+      for (int i = 0; i < 32; ++i) {
+        const float *hr = Hs + (4 * i + g) * (KP + 1);
+        float x[BP], y[B];
 #pragma unroll
-        for (int i = 0; i < GB::BR; ++i) x[i] = hr[c0 + i];
+        for (int ii = 0; ii < BP; ++ii) x[ii] = hr[cp + ii];
 #pragma unroll
-        for (int j = 0; j < GB::BC; ++j) y[j] = hr[d0 + j];
+        for (int jj = 0; jj < B; ++jj) y[jj] = hr[d0 + jj];
 #pragma unroll
-        for (int i = 0; i < GB::BR; ++i)
+        for (int ii = 0; ii < BP; ++ii)
 #pragma unroll
-          for (int j = 0; j < GB::BC; ++j) acc[i][j] = fmaf(x[i], y[j], acc[i][j]);
+          for (int jj = 0; jj < B; ++jj) acc[ii][jj] = fmaf(x[ii], y[jj], acc[ii][jj]);
       }
-      float *gp = e.gram_part + (int64_t)tp * KP * KP;
 #pragma unroll
-      for (int i = 0; i < GB::BR; ++i)
+      for (int ii = 0; ii < BP; ++ii) {
 #pragma unroll
-        for (int j = 0; j < GB::BC; ++j) gp[(c0 + i) * KP + d0 + j] = acc[i][j];
+        for (int jj = 0; jj < B; ++jj) acc[ii][jj] = gram_quad_sum(acc[ii][jj]);
+        if ((ii * 4) / BP == g) {  // the quad's lanes share the stores
+#pragma unroll
+          for (int jj = 0; jj < B; ++jj) gp[(cp + ii) * KP + d0 + jj] = acc[ii][jj];
+        }
+      }
     }
   }
-  // tile scalars: warp xor trees, then warps added in order
-  double v4[4] = {(double)tr, (double)kkt2, (double)sumA, (double)nonfin};
+  // tile scalars: warp xor trees in float-float form (FP64 adds are slow on
+  // this part), the warp sums exact in double, then warps added in order
+  float fh[3] = {tr, kkt2, sumA}, fl[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v4[i] += __shfl_xor_sync(0xffffffffu, v4[i], o);
+    for (int i = 0; i < 3; ++i) ff_xor_add(fh[i], fl[i], o);
+  double v4[4];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v4[i] = (double)fh[i] + (double)fl[i];
+  v4[3] = (double)__reduce_add_sync(0xffffffffu, (unsigned)nonfin);
   if constexpr (DT == 2) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
