@@ -87,6 +87,17 @@ __device__ __forceinline__ float part_sum(const float *P, int nsplit, int skG, i
   return v;
 }
 
+// num / (sqrt(v) + eps), the AdaGrad / RMSprop step (Sec. 2.2), in
+// straight-line code: PTX sqrt.approx.f32 (relative error at most 2^-23)
+// and div.full.f32 (at most 2 ulp over the full range).  With no
+// out-of-line special-case path the columns of a row overlap in flight.
+__device__ __forceinline__ float adaptive_step(float num, float v, float eps) {
+  float r, q;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+  asm("div.full.f32 %0, %1, %2;" : "=f"(q) : "f"(num), "f"(r + eps));
+  return q;
+}
+
 // Row order of every Gram partial (H_tile^T H_tile over a 128-row tile):
 // entry (c, d) is (s_0 + s_1) + (s_2 + s_3), s_g the FMA chain over the rows
 // r = 4 i + g, i = 0..31 in order, starting from zero.  gram_entry forms it

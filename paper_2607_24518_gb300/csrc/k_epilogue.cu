@@ -212,14 +212,14 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(EpiArgs a) {
         if (rms) {
           const float v = a.alpha * av[i] + (1.f - a.alpha) * (g * g);
           a.A[gi] = v;
-          const float m = a.mom * mv[i] + a.eta * g / (sqrtf(v) + a.eps);
+          const float m = a.mom * mv[i] + adaptive_step(a.eta * g, v, a.eps);
           a.M[gi] = m;
           x = h - m;
           sumA += v;
         } else {
           const float acc = av[i] + g * g;
           a.A[gi] = acc;
-          x = h - a.eta * g / (sqrtf(acc) + a.eps);
+          x = h - adaptive_step(a.eta * g, acc, a.eps);
           sumA += acc;
         }
         hn = (x > 0.f) ? x : 0.f;

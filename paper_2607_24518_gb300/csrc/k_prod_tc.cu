@@ -215,6 +215,20 @@ struct Own {
   static constexpr int HW = KH <= 16 ? KH : 16;  // columns whose state is held at once
 };
 
+// Rows [0, rows) of a tile held in Hs (row stride KP + 1) to dst (row
+// stride KP) by the 256 epilogue threads: each warp store covers whole
+// rows of dst, so the tile leaves in full 128-byte lines.
+template <int KP>
+__device__ __forceinline__ void store_rows(const float *Hs, float *dst, int rows, int et) {
+  constexpr int C4 = KP / 4;
+#pragma unroll 2
+  for (int i = et; i < rows * C4; i += 256) {
+    const int r = i / C4, c = (i - r * C4) * 4;
+    const float *sp = Hs + r * (KP + 1) + c;
+    *reinterpret_cast<float4 *>(dst + (int64_t)r * KP + c) = make_float4(sp[0], sp[1], sp[2], sp[3]);
+  }
+}
+
 // What a tile's epilogue needs before its S H rows exist: H_t of the tile in
 // Hs (both column halves), the thread's optimizer state (the first HW
 // owned columns) and its share of H_t Gram_t.  Ends with the tile's H_t in
@@ -409,14 +423,14 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
             } else if (rms) {
               const float v = e.alpha * av[s] + (1.f - e.alpha) * (g * g);
               av[s] = v;
-              const float m = e.mom * mv[s] + e.eta * g / (sqrtf(v) + e.eps);
+              const float m = e.mom * mv[s] + adaptive_step(e.eta * g, v, e.eps);
               mv[s] = m;
               x = h - m;
               sumA += v;
             } else {
               const float acc = av[s] + g * g;
               av[s] = acc;
-              x = h - e.eta * g / (sqrtf(acc) + e.eps);
+              x = h - adaptive_step(e.eta * g, acc, e.eps);
               sumA += acc;
             }
             hn[j] = (x > 0.f) ? x : 0.f;
@@ -444,7 +458,9 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
           for (int j = 0; j < 8; ++j)
             if (cb + cc + j < e.k) e.gcaller[(r0 + row) * e.k + cb + cc + j] = p[cc + j];
         }
-        if (e.update) {
+        // H_{t+1} leaves through Hs below, and so does the optimizer
+        // state when all of the thread's columns are in registers at once
+        if (e.update && KH != HW) {
           float4 *a4 = reinterpret_cast<float4 *>(e.A + base + cc);
           a4[0] = make_float4(av[s0], av[s0 + 1], av[s0 + 2], av[s0 + 3]);
           a4[1] = make_float4(av[s0 + 4], av[s0 + 5], av[s0 + 6], av[s0 + 7]);
@@ -453,9 +469,6 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
             v4[0] = make_float4(mv[s0], mv[s0 + 1], mv[s0 + 2], mv[s0 + 3]);
             v4[1] = make_float4(mv[s0 + 4], mv[s0 + 5], mv[s0 + 6], mv[s0 + 7]);
           }
-          float4 *h4 = reinterpret_cast<float4 *>(e.Hn + base + cc);
-          h4[0] = make_float4(hn[0], hn[1], hn[2], hn[3]);
-          h4[1] = make_float4(hn[4], hn[5], hn[6], hn[7]);
         }
       }
       if (e.update && works) {
@@ -489,6 +502,7 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
     }
   }
   epi_bar();  // Hs holds the tile of H_{t+1}
+  if (e.update) store_rows<KP>(Hs, e.Hn + r0 * KP, rows, et);
   if (e.update && e.gram_part) {
     // Each lane quad sums one B x B block of the 8 x 8 block grid in the
     // Gram row order (gram_quad_sum); a warp holds 2 x 4 blocks so that
@@ -574,6 +588,27 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
         }
       }
       if (et == 0) bt_deq(e.Btn, KP, e.ldb)[tp] = d;
+    }
+  }
+  if constexpr (KH == HW) {
+    if (e.update) {
+      // the new optimizer state goes out through Hs as well
+      epi_bar();  // every read of H_{t+1} from Hs is done
+      if (works) {
+#pragma unroll
+        for (int j = 0; j < KH; ++j) hrow[cb + j] = av[j];
+      }
+      epi_bar();
+      store_rows<KP>(Hs, e.A + r0 * KP, rows, et);
+      if (rms) {
+        epi_bar();
+        if (works) {
+#pragma unroll
+          for (int j = 0; j < KH; ++j) hrow[cb + j] = mv[j];
+        }
+        epi_bar();
+        store_rows<KP>(Hs, e.M + r0 * KP, rows, et);
+      }
     }
   }
   epi_bar();
