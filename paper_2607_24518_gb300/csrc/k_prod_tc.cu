@@ -232,10 +232,36 @@ __device__ __forceinline__ void store_rows(const float *Hs, float *dst, int rows
 // What a tile's epilogue needs before its S H rows exist: H_t of the tile in
 // Hs (both column halves), the thread's optimizer state (the first HW
 // owned columns) and its share of H_t Gram_t.  Ends with the tile's H_t in
-// Hs for every thread.
+// Hs for every thread.  The rows are read in whole 128-byte lines by the
+// 256 threads together and reach each row's threads through Hs: a load of
+// one row per thread would cost one memory request per 16 bytes, and while
+// the stream saturates HBM those requests slow the CTA's own TMA copies.
+template <int KP>
+__device__ __forceinline__ void stage_rows(float *Hs, const float4 (&v)[KP / 8], int et) {
+  constexpr int C4 = KP / 4;
+#pragma unroll
+  for (int i = 0; i < KP / 8; ++i) {
+    const int idx = et + 256 * i, r = idx / C4, c = (idx - r * C4) * 4;
+    float *d = Hs + r * (KP + 1) + c;
+    d[0] = v[i].x;
+    d[1] = v[i].y;
+    d[2] = v[i].z;
+    d[3] = v[i].w;
+  }
+}
+template <int KP>
+__device__ __forceinline__ void load_rows(float4 (&v)[KP / 8], const float *src, int rows, int et) {
+  constexpr int C4 = KP / 4;
+#pragma unroll
+  for (int i = 0; i < KP / 8; ++i) {
+    const int idx = et + 256 * i;
+    v[i] = (idx < rows * C4) ? __ldcg(reinterpret_cast<const float4 *>(src) + idx)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
 template <int DT, int KP>
 __device__ __forceinline__ void tile_prep(const EpiArgs &e, int tp, float *Hs, const float *Gs,
-                                          int row, int half, float (&hg)[Own<KP>::KH],
+                                          int row, int half, int et, float (&hg)[Own<KP>::KH],
                                           float (&av)[Own<KP>::HW], float (&mv)[Own<KP>::HW]) {
   constexpr int KH = Own<KP>::KH;
   constexpr int HW = Own<KP>::HW;
@@ -243,33 +269,63 @@ __device__ __forceinline__ void tile_prep(const EpiArgs &e, int tp, float *Hs, c
   const int cb = (KP >= 16) ? half * KH : 0;
   const int64_t r0 = (int64_t)tp * 128;
   const int rows = (int)((e.n - r0) < 128 ? (e.n - r0) : 128);
-  const bool vrow = works && row < rows;
   const bool rms = (e.method == SYMNMF_RMSPROP);
-  const int64_t base = (r0 + row) * KP + cb;
   float *hrow = Hs + row * (KP + 1);
+  // the thread's state columns of A (and M) through Hs, then H_t
+  auto take = [&](float (&dst)[HW]) {
 #pragma unroll
-  for (int c4 = 0; c4 < HW / 4; ++c4) {
-    float4 u = make_float4(0.f, 0.f, 0.f, 0.f), w = u;
-    if (vrow && e.update) {
-      u = reinterpret_cast<const float4 *>(e.A + base)[c4];
-      if (rms) w = reinterpret_cast<const float4 *>(e.M + base)[c4];
-    }
-    av[4 * c4 + 0] = u.x; av[4 * c4 + 1] = u.y; av[4 * c4 + 2] = u.z; av[4 * c4 + 3] = u.w;
-    mv[4 * c4 + 0] = w.x; mv[4 * c4 + 1] = w.y; mv[4 * c4 + 2] = w.z; mv[4 * c4 + 3] = w.w;
-  }
-  if (works) {
-    const bool in = row < rows;
-    const float4 *src = reinterpret_cast<const float4 *>(e.H + base);
+    for (int j = 0; j < HW; ++j) dst[j] = works ? hrow[cb + j] : 0.f;
+  };
+  float4 v[KP / 8];
 #pragma unroll
-    for (int c4 = 0; c4 < KH / 4; ++c4) {
-      const float4 v = in ? src[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
-      hrow[cb + 4 * c4 + 0] = v.x;
-      hrow[cb + 4 * c4 + 1] = v.y;
-      hrow[cb + 4 * c4 + 2] = v.z;
-      hrow[cb + 4 * c4 + 3] = v.w;
+  for (int j = 0; j < HW; ++j) av[j] = mv[j] = 0.f;
+  if constexpr (DT == 0) {
+    // FP32 storage: the folders read the staged S rows from shared memory
+    // to split them, and extra shared-memory traffic here slows that more
+    // than the row loads below slow the stream
+    const bool vrow = works && row < rows;
+    const int64_t base = (r0 + row) * KP + cb;
+#pragma unroll
+    for (int c4 = 0; c4 < HW / 4; ++c4) {
+      float4 u = make_float4(0.f, 0.f, 0.f, 0.f), w = u;
+      if (vrow && e.update) {
+        u = reinterpret_cast<const float4 *>(e.A + base)[c4];
+        if (rms) w = reinterpret_cast<const float4 *>(e.M + base)[c4];
+      }
+      av[4 * c4 + 0] = u.x; av[4 * c4 + 1] = u.y; av[4 * c4 + 2] = u.z; av[4 * c4 + 3] = u.w;
+      mv[4 * c4 + 0] = w.x; mv[4 * c4 + 1] = w.y; mv[4 * c4 + 2] = w.z; mv[4 * c4 + 3] = w.w;
+    }
+    if (works) {
+      const float4 *src = reinterpret_cast<const float4 *>(e.H + base);
+#pragma unroll
+      for (int c4 = 0; c4 < KH / 4; ++c4) {
+        const float4 u = (row < rows) ? src[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        hrow[cb + 4 * c4 + 0] = u.x;
+        hrow[cb + 4 * c4 + 1] = u.y;
+        hrow[cb + 4 * c4 + 2] = u.z;
+        hrow[cb + 4 * c4 + 3] = u.w;
+      }
+    }
+    epi_bar();  // both halves of each H_t row are in Hs
+  } else {
+  if (e.update) {
+    load_rows<KP>(v, e.A + r0 * KP, rows, et);
+    stage_rows<KP>(Hs, v, et);
+    epi_bar();
+    take(av);
+    epi_bar();
+    if (rms) {
+      load_rows<KP>(v, e.M + r0 * KP, rows, et);
+      stage_rows<KP>(Hs, v, et);
+      epi_bar();
+      take(mv);
+      epi_bar();
     }
   }
+  load_rows<KP>(v, e.H + r0 * KP, rows, et);
+  stage_rows<KP>(Hs, v, et);
   epi_bar();  // both halves of each H_t row are in Hs
+  }
   // (H_t Gram_t) for the owned columns, right to left (Sec. 2.1)
 #pragma unroll
   for (int j = 0; j < KH; ++j) hg[j] = 0.f;
@@ -644,15 +700,29 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
   constexpr int KH = Own<KP>::KH;
   constexpr int HW = Own<KP>::HW;
   float hg[KH], av[HW], mv[HW];
-  // The tile holding this CTA's last unit is, in practice, finished here
-  // (the next CTA streams the rest of it first): prepare it while idle.
+  // The tile segments in streaming order; the epilogue prepares the next
+  // one while it is idle, whether or not this CTA will finish it (the
+  // last CTA of a tile to arrive does), so a finish starts with its tile's
+  // rows and state already loaded.
+  auto tile_from = [&](int si, int64_t L) -> int {  // tile of the segment starting at (si, L)
+    if (si == 0 && L >= sg.hi[0]) {
+      si = 1;
+      L = sg.lo[1];
+    }
+    return (L < sg.hi[si]) ? (int)(L / a.n_cols) : -1;
+  };
+  // (FP8 storage, where the stream is shortest; otherwise only the tile of
+  // the CTA's last unit, which this CTA finishes in practice, is prepared
+  // ahead: the registers held across the wait cost the others more)
+  constexpr bool kPrepNext = (DT == 2);
   int prepared = -1, final_tp = -1;
+  if (sg.hi[0] > sg.lo[0])
+    final_tp = (int)(((sg.hi[1] > sg.lo[1] ? sg.hi[1] : sg.hi[0]) - 1) / a.n_cols);
   if constexpr (KH == HW) {
-    const int last_si = (sg.hi[1] > sg.lo[1]) ? 1 : 0;
-    if (sg.hi[last_si] > sg.lo[last_si]) {
-      final_tp = (int)((sg.hi[last_si] - 1) / a.n_cols);
-      prepared = final_tp;
-      tile_prep<DT, KP>(e, prepared, Hs, Gs, row, half, hg, av, mv);
+    const int t0 = kPrepNext ? tile_from(0, sg.lo[0]) : final_tp;
+    if (t0 >= 0) {
+      prepared = t0;
+      tile_prep<DT, KP>(e, prepared, Hs, Gs, row, half, et, hg, av, mv);
     }
   }
   int pb = 0;
@@ -725,15 +795,18 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     if (epi) {
       if (tp != prepared) {
         epi_bar();  // no thread still reads Hs of an earlier tile
-        tile_prep<DT, KP>(e, tp, Hs, Gs, row, half, hg, av, mv);
+        tile_prep<DT, KP>(e, tp, Hs, Gs, row, half, et, hg, av, mv);
       }
       prepared = -1;
       tile_finish<DT, KP>(e, tp, p, hg, av, mv, Hs, scratch, et, row, half);
-      // a tile finished mid-stream: prepare the final one again while the
-      // stream goes on (tile_finish ends on a barrier, Hs is free)
-      if (final_tp >= 0 && tp != final_tp) {
-        prepared = final_tp;
-        tile_prep<DT, KP>(e, prepared, Hs, Gs, row, half, hg, av, mv);
+    }
+    if constexpr (KH == HW) {
+      // prepare the next segment's tile while the stream goes on
+      const int nx = kPrepNext ? tile_from(si, L) : (epi && tp != final_tp) ? final_tp : -1;
+      if (nx >= 0 && nx != prepared) {
+        epi_bar();  // no thread still reads Hs
+        prepared = nx;
+        tile_prep<DT, KP>(e, prepared, Hs, Gs, row, half, et, hg, av, mv);
       }
     }
   }
