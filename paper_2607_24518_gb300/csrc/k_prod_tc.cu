@@ -117,6 +117,10 @@ struct Cfg {
   static constexpr uint32_t BUDGET = 232448u - 1024u - BAR_BYTES - EPI_BYTES;
   static constexpr int STAGES = (BUDGET / STAGE) < 8u ? (int)(BUDGET / STAGE) : 8;
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + BAR_BYTES + EPI_BYTES;
+  // partial slots of a fused launch column-major (fslot) rather than
+  // row-major: fewer memory requests, but four times the folder's store
+  // and load instructions, which the FP32 folders (also splitting S) pay
+  static constexpr bool COLSLOT = !F32;
   // MMA issuing threads (warps 1 and 14).  One thread issues a tcgen05.mma
   // about every 60 SM cycles at best, so a skinny-N stream of S is bounded
   // by the issuer unless the chains are split between two of them.
@@ -192,6 +196,15 @@ __device__ __forceinline__ Segs cta_segments(const TcArgs &a, int b) {
 // column position visited for unit L
 __device__ __forceinline__ int unit_col(const TcArgs &a, int64_t L) {
   return (int)(L % a.n_cols);
+}
+// Element (r, c) of partial slot s of a fused step with BF16 or FP8
+// storage.  Its slots are read by the same kernel only and are column-
+// major, so the 32 rows of a warp's load or store of one column are one
+// 128-byte line.  (Slots of a launch without the fused epilogue, and of
+// FP32 storage, keep the row-major layout of part_sum.)
+template <int KP>
+__device__ __forceinline__ int64_t fslot(int64_t s, int c, int r) {
+  return (s * KP + c) * 128 + r;
 }
 
 // ------------------------------------------------------------------ epilogue
@@ -769,26 +782,42 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
       __threadfence();
       if (KP >= 16 || half == 0) {
         // GB slots' loads in flight at once, then added in CTA order
-        constexpr int GB = (KH <= 16) ? 4 : 2;
-        for (int64_t bb = b0; bb <= b1; bb += GB) {
-          float4 v[GB][KH / 4];
+        if constexpr (C::COLSLOT) {
+          constexpr int GB = (KH <= 16) ? 2 : 1;
+          for (int64_t bb = b0; bb <= b1; bb += GB) {
+            float v[GB][KH];
 #pragma unroll
-          for (int g = 0; g < GB; ++g) {
-            const float4 *src =
-                reinterpret_cast<const float4 *>(a.out + ((bb + g + tp) * 128 + row) * KP + cb);
+            for (int g = 0; g < GB; ++g)
 #pragma unroll
-            for (int c4 = 0; c4 < KH / 4; ++c4)
-              v[g][c4] = (bb + g <= b1) ? __ldcg(src + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+              for (int j = 0; j < KH; ++j)
+                v[g][j] = (bb + g <= b1) ? __ldcg(a.out + fslot<KP>(bb + g + tp, cb + j, row)) : 0.f;
+#pragma unroll
+            for (int g = 0; g < GB; ++g)
+#pragma unroll
+              for (int j = 0; j < KH; ++j) p[j] += v[g][j];
           }
+        } else {
+          constexpr int GB = (KH <= 16) ? 4 : 2;
+          for (int64_t bb = b0; bb <= b1; bb += GB) {
+            float4 v[GB][KH / 4];
 #pragma unroll
-          for (int g = 0; g < GB; ++g)
+            for (int g = 0; g < GB; ++g) {
+              const float4 *src =
+                  reinterpret_cast<const float4 *>(a.out + ((bb + g + tp) * 128 + row) * KP + cb);
 #pragma unroll
-            for (int c4 = 0; c4 < KH / 4; ++c4) {
-              p[4 * c4 + 0] += v[g][c4].x;
-              p[4 * c4 + 1] += v[g][c4].y;
-              p[4 * c4 + 2] += v[g][c4].z;
-              p[4 * c4 + 3] += v[g][c4].w;
+              for (int c4 = 0; c4 < KH / 4; ++c4)
+                v[g][c4] = (bb + g <= b1) ? __ldcg(src + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+#pragma unroll
+            for (int g = 0; g < GB; ++g)
+#pragma unroll
+              for (int c4 = 0; c4 < KH / 4; ++c4) {
+                p[4 * c4 + 0] += v[g][c4].x;
+                p[4 * c4 + 1] += v[g][c4].y;
+                p[4 * c4 + 2] += v[g][c4].z;
+                p[4 * c4 + 3] += v[g][c4].w;
+              }
+          }
         }
       }
     }
@@ -947,15 +976,23 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
             tmem_wait_ld_all(x);
             for (int64_t bb = b0; bb <= b1; ++bb) {
               if (bb == b) continue;
-              const float4 *src =
-                  reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP + cc);
+              if constexpr (C::COLSLOT) {
+                float v[16];
 #pragma unroll
-              for (int c4 = 0; c4 < 4; ++c4) {
-                const float4 v = __ldcg(src + c4);
-                x[4 * c4 + 0] = __float_as_uint(__uint_as_float(x[4 * c4 + 0]) + v.x);
-                x[4 * c4 + 1] = __float_as_uint(__uint_as_float(x[4 * c4 + 1]) + v.y);
-                x[4 * c4 + 2] = __float_as_uint(__uint_as_float(x[4 * c4 + 2]) + v.z);
-                x[4 * c4 + 3] = __float_as_uint(__uint_as_float(x[4 * c4 + 3]) + v.w);
+                for (int j = 0; j < 16; ++j) v[j] = __ldcg(a.out + fslot<KP>(bb + tp, cc + j, row));
+#pragma unroll
+                for (int j = 0; j < 16; ++j) x[j] = __float_as_uint(__uint_as_float(x[j]) + v[j]);
+              } else {
+                const float4 *src =
+                    reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP + cc);
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                  const float4 v = __ldcg(src + c4);
+                  x[4 * c4 + 0] = __float_as_uint(__uint_as_float(x[4 * c4 + 0]) + v.x);
+                  x[4 * c4 + 1] = __float_as_uint(__uint_as_float(x[4 * c4 + 1]) + v.y);
+                  x[4 * c4 + 2] = __float_as_uint(__uint_as_float(x[4 * c4 + 2]) + v.z);
+                  x[4 * c4 + 3] = __float_as_uint(__uint_as_float(x[4 * c4 + 3]) + v.w);
+                }
               }
             }
             tmem_st16(tpa + cc, x);
@@ -964,15 +1001,23 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
         } else {
           for (int64_t bb = b0; bb <= b1; ++bb) {
             if (bb == b) continue;
-            const float4 *src =
-                reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP);
+            if constexpr (C::COLSLOT) {
+              float v[KP];
 #pragma unroll
-            for (int c4 = 0; c4 < KP / 4; ++c4) {
-              const float4 v = __ldcg(src + c4);
-              p[4 * c4 + 0] += v.x;
-              p[4 * c4 + 1] += v.y;
-              p[4 * c4 + 2] += v.z;
-              p[4 * c4 + 3] += v.w;
+              for (int c = 0; c < KP; ++c) v[c] = __ldcg(a.out + fslot<KP>(bb + tp, c, row));
+#pragma unroll
+              for (int c = 0; c < KP; ++c) p[c] += v[c];
+            } else {
+              const float4 *src =
+                  reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP);
+#pragma unroll
+              for (int c4 = 0; c4 < KP / 4; ++c4) {
+                const float4 v = __ldcg(src + c4);
+                p[4 * c4 + 0] += v.x;
+                p[4 * c4 + 1] += v.y;
+                p[4 * c4 + 2] += v.z;
+                p[4 * c4 + 3] += v.w;
+              }
             }
           }
         }
@@ -989,12 +1034,20 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
           tmem_ld8_nw(tpa + cc, x, 0);
           tmem_ld8_nw(tpa + cc + 8, x, 8);
           tmem_wait_ld_all(x);
+          if (a.fused && C::COLSLOT) {
 #pragma unroll
-          for (int c4 = 0; c4 < 4; ++c4)
-            reinterpret_cast<float4 *>(dst + cc)[c4] =
-                make_float4(__uint_as_float(x[4 * c4]), __uint_as_float(x[4 * c4 + 1]),
-                            __uint_as_float(x[4 * c4 + 2]), __uint_as_float(x[4 * c4 + 3]));
+            for (int j = 0; j < 16; ++j) a.out[fslot<KP>(b + tp, cc + j, row)] = __uint_as_float(x[j]);
+          } else {
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4)
+              reinterpret_cast<float4 *>(dst + cc)[c4] =
+                  make_float4(__uint_as_float(x[4 * c4]), __uint_as_float(x[4 * c4 + 1]),
+                              __uint_as_float(x[4 * c4 + 2]), __uint_as_float(x[4 * c4 + 3]));
+          }
         }
+      } else if (a.fused && C::COLSLOT) {
+#pragma unroll
+        for (int c = 0; c < KP; ++c) a.out[fslot<KP>(b + tp, c, row)] = p[c];
       } else {
 #pragma unroll
         for (int cc = 0; cc < KP; cc += 4)
