@@ -117,10 +117,6 @@ struct Cfg {
   static constexpr uint32_t BUDGET = 232448u - 1024u - BAR_BYTES - EPI_BYTES;
   static constexpr int STAGES = (BUDGET / STAGE) < 8u ? (int)(BUDGET / STAGE) : 8;
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + BAR_BYTES + EPI_BYTES;
-  // partial slots of a fused launch column-major (fslot) rather than
-  // row-major: fewer memory requests, but four times the folder's store
-  // and load instructions, which the FP32 folders (also splitting S) pay
-  static constexpr bool COLSLOT = !F32;
   // MMA issuing threads (warps 1 and 14).  One thread issues a tcgen05.mma
   // about every 60 SM cycles at best, so a skinny-N stream of S is bounded
   // by the issuer unless the chains are split between two of them.
@@ -197,11 +193,11 @@ __device__ __forceinline__ Segs cta_segments(const TcArgs &a, int b) {
 __device__ __forceinline__ int unit_col(const TcArgs &a, int64_t L) {
   return (int)(L % a.n_cols);
 }
-// Element (r, c) of partial slot s of a fused step with BF16 or FP8
-// storage.  Its slots are read by the same kernel only and are column-
+// Element (r, c) of partial slot s of a fused step.  Its slots are written
+// and read by the epilogue warps of the same kernel only and are column-
 // major, so the 32 rows of a warp's load or store of one column are one
-// 128-byte line.  (Slots of a launch without the fused epilogue, and of
-// FP32 storage, keep the row-major layout of part_sum.)
+// 128-byte line.  (Slots of a launch without the fused epilogue keep the
+// row-major layout of part_sum.)
 template <int KP>
 __device__ __forceinline__ int64_t fslot(int64_t s, int c, int r) {
   return (s * KP + c) * 128 + r;
@@ -685,11 +681,11 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
 
 // Shared-memory handshake between the folder and epilogue warps: the folders
 // hand over one finished P row block per tile segment through the TMEM P
-// buffer pb (double-buffered); pflag[pb] says whether this CTA finishes the
-// tile (otherwise another CTA does, from the partial slots).
+// buffer pb (double-buffered); sflag carries the epilogue's decisions
+// between its threads.
 struct Hand {
   uint64_t *pfull, *pempty;
-  volatile int *pflag;
+  volatile int *sflag;
 };
 
 // Epilogue warps 2-5: one thread per tile row.
@@ -738,6 +734,47 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
       tile_prep<DT, KP>(e, prepared, Hs, Gs, row, half, et, hg, av, mv);
     }
   }
+  // Parts of tile tp left by other CTAs (fused slots, column-major): the
+  // thread's KH columns from cb, for its row.  add_parts adds the parts of
+  // CTAs b0..b1 but `self` to p in CTA order (p holds this CTA's part,
+  // first in the order); sum_parts forms the CTA-order sum of all of them
+  // with p standing for this CTA's part at its place.
+  auto load_part = [&](float (&v)[KH], int64_t bb, int tp, int cb) {
+#pragma unroll
+    for (int j = 0; j < KH; ++j) v[j] = __ldcg(a.out + fslot<KP>(bb + tp, cb + j, row));
+  };
+  auto add_parts = [&](float (&pp)[KH], int64_t b0, int64_t b1, int64_t self, int tp, int cb) {
+    for (int64_t bb = b0; bb <= b1; ++bb) {
+      if (bb == self) continue;
+      float v[KH];
+      load_part(v, bb, tp, cb);
+#pragma unroll
+      for (int j = 0; j < KH; ++j) pp[j] += v[j];
+    }
+  };
+  auto sum_parts = [&](float (&pp)[KH], int64_t b0, int64_t b1, int64_t self, int tp, int cb) {
+    float acc[KH];
+    if (b0 == self) {
+#pragma unroll
+      for (int j = 0; j < KH; ++j) acc[j] = pp[j];
+    } else {
+      load_part(acc, b0, tp, cb);
+    }
+    for (int64_t bb = b0 + 1; bb <= b1; ++bb) {
+      if (bb == self) {
+#pragma unroll
+        for (int j = 0; j < KH; ++j) acc[j] += pp[j];
+      } else {
+        float v[KH];
+        load_part(v, bb, tp, cb);
+#pragma unroll
+        for (int j = 0; j < KH; ++j) acc[j] += v[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < KH; ++j) pp[j] = acc[j];
+  };
+  const int b = blockIdx.x;
   int pb = 0;
   uint32_t pph = 0u;  // bit b: parity of P buffer b
   for (int si = 0; si < 2; ++si)
@@ -753,9 +790,9 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
       return;
     }
     fence_after();
-    const int epi = hd.pflag[pb];  // 0: none, 1: P in TMEM, 2: add the partial slots
+    // this CTA's part of tile tp, the thread's KH columns
     float p[KH];
-    if (epi == 1) {
+    {
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + C::PB0 +
                           (uint32_t)(pb * KP + ((KP >= 16) ? half * KH : 0));
 #pragma unroll
@@ -771,54 +808,55 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     if (lane == 0) mbar_arrive(&hd.pempty[pb]);
     pph ^= 1u << pb;
     pb ^= 1;
-    if (epi == 2) {
-      // shared row position: its partials in slots cta + tp, CTA order
-      const int64_t WR = (int64_t)a.R * a.n_cols;
-      const int64_t b0 = sk_owner(a, (int64_t)tp * a.n_cols, WR);
-      const int64_t b1 = sk_owner(a, (int64_t)tp * a.n_cols + a.n_cols - 1, WR);
-      const int cb = (KP >= 16) ? half * KH : 0;
-#pragma unroll
-      for (int j = 0; j < KH; ++j) p[j] = 0.f;
-      __threadfence();
-      if (KP >= 16 || half == 0) {
-        // GB slots' loads in flight at once, then added in CTA order
-        if constexpr (C::COLSLOT) {
-          constexpr int GB = (KH <= 16) ? 2 : 1;
-          for (int64_t bb = b0; bb <= b1; bb += GB) {
-            float v[GB][KH];
-#pragma unroll
-            for (int g = 0; g < GB; ++g)
-#pragma unroll
-              for (int j = 0; j < KH; ++j)
-                v[g][j] = (bb + g <= b1) ? __ldcg(a.out + fslot<KP>(bb + g + tp, cb + j, row)) : 0.f;
-#pragma unroll
-            for (int g = 0; g < GB; ++g)
-#pragma unroll
-              for (int j = 0; j < KH; ++j) p[j] += v[g][j];
-          }
-        } else {
-          constexpr int GB = (KH <= 16) ? 4 : 2;
-          for (int64_t bb = b0; bb <= b1; bb += GB) {
-            float4 v[GB][KH / 4];
-#pragma unroll
-            for (int g = 0; g < GB; ++g) {
-              const float4 *src =
-                  reinterpret_cast<const float4 *>(a.out + ((bb + g + tp) * 128 + row) * KP + cb);
-#pragma unroll
-              for (int c4 = 0; c4 < KH / 4; ++c4)
-                v[g][c4] = (bb + g <= b1) ? __ldcg(src + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int g = 0; g < GB; ++g)
-#pragma unroll
-              for (int c4 = 0; c4 < KH / 4; ++c4) {
-                p[4 * c4 + 0] += v[g][c4].x;
-                p[4 * c4 + 1] += v[g][c4].y;
-                p[4 * c4 + 2] += v[g][c4].z;
-                p[4 * c4 + 3] += v[g][c4].w;
-              }
-          }
+    // A row position held by several CTAs is finished by the last of them
+    // to arrive (per-tile counter), adding the parts in CTA order.  The
+    // first or second holder (own part first: own + s_b0 equals s_b0 + own
+    // exactly) finishes without leaving its part when all the others have
+    // already arrived; any other arrival stores its part in slot (cta +
+    // tile), fenced, and counts itself in.
+    int epi = 1;
+    const int cb = (KP >= 16) ? half * KH : 0;
+    const bool owns = (KP >= 16) || half == 0;
+    const int64_t WR = (int64_t)a.R * a.n_cols;
+    const int64_t b0 = sk_owner(a, (int64_t)tp * a.n_cols, WR);
+    const int64_t b1 = sk_owner(a, (int64_t)tp * a.n_cols + a.n_cols - 1, WR);
+    if (b0 < b1) {
+      epi = 0;
+      if (b - b0 <= 1) {
+        if (et == 0) {
+          const int arrived = *reinterpret_cast<volatile int *>(&a.tile_cnt[tp]);
+          const int last = (arrived == (int)(b1 - b0));
+          if (last) a.tile_cnt[tp] = 0;
+          *hd.sflag = last;
         }
+        epi_bar();
+        if (*hd.sflag) epi = 1;
+        epi_bar();  // sflag is read before it is reused
+      }
+      if (epi) {
+        __threadfence();
+        if (owns) add_parts(p, b0, b1, b, tp, cb);  // own part first
+      } else {
+        if (owns) {
+#pragma unroll
+          for (int j = 0; j < KH; ++j) a.out[fslot<KP>(b + tp, cb + j, row)] = p[j];
+        }
+        __threadfence();
+        epi_bar();
+        if (et == 0) {
+          const int old = atomicAdd(&a.tile_cnt[tp], 1);
+          const int last = (old == (int)(b1 - b0));
+          if (last) a.tile_cnt[tp] = 0;
+          *hd.sflag = last;
+        }
+        epi_bar();
+        if (*hd.sflag) {
+          epi = 1;
+          __threadfence();
+          // every part, this CTA's own at its place in CTA order
+          if (owns) sum_parts(p, b0, b1, b, tp, cb);
+        }
+        epi_bar();  // sflag is read before it is reused
       }
     }
     if (epi) {
@@ -848,7 +886,7 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
 template <int DT, int KP>
 __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, uint64_t *full,
                             uint64_t *empty, uint64_t *afull, uint64_t *aempty, uint64_t *tfull,
-                            uint64_t *tempty, const Hand &hd, int *sflag,
+                            uint64_t *tempty, const Hand &hd,
                             volatile int *abort_flag, const Segs &sg, int b, float *sring) {
   using C = Cfg<DT, KP>;
   constexpr int STAGES = C::STAGES;
@@ -874,158 +912,47 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     }
     ok = false;
   };
-  // hand the finished segment of tile tp over (or leave a partial)
-  // hand a tile segment over to the epilogue warps: epi 0 (another CTA
-  // finishes the tile), 1 (P in TMEM buffer pb, stored from p), 2 (the
-  // epilogue warps add the partial slots)
-  auto handoff = [&](int epi) {
+  // A fused step hands every finished tile segment's P over to the
+  // epilogue warps through TMEM P buffer pb; they finish the tile or leave
+  // the partial for another CTA, so no store, fence or counter waits in
+  // the folders' path.  Without the fused epilogue the folders store the
+  // segment's partial themselves (row-major slot b + tp).
+  auto handoff = [&]() {
     if (!warp_wait_idle(&hd.pempty[pb], ((pph >> pb) & 1u) ^ 1u, abort_flag)) {
       fail(7);
       return;
     }
     fence_after();
-    if (epi == 1) {
-      const uint32_t tb = tmem_base + lane_off + C::PB0 + (uint32_t)(pb * KP);
-      if constexpr (C::PTMEM) {
+    const uint32_t tb = tmem_base + lane_off + C::PB0 + (uint32_t)(pb * KP);
+    if constexpr (C::PTMEM) {
 #pragma unroll
-        for (int cc = 0; cc < KP; cc += 16) {
-          uint32_t x[16];
-          tmem_ld8_nw(tpa + cc, x, 0);
-          tmem_ld8_nw(tpa + cc + 8, x, 8);
-          tmem_wait_ld_all(x);
-          tmem_st16(tb + cc, x);
-        }
-      } else {
-#pragma unroll
-        for (int cc = 0; cc < KP; cc += 8) {
-          float v[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = p[cc + j];
-          tmem_st8(tb + cc, v);
-        }
+      for (int cc = 0; cc < KP; cc += 16) {
+        uint32_t x[16];
+        tmem_ld8_nw(tpa + cc, x, 0);
+        tmem_ld8_nw(tpa + cc + 8, x, 8);
+        tmem_wait_ld_all(x);
+        tmem_st16(tb + cc, x);
       }
-      tmem_wait_st();
+    } else {
+#pragma unroll
+      for (int cc = 0; cc < KP; cc += 8) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = p[cc + j];
+        tmem_st8(tb + cc, v);
+      }
     }
-    if (ft == 0) hd.pflag[pb] = epi;
+    tmem_wait_st();
     fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&hd.pfull[pb]);
     pph ^= 1u << pb;
     pb ^= 1;
   };
-  // A partial left for another CTA is published (fence, arrival count)
-  // some folds later, once its stores have drained: a fence right behind
-  // them, with HBM saturated, stalls the folders long enough to drain the
-  // ring.  Whoever arrives last still finishes the tile.
-  constexpr int kDefer = 8;
-  int pend_tp = -1, pend_cd = 0;
-  int64_t pend_b0 = 0, pend_b1 = 0;
-  auto publish_pending = [&]() {
-    const int tp = pend_tp;
-    pend_tp = -1;
-    __threadfence();
-    fold_bar();
-    if (ft == 0) {
-      const int old = atomicAdd(&a.tile_cnt[tp], 1);
-      const int last = (old == (int)(pend_b1 - pend_b0));
-      if (last) a.tile_cnt[tp] = 0;
-      *reinterpret_cast<volatile int *>(sflag) = last;
-    }
-    fold_bar();
-    const int epi = *reinterpret_cast<volatile int *>(sflag) ? 2 : 0;
-    if (epi) __threadfence();
-    fold_bar();  // sflag is read before it is reused
-    handoff(epi);
-  };
-  // hand the finished segment of tile tp over (or leave a partial)
   auto finish_segment = [&](int tp) {
-    if (pend_tp >= 0) publish_pending();
-    int64_t b0 = b, b1 = b;
-    int epi = 0;
     if (a.fused) {
-      if (tp < a.R) {  // shared row position: the CTAs holding its units
-        const int64_t WR = (int64_t)a.R * a.n_cols;
-        b0 = sk_owner(a, (int64_t)tp * a.n_cols, WR);
-        b1 = sk_owner(a, (int64_t)tp * a.n_cols + a.n_cols - 1, WR);
-      }
-      epi = (b0 == b1);
-    }
-    // when every other CTA sharing the tile has already left its partial,
-    // the tile is finished here without storing this CTA's own.  The sum
-    // stays in CTA order: for the first sharer its own partial comes first;
-    // for the second, own + s_b0 equals s_b0 + own exactly (floating-point
-    // addition commutes) and the later partials follow in order.  A CTA
-    // further down the order leaves its partial like any other.
-    if (!epi && a.fused && b - b0 <= 1) {
-      if (ft == 0) {
-        const int arrived = *reinterpret_cast<volatile int *>(&a.tile_cnt[tp]);
-        const int last = (arrived == (int)(b1 - b0));
-        if (last) a.tile_cnt[tp] = 0;
-        *reinterpret_cast<volatile int *>(sflag) = last;
-      }
-      fold_bar();
-      if (*reinterpret_cast<volatile int *>(sflag)) {
-        __threadfence();
-        if constexpr (C::PTMEM) {
-          // PA += the other partials, 16 columns at a time
-#pragma unroll 1
-          for (int cc = 0; cc < KP; cc += 16) {
-            uint32_t x[16];
-            tmem_ld8_nw(tpa + cc, x, 0);
-            tmem_ld8_nw(tpa + cc + 8, x, 8);
-            tmem_wait_ld_all(x);
-            for (int64_t bb = b0; bb <= b1; ++bb) {
-              if (bb == b) continue;
-              if constexpr (C::COLSLOT) {
-                float v[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = __ldcg(a.out + fslot<KP>(bb + tp, cc + j, row));
-#pragma unroll
-                for (int j = 0; j < 16; ++j) x[j] = __float_as_uint(__uint_as_float(x[j]) + v[j]);
-              } else {
-                const float4 *src =
-                    reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP + cc);
-#pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                  const float4 v = __ldcg(src + c4);
-                  x[4 * c4 + 0] = __float_as_uint(__uint_as_float(x[4 * c4 + 0]) + v.x);
-                  x[4 * c4 + 1] = __float_as_uint(__uint_as_float(x[4 * c4 + 1]) + v.y);
-                  x[4 * c4 + 2] = __float_as_uint(__uint_as_float(x[4 * c4 + 2]) + v.z);
-                  x[4 * c4 + 3] = __float_as_uint(__uint_as_float(x[4 * c4 + 3]) + v.w);
-                }
-              }
-            }
-            tmem_st16(tpa + cc, x);
-          }
-          tmem_wait_st();
-        } else {
-          for (int64_t bb = b0; bb <= b1; ++bb) {
-            if (bb == b) continue;
-            if constexpr (C::COLSLOT) {
-              float v[KP];
-#pragma unroll
-              for (int c = 0; c < KP; ++c) v[c] = __ldcg(a.out + fslot<KP>(bb + tp, c, row));
-#pragma unroll
-              for (int c = 0; c < KP; ++c) p[c] += v[c];
-            } else {
-              const float4 *src =
-                  reinterpret_cast<const float4 *>(a.out + ((bb + tp) * 128 + row) * KP);
-#pragma unroll
-              for (int c4 = 0; c4 < KP / 4; ++c4) {
-                const float4 v = __ldcg(src + c4);
-                p[4 * c4 + 0] += v.x;
-                p[4 * c4 + 1] += v.y;
-                p[4 * c4 + 2] += v.z;
-                p[4 * c4 + 3] += v.w;
-              }
-            }
-          }
-        }
-        epi = 1;
-      }
-      fold_bar();  // sflag is read before it is reused
-    }
-    if (!epi) {
+      handoff();
+    } else {
       float *dst = a.out + ((int64_t)(b + tp) * 128 + row) * KP;
       if constexpr (C::PTMEM) {
 #pragma unroll
@@ -1034,33 +961,17 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
           tmem_ld8_nw(tpa + cc, x, 0);
           tmem_ld8_nw(tpa + cc + 8, x, 8);
           tmem_wait_ld_all(x);
-          if (a.fused && C::COLSLOT) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) a.out[fslot<KP>(b + tp, cc + j, row)] = __uint_as_float(x[j]);
-          } else {
-#pragma unroll
-            for (int c4 = 0; c4 < 4; ++c4)
-              reinterpret_cast<float4 *>(dst + cc)[c4] =
-                  make_float4(__uint_as_float(x[4 * c4]), __uint_as_float(x[4 * c4 + 1]),
-                              __uint_as_float(x[4 * c4 + 2]), __uint_as_float(x[4 * c4 + 3]));
-          }
+          for (int c4 = 0; c4 < 4; ++c4)
+            reinterpret_cast<float4 *>(dst + cc)[c4] =
+                make_float4(__uint_as_float(x[4 * c4]), __uint_as_float(x[4 * c4 + 1]),
+                            __uint_as_float(x[4 * c4 + 2]), __uint_as_float(x[4 * c4 + 3]));
         }
-      } else if (a.fused && C::COLSLOT) {
-#pragma unroll
-        for (int c = 0; c < KP; ++c) a.out[fslot<KP>(b + tp, c, row)] = p[c];
       } else {
 #pragma unroll
         for (int cc = 0; cc < KP; cc += 4)
           reinterpret_cast<float4 *>(dst + cc)[0] = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
       }
-      if (a.fused) {
-        pend_tp = tp;
-        pend_b0 = b0;
-        pend_b1 = b1;
-        pend_cd = kDefer;
-      }
-    } else if (a.fused) {
-      handoff(epi);
     }
 #pragma unroll
     for (int c = 0; c < NP; ++c) p[c] = 0.f;
@@ -1183,7 +1094,6 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       if (u + 1 == Lhi || u + 1 == tile_end) finish_segment((int)(u / a.n_cols));
       if (u + 1 == tile_end) tile_end += a.n_cols;
     }
-    if (pend_tp >= 0 && --pend_cd <= 0 && ok) publish_pending();
   };
 
   if constexpr (C::F32) {
@@ -1265,7 +1175,6 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       for (int64_t f = sg.lo[si] * C::SPU / C::FOLD; f < sg.hi[si] * C::SPU / C::FOLD && ok; ++f)
         fold(f, sg.hi[si], si);
   }
-  if (ok && pend_tp >= 0) publish_pending();
 }
 
 // MMA issuer `who` of NISSUE: issues the accumulator chains c with
@@ -1406,8 +1315,7 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
   uint32_t *holder = reinterpret_cast<uint32_t *>(drain + 2);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(holder + 1);
   int *consumed = const_cast<int *>(abort_flag) + 1;  // one per MMA issuer
-  int *sflag = consumed + 2;
-  volatile int *pflag = sflag + 1;  // two entries
+  volatile int *sflag = consumed + 2;
   float *Hs = reinterpret_cast<float *>(smem + STAGES * C::STAGE + C::BAR_BYTES);
   double *scratch = reinterpret_cast<double *>(
       (reinterpret_cast<uintptr_t>(Hs + 128 * (KP + 1)) + 15) & ~uintptr_t(15));
@@ -1501,11 +1409,11 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
       mma_role<DT, KP>(a, sg, smem, tmem_base, full, empty, afull, aempty, tfull, tempty, drain,
                        consumed, abort_flag, warp == 1 ? 0 : 1);
   } else if (warp >= 10 && warp < 14) {
-    const Hand hd{pfull, pempty, pflag};
-    folder_role<DT, KP>(a, tmem_base, smem, full, empty, afull, aempty, tfull, tempty, hd, sflag,
+    const Hand hd{pfull, pempty, sflag};
+    folder_role<DT, KP>(a, tmem_base, smem, full, empty, afull, aempty, tfull, tempty, hd,
                         abort_flag, sg, b, reinterpret_cast<float *>(scratch + 64));
   } else if (warp >= 2 && warp < 10) {
-    const Hand hd{pfull, pempty, pflag};
+    const Hand hd{pfull, pempty, sflag};
     epilogue_role<DT, KP>(a, e, tmem_base, Hs, scratch, hd, abort_flag, sg);
   }
   __syncthreads();
