@@ -775,6 +775,28 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     for (int j = 0; j < KH; ++j) pp[j] = acc[j];
   };
   const int b = blockIdx.x;
+  // holders of the row positions of the share's first and last unit (any
+  // other row position of the share is held by this CTA alone), found
+  // once while idle (each is a 64-bit division loop) and kept in shared
+  // memory: {tile, first holder, last holder} twice, after the scratch
+  // sums of tile_finish
+  // (kp = 64 with BF16 / FP8 storage computes them per segment: there the
+  // extra live state measured slower than the divisions in the tail)
+  constexpr bool kOwnersAhead = (KP < 64 || DT == 0);
+  int64_t *own = reinterpret_cast<int64_t *>(scratch + 48);
+  if (kOwnersAhead && et == 0) {
+    const int64_t WR = (int64_t)a.R * a.n_cols;
+    const bool two = sg.hi[1] > sg.lo[1];
+    const int64_t ulo = two ? (sg.lo[0] < sg.lo[1] ? sg.lo[0] : sg.lo[1]) : sg.lo[0];
+    const int64_t uhi = two ? (sg.hi[0] > sg.hi[1] ? sg.hi[0] : sg.hi[1]) : sg.hi[0];
+    const int64_t t2[2] = {ulo / a.n_cols, (uhi > ulo ? uhi - 1 : ulo) / a.n_cols};
+    for (int i = 0; i < 2; ++i) {
+      own[3 * i] = t2[i];
+      own[3 * i + 1] = sk_owner(a, t2[i] * a.n_cols, WR);
+      own[3 * i + 2] = sk_owner(a, t2[i] * a.n_cols + a.n_cols - 1, WR);
+    }
+  }
+  epi_bar();
   int pb = 0;
   uint32_t pph = 0u;  // bit b: parity of P buffer b
   for (int si = 0; si < 2; ++si)
@@ -817,9 +839,20 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     int epi = 1;
     const int cb = (KP >= 16) ? half * KH : 0;
     const bool owns = (KP >= 16) || half == 0;
-    const int64_t WR = (int64_t)a.R * a.n_cols;
-    const int64_t b0 = sk_owner(a, (int64_t)tp * a.n_cols, WR);
-    const int64_t b1 = sk_owner(a, (int64_t)tp * a.n_cols + a.n_cols - 1, WR);
+    int64_t b0 = b, b1 = b;
+    if constexpr (kOwnersAhead) {
+      if (tp == own[0]) {
+        b0 = own[1];
+        b1 = own[2];
+      } else if (tp == own[3]) {
+        b0 = own[4];
+        b1 = own[5];
+      }
+    } else {
+      const int64_t WR = (int64_t)a.R * a.n_cols;
+      b0 = sk_owner(a, (int64_t)tp * a.n_cols, WR);
+      b1 = sk_owner(a, (int64_t)tp * a.n_cols + a.n_cols - 1, WR);
+    }
     if (b0 < b1) {
       epi = 0;
       if (b - b0 <= 1) {
