@@ -14,10 +14,12 @@
 //   dep_gemm    persistent, one CTA per SM over the list of 128 x 256
 //               tiles of G, on tcgen05 (kind::tf32, M = 128, N = 256, two
 //               accumulators in tensor memory taken in turn, so a tile's
-//               epilogue overlaps the next tile's MMAs) over
-//               K = 3 Tp: A = [hi | lo | hi], B = [hi | hi | lo] fetched
-//               from P by TMA (the three products hi hi, lo hi, hi lo; the
-//               dropped lo lo term is below 2^-21 relative); the epilogue
+//               epilogue overlaps the next tile's MMAs): each stage holds a
+//               16-column chunk of A_hi, A_lo, B_hi and B_lo (64-byte
+//               swizzle, fetched from P by TMA) and feeds the three products
+//               hi hi, lo hi and hi lo (the dropped lo lo term is below
+//               2^-21 relative), so every staged byte serves two products;
+//               the epilogue
 //               normalises, clamps to [0, 1], writes 1 on the diagonal and
 //               stores S as FP32, BF16 (round to nearest) or E4M3 with one
 //               power-of-two scale per 128 x 128 tile, plus the CTA's FP64
@@ -46,9 +48,10 @@ namespace {
 using namespace tc;
 
 constexpr int kDepStages = 4;
-constexpr uint32_t kDepA = 128 * 128;          // 128 rows x 32 tf32
-constexpr uint32_t kDepB = 256 * 128;          // 256 rows x 32 tf32
-constexpr uint32_t kDepStage = kDepA + kDepB;  // 48 KB
+constexpr int kDepKC = 16;                             // tf32 per staged row (64 bytes)
+constexpr uint32_t kDepA = 128 * 64;                   // 128 rows x 16 tf32
+constexpr uint32_t kDepB = 256 * 64;                   // 256 rows x 16 tf32
+constexpr uint32_t kDepStage = 2 * kDepA + 2 * kDepB;  // A_hi, A_lo, B_hi, B_lo: 48 KB
 constexpr size_t kDepSmem = 1024 + (size_t)kDepStages * kDepStage + 256 + 256 * 4 + 64 * 8;
 constexpr int kDepThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 
@@ -100,7 +103,7 @@ __global__ void dep_split_kernel(const float *Y, int64_t T, int64_t n, int64_t l
 struct DepArgs {
   int64_t n;
   int Tp;
-  int natoms;       // 3 Tp / 32
+  int natoms;       // Tp / 16 staged chunks per tile
   int ntiles;       // entries of the tile list
   const int *tiles; // (ib << 16 | jb) per 128 x 256 tile on or above the diagonal
   const double *inv_d;
@@ -155,7 +158,6 @@ __global__ void __launch_bounds__(kDepThreads, 1)
   fence_after();
   const uint32_t tbase = *holder;
   int issued = 0;
-  const int apt = a.Tp / 32;  // atoms per segment
 
   if (warp == 0) {
     if (lane == 0) {
@@ -174,14 +176,16 @@ __global__ void __launch_bounds__(kDepThreads, 1)
             stop = true;
             break;
           }
-          const int seg = at / apt, o = (at % apt) * 32;
-          const int xa = (seg == 1 ? a.Tp : 0) + o;
-          const int xb = (seg == 2 ? a.Tp : 0) + o;
+          const int o = at * kDepKC;
           uint8_t *st = smem + (size_t)s * kDepStage;
+          uint8_t *sb = st + 2 * kDepA;
           mbar_expect_tx(&full[s], kDepStage);
-          tma_load_2d(st, &mP, &full[s], xa, ib * 128);
-          tma_load_2d(st + kDepA, &mP, &full[s], xb, jb * 256);
-          tma_load_2d(st + kDepA + kDepA, &mP, &full[s], xb, jb * 256 + 128);
+          tma_load_2d(st, &mP, &full[s], o, ib * 128);                    // A_hi
+          tma_load_2d(st + kDepA, &mP, &full[s], a.Tp + o, ib * 128);     // A_lo
+          tma_load_2d(sb, &mP, &full[s], o, jb * 256);                    // B_hi
+          tma_load_2d(sb + kDepB / 2, &mP, &full[s], o, jb * 256 + 128);
+          tma_load_2d(sb + kDepB, &mP, &full[s], a.Tp + o, jb * 256);     // B_lo
+          tma_load_2d(sb + kDepB + kDepB / 2, &mP, &full[s], a.Tp + o, jb * 256 + 128);
           ++issued;
         }
       }
@@ -209,11 +213,15 @@ __global__ void __launch_bounds__(kDepThreads, 1)
             break;
           }
           fence_after();
-          const uint32_t sa = smem_u32(smem + (size_t)s * kDepStage), sb = sa + kDepA;
+          const uint32_t ah = smem_u32(smem + (size_t)s * kDepStage), al = ah + kDepA;
+          const uint32_t bh = ah + 2 * kDepA, bl = bh + kDepB;
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            mma_tf32_ss(tacc, sdesc(sa + ks * 32), sdesc(sb + ks * 32), idesc,
-                        (at > 0 || ks > 0) ? 1u : 0u);
+          for (int ks = 0; ks < kDepKC / 8; ++ks) {  // K = 8 tf32 (32 bytes) per MMA
+            const uint32_t o = (uint32_t)ks * 32u;
+            mma_tf32_ss(tacc, sdesc64(ah + o), sdesc64(bh + o), idesc, (at > 0 || ks > 0) ? 1u : 0u);
+            mma_tf32_ss(tacc, sdesc64(al + o), sdesc64(bh + o), idesc, 1u);
+            mma_tf32_ss(tacc, sdesc64(ah + o), sdesc64(bl + o), idesc, 1u);
+          }
           mma_commit(&empty[s]);
           done = c + 1;
         }
@@ -498,7 +506,7 @@ cudaError_t launch_dependence(const float *Y, int64_t T, int64_t n, int64_t ldy,
         Y, T, n, ldy, mean32, Tp, P);
     CUtensorMap mP;
     if (!make_map_2d(&mP, P, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (uint64_t)2 * Tp, (uint64_t)n,
-                     (uint64_t)2 * Tp * 4, 32, 128)) {
+                     (uint64_t)2 * Tp * 4, kDepKC, 128, 64)) {
       e = cudaErrorInvalidValue;
     } else {
       e = cudaFuncSetAttribute(dep_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -508,7 +516,7 @@ cudaError_t launch_dependence(const float *Y, int64_t T, int64_t n, int64_t ldy,
       DepArgs a{};
       a.n = n;
       a.Tp = Tp;
-      a.natoms = 3 * Tp / 32;
+      a.natoms = Tp / kDepKC;
       a.ntiles = ntiles;
       a.tiles = dtiles;
       a.inv_d = inv_d;

@@ -153,9 +153,11 @@ cudaError_t launch_step_tc(const ProdArgs &a, const EpiArgs *epi, int *tile_cnt,
                            int num_sms, int *G_out, int *err);
 bool tc_supported(int dtype, int kp);
 // TMA descriptor of a 2-D row-major array: inner extent, outer extent, row
-// pitch in bytes, box; 128-byte swizzle, zero fill out of bounds
+// pitch in bytes, box; 128-byte (or 64-byte) swizzle, zero fill out of
+// bounds
 bool make_map_2d(CUtensorMap *m, const void *base, CUtensorMapDataType dt, uint64_t inner,
-                 uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
+                 uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
+                 int swizzle_bytes = 128);
 // ADMM (appendix, Family 6): minv = (2 G + rho I)^-1 for the FP64 Gram G
 // (kp x kp, entries past k ignored; minv is the identity there).  Launched
 // as a programmatic dependent of the preceding kernel.
