@@ -659,10 +659,11 @@ def run_large_fp8(args):
 def run_batch(args):
     """Batching workload: 64 instances (n ~ U{2000..30000}, k in {8,16,32,64},
     even = correlation, odd = TPDM), BF16 S, 4 random restarts each, Piecewise
-    AdaGrad (eta 1, c 10, c_r 10).  Where 4 k <= 64 the restarts are
-    concatenated along N in one handle (symnmf_set_restarts: one stream of S
-    feeds all four); the other instances run one handle per restart, each
-    handle on its own stream.  The library's autotuner picks the CTA caps
+    AdaGrad (eta 1, c 10, c_r 10).  The restarts of an instance are
+    concatenated along N, as many per handle as fit the rank-64 kernels
+    (symnmf_set_restarts: one stream of S feeds them all): all four for
+    k <= 16, two handles of two for k = 32, one handle per restart for
+    k = 64; each handle runs on its own stream.  The library's autotuner picks the CTA caps
     (its trial iterations are part of the solves); then the batch runs to
     the AND rule.  Reports aggregate restart-iterations/s and per-instance
     time to tolerance (first handle of the instance to converge)."""
@@ -690,19 +691,22 @@ def run_batch(args):
         mats.append(S)
         mean = float(S[: min(n, 4096), :n].double().mean())
         R = args.restarts
-        if args.joint and R * k <= 64:
-            st = torch.cuda.Stream(device=dev)
-            h = L.symnmf_create_ld(S, n, ld, R * k, L.BF16)
-            L.symnmf_set_stream(h, st)
-            L.symnmf_set_restarts(h, R)
-            H0 = np.concatenate([gen.init_scaled(mean, n, k, seed=sp["seed"], stream=r)
-                                 for r in range(R)], axis=1)
-            L.symnmf_set_H(h, torch.tensor(H0, dtype=torch.float32, device=dev))
-            handles.append(h)
-            streams.append(st)
-            hps.append(L.symnmf_hparams_default(L.PIECEWISE_ADAGRAD, eta=1.0, c=10.0, c_r=10.0))
-            owner.append(i)
-            mult.append(R)
+        # restarts per handle: the largest divisor g of R with g k <= 64
+        g = max(d for d in range(1, R + 1) if R % d == 0 and d * k <= 64) if args.joint else 1
+        if g > 1:
+            for r0 in range(0, R, g):
+                st = torch.cuda.Stream(device=dev)
+                h = L.symnmf_create_ld(S, n, ld, g * k, L.BF16)
+                L.symnmf_set_stream(h, st)
+                L.symnmf_set_restarts(h, g)
+                H0 = np.concatenate([gen.init_scaled(mean, n, k, seed=sp["seed"], stream=r)
+                                     for r in range(r0, r0 + g)], axis=1)
+                L.symnmf_set_H(h, torch.tensor(H0, dtype=torch.float32, device=dev))
+                handles.append(h)
+                streams.append(st)
+                hps.append(L.symnmf_hparams_default(L.PIECEWISE_ADAGRAD, eta=1.0, c=10.0, c_r=10.0))
+                owner.append(i)
+                mult.append(g)
             continue
         for r in range(R):
             st = torch.cuda.Stream(device=dev)
@@ -737,6 +741,10 @@ def run_batch(args):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     total_iters = sum(it * m for it, m in zip(iters_done, mult))
+    # S bytes one round (an iteration of every handle) streams, and the
+    # algorithmic figure (each instance's S once per round)
+    s_round = sum(2 * specs[owner[j]]["n"] ** 2 for j in range(len(handles)))
+    s_alg = sum(2 * sp["n"] ** 2 for sp in specs)
     per_inst = []
     for i, sp in enumerate(specs):
         js = [j for j in range(len(handles)) if owner[j] == i]
@@ -758,6 +766,7 @@ def run_batch(args):
                        "sum_n2": int(sum(sp["n"] ** 2 for sp in specs)),
                        "autotune_iters_per_candidate": args.tune_iters, "iteration_cap": args.batch_cap},
             "wall_s": wall, "total_iters": total_iters,
+            "s_bytes_per_round": s_round, "s_bytes_per_round_algorithmic": s_alg,
             "converged_handles": sum(1 for c in conv_at if c is not None),
             "instances_converged": len(tt),
             "time_to_tol_s": {"median": float(np.median(tt)) if tt else None,

@@ -115,7 +115,11 @@ struct Cfg {
   static constexpr uint32_t EPI_BYTES = EPI_FLOATS * 4 + 512 + (F8 ? 1024 : 0);
   static constexpr uint32_t BAR_BYTES = 512;
   static constexpr uint32_t BUDGET = 232448u - 1024u - BAR_BYTES - EPI_BYTES;
-  static constexpr int STAGES = (BUDGET / STAGE) < 8u ? (int)(BUDGET / STAGE) : 8;
+  // fewer stages than fit measured faster at kp = 64 (every storage type)
+  // and with FP8 at kp = 32: about 120-130 KB in flight per SM; more only
+  // lengthens the round trips
+  static constexpr int STAGE_CAP = KP == 64 ? 4 : (F8 && KP == 32) ? 5 : 8;
+  static constexpr int STAGES = (BUDGET / STAGE) < (uint32_t)STAGE_CAP ? (int)(BUDGET / STAGE) : STAGE_CAP;
   static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + BAR_BYTES + EPI_BYTES;
   // MMA issuing threads (warps 1 and 14).  One thread issues a tcgen05.mma
   // about every 60 SM cycles at best, so a skinny-N stream of S is bounded
@@ -222,7 +226,33 @@ template <int KP>
 struct Own {
   static constexpr int KH = KP >= 16 ? KP / 2 : KP;
   static constexpr int HW = KH <= 16 ? KH : 16;  // columns whose state is held at once
+  // kp = 64: H_t Gram_t is formed 8 columns at a time once the tile's S H
+  // rows are in (the 32 values would be held across the wait otherwise)
+  static constexpr bool LATE_HG = (KP == 64);
+  static constexpr int HG = LATE_HG ? 1 : KH;
 };
+// the thread's H_t Gram_t for the 8 owned columns from c (row hrow of Hs,
+// columns cb + c ..), summed over d in order
+template <int KP>
+__device__ __forceinline__ void hgram8(const float *hrow, const float *Gs, int cb, int c,
+                                       float (&h8)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) h8[j] = 0.f;
+#pragma unroll 4
+  for (int d = 0; d < KP; ++d) {
+    const float hv = hrow[d];
+    const float4 *gr = reinterpret_cast<const float4 *>(Gs + d * KP + cb + c);
+    const float4 g0 = __ldg(gr), g1 = __ldg(gr + 1);
+    h8[0] = fmaf(hv, g0.x, h8[0]);
+    h8[1] = fmaf(hv, g0.y, h8[1]);
+    h8[2] = fmaf(hv, g0.z, h8[2]);
+    h8[3] = fmaf(hv, g0.w, h8[3]);
+    h8[4] = fmaf(hv, g1.x, h8[4]);
+    h8[5] = fmaf(hv, g1.y, h8[5]);
+    h8[6] = fmaf(hv, g1.z, h8[6]);
+    h8[7] = fmaf(hv, g1.w, h8[7]);
+  }
+}
 
 // Rows [0, rows) of a tile held in Hs (row stride KP + 1) to dst (row
 // stride KP) by the 256 epilogue threads: each warp store covers whole
@@ -270,7 +300,7 @@ __device__ __forceinline__ void load_rows(float4 (&v)[KP / 8], const float *src,
 }
 template <int DT, int KP>
 __device__ __forceinline__ void tile_prep(const EpiArgs &e, int tp, float *Hs, const float *Gs,
-                                          int row, int half, int et, float (&hg)[Own<KP>::KH],
+                                          int row, int half, int et, float (&hg)[Own<KP>::HG],
                                           float (&av)[Own<KP>::HW], float (&mv)[Own<KP>::HW]) {
   constexpr int KH = Own<KP>::KH;
   constexpr int HW = Own<KP>::HW;
@@ -336,14 +366,15 @@ __device__ __forceinline__ void tile_prep(const EpiArgs &e, int tp, float *Hs, c
   epi_bar();  // both halves of each H_t row are in Hs
   }
   // (H_t Gram_t) for the owned columns, right to left (Sec. 2.1)
+  if constexpr (Own<KP>::LATE_HG) return;
 #pragma unroll
-  for (int j = 0; j < KH; ++j) hg[j] = 0.f;
+  for (int j = 0; j < Own<KP>::HG; ++j) hg[j] = 0.f;
 #pragma unroll 2
   for (int d = 0; d < KP; ++d) {
     const float hv = hrow[d];
     const float4 *gr = reinterpret_cast<const float4 *>(Gs + d * KP + cb);
 #pragma unroll
-    for (int c4 = 0; c4 < KH / 4; ++c4) {
+    for (int c4 = 0; c4 < Own<KP>::HG / 4; ++c4) {
       const float4 gv = __ldg(gr + c4);
       hg[4 * c4 + 0] = fmaf(hv, gv.x, hg[4 * c4 + 0]);
       hg[4 * c4 + 1] = fmaf(hv, gv.y, hg[4 * c4 + 1]);
@@ -361,7 +392,7 @@ __device__ __forceinline__ void tile_prep(const EpiArgs &e, int tp, float *Hs, c
 // are left to the reduction kernel.
 template <int DT, int KP>
 __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)[Own<KP>::KH],
-                                            const float (&hg)[Own<KP>::KH],
+                                            const float (&hg)[Own<KP>::HG],
                                             float (&av)[Own<KP>::HW], float (&mv)[Own<KP>::HW],
                                             float *Hs, double *scratch, int et, int row,
                                             int half) {
@@ -396,13 +427,24 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
     if constexpr (KH == HW) return av[j];
     else return (vrow && e.update) ? e.A[base + j] : 0.f;
   };
+  // H_t Gram_t of column j: precomputed, or (kp = 64) formed 8 at a time
+  float h8[8];
+  auto hg_of = [&](int j) -> float {
+    if constexpr (Own<KP>::LATE_HG) {
+      if ((j & 7) == 0) hgram8<KP>(hrow, e.gram, cb, j, h8);
+      return h8[j & 7];
+    } else {
+      return hg[j];
+    }
+  };
   if (!admm) {
 #pragma unroll
     for (int j = 0; j < KH; ++j) {
       float g = 0.f;
+      const float hgj = hg_of(j);
       if (cb + j < e.k) {
         tr = fmaf(hrow[cb + j], p[j], tr);
-        g = e.coef * (hg[j] - p[j]);
+        g = e.coef * (hgj - p[j]);
         const float pg = (hrow[cb + j] > 0.f) ? g : fminf(0.f, g);
         kkt2 = fmaf(pg, pg, kkt2);
         if (!isfinite(g)) nonfin += 1.f;
@@ -419,10 +461,11 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
       for (int jj = 0; jj < 4; ++jj) {
         const int j = 4 * c4 + jj;
         float g = 0.f, r = 0.f;
+        const float hgj = hg_of(j);
         if (cb + j < e.k) {
           const float h = hrow[cb + j];
           tr = fmaf(h, p[j], tr);
-          g = e.coef * (hg[j] - p[j]);
+          g = e.coef * (hgj - p[j]);
           const float pg = (h > 0.f) ? g : fminf(0.f, g);
           kkt2 = fmaf(pg, pg, kkt2);
           if (!isfinite(g)) nonfin += 1.f;
@@ -708,7 +751,7 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
   const float *Gs = e.gram;
   constexpr int KH = Own<KP>::KH;
   constexpr int HW = Own<KP>::HW;
-  float hg[KH], av[HW], mv[HW];
+  float hg[Own<KP>::HG], av[HW], mv[HW];
   // The tile segments in streaming order; the epilogue prepares the next
   // one while it is idle, whether or not this CTA will finish it (the
   // last CTA of a tile to arrive does), so a finish starts with its tile's
@@ -739,40 +782,49 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
   // CTAs b0..b1 but `self` to p in CTA order (p holds this CTA's part,
   // first in the order); sum_parts forms the CTA-order sum of all of them
   // with p standing for this CTA's part at its place.
-  auto load_part = [&](float (&v)[KH], int64_t bb, int tp, int cb) {
+  // (kp = 64: 8 columns at a time, fewer live registers; the additions of
+  // each column keep CTA order either way)
+  constexpr int PC = Own<KP>::LATE_HG ? 8 : KH;
+  auto load_pc = [&](float (&v)[PC], int64_t bb, int tp, int c) {
 #pragma unroll
-    for (int j = 0; j < KH; ++j) v[j] = __ldcg(a.out + fslot<KP>(bb + tp, cb + j, row));
+    for (int j = 0; j < PC; ++j) v[j] = __ldcg(a.out + fslot<KP>(bb + tp, c + j, row));
   };
   auto add_parts = [&](float (&pp)[KH], int64_t b0, int64_t b1, int64_t self, int tp, int cb) {
-    for (int64_t bb = b0; bb <= b1; ++bb) {
-      if (bb == self) continue;
-      float v[KH];
-      load_part(v, bb, tp, cb);
 #pragma unroll
-      for (int j = 0; j < KH; ++j) pp[j] += v[j];
+    for (int c0 = 0; c0 < KH; c0 += PC) {
+      for (int64_t bb = b0; bb <= b1; ++bb) {
+        if (bb == self) continue;
+        float v[PC];
+        load_pc(v, bb, tp, cb + c0);
+#pragma unroll
+        for (int j = 0; j < PC; ++j) pp[c0 + j] += v[j];
+      }
     }
   };
   auto sum_parts = [&](float (&pp)[KH], int64_t b0, int64_t b1, int64_t self, int tp, int cb) {
-    float acc[KH];
-    if (b0 == self) {
 #pragma unroll
-      for (int j = 0; j < KH; ++j) acc[j] = pp[j];
-    } else {
-      load_part(acc, b0, tp, cb);
-    }
-    for (int64_t bb = b0 + 1; bb <= b1; ++bb) {
-      if (bb == self) {
+    for (int c0 = 0; c0 < KH; c0 += PC) {
+      float acc[PC];
+      if (b0 == self) {
 #pragma unroll
-        for (int j = 0; j < KH; ++j) acc[j] += pp[j];
+        for (int j = 0; j < PC; ++j) acc[j] = pp[c0 + j];
       } else {
-        float v[KH];
-        load_part(v, bb, tp, cb);
-#pragma unroll
-        for (int j = 0; j < KH; ++j) acc[j] += v[j];
+        load_pc(acc, b0, tp, cb + c0);
       }
-    }
+      for (int64_t bb = b0 + 1; bb <= b1; ++bb) {
+        if (bb == self) {
 #pragma unroll
-    for (int j = 0; j < KH; ++j) pp[j] = acc[j];
+          for (int j = 0; j < PC; ++j) acc[j] += pp[c0 + j];
+        } else {
+          float v[PC];
+          load_pc(v, bb, tp, cb + c0);
+#pragma unroll
+          for (int j = 0; j < PC; ++j) acc[j] += v[j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < PC; ++j) pp[c0 + j] = acc[j];
+    }
   };
   const int b = blockIdx.x;
   // holders of the row positions of the share's first and last unit (any
