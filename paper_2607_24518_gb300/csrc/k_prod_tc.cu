@@ -109,8 +109,10 @@ struct Cfg {
   static constexpr int FOLD = F32 ? 1 : SPU;
   // accumulator columns per part read before one wait when folding
   static constexpr int FOLD_CW = F32 ? 8 : (KP == 64 ? 16 : 32);
-  // the epilogue's H tile; the Gram of H_t is read from global memory (L1)
-  static constexpr uint32_t EPI_FLOATS = 128 * (KP + 1);
+  // the epilogue's H tile (kp = 64: and a second tile-shaped buffer for
+  // H_t Gram_t and then g, which 32 columns per thread cannot keep in
+  // registers); the Gram of H_t is read from global memory (L1)
+  static constexpr uint32_t EPI_FLOATS = 128 * (KP + 1) * (KP == 64 ? 2 : 1);
   // + FP8: a ring of 256 unit scales after the epilogue scratch
   static constexpr uint32_t EPI_BYTES = EPI_FLOATS * 4 + 512 + (F8 ? 1024 : 0);
   static constexpr uint32_t BAR_BYTES = 512;
@@ -226,10 +228,10 @@ template <int KP>
 struct Own {
   static constexpr int KH = KP >= 16 ? KP / 2 : KP;
   static constexpr int HW = KH <= 16 ? KH : 16;  // columns whose state is held at once
-  // kp = 64: H_t Gram_t is formed 8 columns at a time once the tile's S H
-  // rows are in (the 32 values would be held across the wait otherwise)
-  static constexpr bool LATE_HG = (KP == 64);
-  static constexpr int HG = LATE_HG ? 1 : KH;
+  // kp = 64: H_t Gram_t, then g (or ADMM's x), live in the shared-memory
+  // buffer Gx rather than in 32 registers per thread
+  static constexpr bool GX = (KP == 64);
+  static constexpr int HG = GX ? 1 : KH;
 };
 // the thread's H_t Gram_t for the 8 owned columns from c (row hrow of Hs,
 // columns cb + c ..), summed over d in order
@@ -299,8 +301,9 @@ __device__ __forceinline__ void load_rows(float4 (&v)[KP / 8], const float *src,
   }
 }
 template <int DT, int KP>
-__device__ __forceinline__ void tile_prep(const EpiArgs &e, int tp, float *Hs, const float *Gs,
-                                          int row, int half, int et, float (&hg)[Own<KP>::HG],
+__device__ __forceinline__ void tile_prep(const EpiArgs &e, int tp, float *Hs, float *Gx,
+                                          const float *Gs, int row, int half, int et,
+                                          float (&hg)[Own<KP>::HG],
                                           float (&av)[Own<KP>::HW], float (&mv)[Own<KP>::HW]) {
   constexpr int KH = Own<KP>::KH;
   constexpr int HW = Own<KP>::HW;
@@ -366,7 +369,17 @@ __device__ __forceinline__ void tile_prep(const EpiArgs &e, int tp, float *Hs, c
   epi_bar();  // both halves of each H_t row are in Hs
   }
   // (H_t Gram_t) for the owned columns, right to left (Sec. 2.1)
-  if constexpr (Own<KP>::LATE_HG) return;
+  if constexpr (Own<KP>::GX) {
+    float *gx = Gx + row * (KP + 1) + cb;
+#pragma unroll 1
+    for (int c = 0; c < KH; c += 8) {
+      float h8[8];
+      hgram8<KP>(hrow, Gs, cb, c, h8);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) gx[c + j] = h8[j];
+    }
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < Own<KP>::HG; ++j) hg[j] = 0.f;
 #pragma unroll 2
@@ -394,8 +407,8 @@ template <int DT, int KP>
 __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)[Own<KP>::KH],
                                             const float (&hg)[Own<KP>::HG],
                                             float (&av)[Own<KP>::HW], float (&mv)[Own<KP>::HW],
-                                            float *Hs, double *scratch, int et, int row,
-                                            int half) {
+                                            float *Hs, float *Gx, double *scratch, int et,
+                                            int row, int half) {
   constexpr int KH = Own<KP>::KH;
   constexpr int HW = Own<KP>::HW;
   const bool works = (KP >= 16) || half == 0;
@@ -427,15 +440,11 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
     if constexpr (KH == HW) return av[j];
     else return (vrow && e.update) ? e.A[base + j] : 0.f;
   };
-  // H_t Gram_t of column j: precomputed, or (kp = 64) formed 8 at a time
-  float h8[8];
+  // H_t Gram_t of column j: in registers, or (kp = 64) in Gx
+  float *gxrow = Gx + row * (KP + 1) + cb;
   auto hg_of = [&](int j) -> float {
-    if constexpr (Own<KP>::LATE_HG) {
-      if ((j & 7) == 0) hgram8<KP>(hrow, e.gram, cb, j, h8);
-      return h8[j & 7];
-    } else {
-      return hg[j];
-    }
+    if constexpr (Own<KP>::GX) return gxrow[j];
+    else return hg[j];
   };
   if (!admm) {
 #pragma unroll
@@ -449,7 +458,8 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
         kkt2 = fmaf(pg, pg, kkt2);
         if (!isfinite(g)) nonfin += 1.f;
       }
-      p[j] = g;
+      if constexpr (Own<KP>::GX) gxrow[j] = g;
+      else p[j] = g;
     }
   } else {
     // g goes out at once (checks only); p becomes the right-hand side
@@ -507,8 +517,21 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
     }
     epi_bar();  // every thread has read the right-hand sides from Hs
   }
-  // update and projection, HW columns at a time
+  if constexpr (Own<KP>::GX) {
+    if (admm) {
 #pragma unroll
+      for (int j = 0; j < KH; ++j) gxrow[j] = p[j];  // x (update) or the rhs
+    }
+  }
+  // g (ADMM: x) of owned column c
+  auto gv = [&](int c) -> float {
+    if constexpr (Own<KP>::GX) return gxrow[c];
+    else return p[c];
+  };
+  // update and projection, HW columns at a time (one pass below kp = 64;
+  // at kp = 64 the two passes stay a loop, which keeps the state of one
+  // in registers at a time)
+#pragma unroll 1
   for (int hc = 0; hc < KH; hc += HW) {
     if (hc > 0) load_state(hc);
 #pragma unroll
@@ -518,14 +541,14 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
       for (int j = 0; j < 8; ++j) {
         const int c = cb + cc + j, s = cc - hc + j;
         const float h = hrow[c];
-        const float g = p[cc + j];
+        const float g = gv(cc + j);
         hn[j] = h;
         if (e.update) {
           if (c < e.k && vrow) {
             float x;
             if (admm) {
               // W' = [x]_+, U' = x - W' = U + H - W'
-              x = p[cc + j];
+              x = gv(cc + j);
               av[s] = x - ((x > 0.f) ? x : 0.f);
               sumA += av[s];
             } else if (rms) {
@@ -549,8 +572,8 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
       }
       const int s0 = cc - hc;
       if (vrow) {
-        const float4 p0 = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
-        const float4 p1 = make_float4(p[cc + 4], p[cc + 5], p[cc + 6], p[cc + 7]);
+        const float4 p0 = make_float4(gv(cc), gv(cc + 1), gv(cc + 2), gv(cc + 3));
+        const float4 p1 = make_float4(gv(cc + 4), gv(cc + 5), gv(cc + 6), gv(cc + 7));
         if (e.gout && !admm) {
           float4 *g4 = reinterpret_cast<float4 *>(e.gout + base + cc);
           g4[0] = p0;
@@ -564,7 +587,7 @@ __device__ __forceinline__ void tile_finish(const EpiArgs &e, int tp, float (&p)
         if (e.gcaller && !admm) {
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            if (cb + cc + j < e.k) e.gcaller[(r0 + row) * e.k + cb + cc + j] = p[cc + j];
+            if (cb + cc + j < e.k) e.gcaller[(r0 + row) * e.k + cb + cc + j] = gv(cc + j);
         }
         // H_{t+1} leaves through Hs below, and so does the optimizer
         // state when all of the thread's columns are in registers at once
@@ -742,6 +765,7 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
   const int row = q * 32 + lane;
   const int et = (warp - 2) * 32 + lane;  // 0..255
   const int half = (warp - 2) >> 2;       // column half owned
+  float *Gx = Hs + 128 * (KP + 1);        // kp = 64 only (Own<KP>::GX)
   if (!a.fused) return;
   // the Gram of H_t and the tile slots belong to the preceding reduction
   // kernel, which may still run (programmatic dependent launch).  The Gram
@@ -770,11 +794,13 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
   int prepared = -1, final_tp = -1;
   if (sg.hi[0] > sg.lo[0])
     final_tp = (int)(((sg.hi[1] > sg.lo[1] ? sg.hi[1] : sg.hi[0]) - 1) / a.n_cols);
-  if constexpr (KH == HW) {
+  // (kp = 64 too: its H_t Gram_t waits in Gx, not in registers)
+  constexpr bool kPrepAhead = (KH == HW) || Own<KP>::GX;
+  if constexpr (kPrepAhead) {
     const int t0 = kPrepNext ? tile_from(0, sg.lo[0]) : final_tp;
     if (t0 >= 0) {
       prepared = t0;
-      tile_prep<DT, KP>(e, prepared, Hs, Gs, row, half, et, hg, av, mv);
+      tile_prep<DT, KP>(e, prepared, Hs, Gx, Gs, row, half, et, hg, av, mv);
     }
   }
   // Parts of tile tp left by other CTAs (fused slots, column-major): the
@@ -784,7 +810,7 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
   // with p standing for this CTA's part at its place.
   // (kp = 64: 8 columns at a time, fewer live registers; the additions of
   // each column keep CTA order either way)
-  constexpr int PC = Own<KP>::LATE_HG ? 8 : KH;
+  constexpr int PC = Own<KP>::GX ? 8 : KH;
   auto load_pc = [&](float (&v)[PC], int64_t bb, int tp, int c) {
 #pragma unroll
     for (int j = 0; j < PC; ++j) v[j] = __ldcg(a.out + fslot<KP>(bb + tp, c + j, row));
@@ -947,18 +973,18 @@ __device__ void epilogue_role(const TcArgs &a, const EpiArgs &e, uint32_t tmem_b
     if (epi) {
       if (tp != prepared) {
         epi_bar();  // no thread still reads Hs of an earlier tile
-        tile_prep<DT, KP>(e, tp, Hs, Gs, row, half, et, hg, av, mv);
+        tile_prep<DT, KP>(e, tp, Hs, Gx, Gs, row, half, et, hg, av, mv);
       }
       prepared = -1;
-      tile_finish<DT, KP>(e, tp, p, hg, av, mv, Hs, scratch, et, row, half);
+      tile_finish<DT, KP>(e, tp, p, hg, av, mv, Hs, Gx, scratch, et, row, half);
     }
-    if constexpr (KH == HW) {
+    if constexpr (kPrepAhead) {
       // prepare the next segment's tile while the stream goes on
       const int nx = kPrepNext ? tile_from(si, L) : (epi && tp != final_tp) ? final_tp : -1;
       if (nx >= 0 && nx != prepared) {
         epi_bar();  // no thread still reads Hs
         prepared = nx;
-        tile_prep<DT, KP>(e, prepared, Hs, Gs, row, half, et, hg, av, mv);
+        tile_prep<DT, KP>(e, prepared, Hs, Gx, Gs, row, half, et, hg, av, mv);
       }
     }
   }
@@ -1403,7 +1429,7 @@ __global__ void __launch_bounds__(Cfg<DT, KP>::THREADS, 1)
   volatile int *sflag = consumed + 2;
   float *Hs = reinterpret_cast<float *>(smem + STAGES * C::STAGE + C::BAR_BYTES);
   double *scratch = reinterpret_cast<double *>(
-      (reinterpret_cast<uintptr_t>(Hs + 128 * (KP + 1)) + 15) & ~uintptr_t(15));
+      (reinterpret_cast<uintptr_t>(Hs + C::EPI_FLOATS) + 15) & ~uintptr_t(15));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
