@@ -144,7 +144,11 @@ struct Cfg {
   // budget of a 16-warp CTA cannot hold next to a fold's loads
   static constexpr bool PTMEM = (KP == 64);
   static constexpr uint32_t PA0 = PB0 + 2 * KP;
-  static constexpr uint32_t TMEM_NEED = PA0 + (PTMEM ? KP : 0);
+  // columns of the running sum kept in registers (kp = 64 with FP32
+  // storage: half of them, which measured faster there; BF16 and FP8 keep
+  // all of them in PA)
+  static constexpr int NPR = !PTMEM ? KP : F32 ? KP / 2 : 0;
+  static constexpr uint32_t TMEM_NEED = PA0 + (uint32_t)(KP - NPR);
   static constexpr uint32_t TMEM_COLS = TMEM_NEED <= 32 ? 32 : TMEM_NEED <= 64 ? 64 : TMEM_NEED <= 128 ? 128 : TMEM_NEED <= 256 ? 256 : 512;
   static_assert(STAGES >= 2, "shared memory ring too small");
   static_assert(TMEM_NEED <= 512, "tensor memory budget exceeded");
@@ -1006,11 +1010,12 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
   const int row = q * 32 + lane;
   const int ft = (warp - 10) * 32 + lane;
   const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-  constexpr int NP = C::PTMEM ? 1 : KP;  // register sum (PTMEM: unused)
-  float p[NP];
+  constexpr int NP = C::NPR;  // columns [0, NP) of the sum in registers, the rest in PA
+  constexpr int NPA = NP > 0 ? NP : 1;
+  float p[NPA];
 #pragma unroll
-  for (int c = 0; c < NP; ++c) p[c] = 0.f;
-  bool pa_first = true;                   // PTMEM: the next fold starts PA
+  for (int c = 0; c < NPA; ++c) p[c] = 0.f;
+  bool pa_first = true;                   // PTMEM: the next fold starts PA (columns [NP, kp))
   const uint32_t tpa = tmem_base + lane_off + C::PA0;
   int acc = 0, pb = 0;
   uint32_t tph = 0u, pph = 0u;  // bit i: parity of accumulator / P buffer i
@@ -1037,16 +1042,17 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     const uint32_t tb = tmem_base + lane_off + C::PB0 + (uint32_t)(pb * KP);
     if constexpr (C::PTMEM) {
 #pragma unroll
-      for (int cc = 0; cc < KP; cc += 16) {
+      for (int cc = NP; cc < KP; cc += 16) {
         uint32_t x[16];
-        tmem_ld8_nw(tpa + cc, x, 0);
-        tmem_ld8_nw(tpa + cc + 8, x, 8);
+        tmem_ld8_nw(tpa + (cc - NP), x, 0);
+        tmem_ld8_nw(tpa + (cc - NP) + 8, x, 8);
         tmem_wait_ld_all(x);
         tmem_st16(tb + cc, x);
       }
-    } else {
+    }
+    {
 #pragma unroll
-      for (int cc = 0; cc < KP; cc += 8) {
+      for (int cc = 0; cc < NP; cc += 8) {
         float v[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = p[cc + j];
@@ -1067,10 +1073,10 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       float *dst = a.out + ((int64_t)(b + tp) * 128 + row) * KP;
       if constexpr (C::PTMEM) {
 #pragma unroll
-        for (int cc = 0; cc < KP; cc += 16) {
+        for (int cc = NP; cc < KP; cc += 16) {
           uint32_t x[16];
-          tmem_ld8_nw(tpa + cc, x, 0);
-          tmem_ld8_nw(tpa + cc + 8, x, 8);
+          tmem_ld8_nw(tpa + (cc - NP), x, 0);
+          tmem_ld8_nw(tpa + (cc - NP) + 8, x, 8);
           tmem_wait_ld_all(x);
 #pragma unroll
           for (int c4 = 0; c4 < 4; ++c4)
@@ -1078,11 +1084,10 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
                 make_float4(__uint_as_float(x[4 * c4]), __uint_as_float(x[4 * c4 + 1]),
                             __uint_as_float(x[4 * c4 + 2]), __uint_as_float(x[4 * c4 + 3]));
         }
-      } else {
-#pragma unroll
-        for (int cc = 0; cc < KP; cc += 4)
-          reinterpret_cast<float4 *>(dst + cc)[0] = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
       }
+#pragma unroll
+      for (int cc = 0; cc < NP; cc += 4)
+        reinterpret_cast<float4 *>(dst + cc)[0] = make_float4(p[cc], p[cc + 1], p[cc + 2], p[cc + 3]);
     }
 #pragma unroll
     for (int c = 0; c < NP; ++c) p[c] = 0.f;
@@ -1137,16 +1142,39 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     constexpr int NPART = 2 + (C::NL > 0 ? 1 : 0);
     constexpr int CW = (KP < C::FOLD_CW) ? KP : C::FOLD_CW;
     if constexpr (C::PTMEM) {
-      // PA = (pa_first ? 0 : PA) + this chain, 16 columns per round
+      // columns [0, NP): p += this chain, 16 columns per round
 #pragma unroll
-      for (int cc = 0; cc < KP; cc += 16) {
+      for (int cc = 0; cc < NP; cc += 16) {
+        uint32_t x[NPART * 16];
+#pragma unroll
+        for (int u = 0; u < 16; u += 8) {
+          tmem_ld8_nw(tb + cc + u, x, u);
+          tmem_ld8_nw(tb + KP + cc + u, x, 16 + u);
+          if constexpr (C::NL > 0) tmem_ld8_nw(tb + C::N + cc + u, x, 32 + u);
+        }
+        tmem_wait_ld_all(x);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float v;
+          if constexpr (C::F8) {
+            v = fmaf(__uint_as_float(x[16 + j]), 0.0625f, __uint_as_float(x[j])) * sc;
+          } else {
+            v = __uint_as_float(x[j]) + __uint_as_float(x[16 + j]);
+          }
+          if constexpr (C::NL > 0) v += __uint_as_float(x[32 + j]);
+          p[cc + j] += v;
+        }
+      }
+      // columns [NP, kp): PA = (pa_first ? 0 : PA) + this chain
+#pragma unroll
+      for (int cc = NP; cc < KP; cc += 16) {
         uint32_t x[(NPART + 1) * 16];
 #pragma unroll
         for (int u = 0; u < 16; u += 8) {
           tmem_ld8_nw(tb + cc + u, x, u);
           tmem_ld8_nw(tb + KP + cc + u, x, 16 + u);
           if constexpr (C::NL > 0) tmem_ld8_nw(tb + C::N + cc + u, x, 32 + u);
-          if (!pa_first) tmem_ld8_nw(tpa + cc + u, x, NPART * 16 + u);
+          if (!pa_first) tmem_ld8_nw(tpa + (cc - NP) + u, x, NPART * 16 + u);
         }
         tmem_wait_ld_all(x);
         uint32_t o[16];
@@ -1161,7 +1189,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
           if constexpr (C::NL > 0) v += __uint_as_float(x[32 + j]);
           o[j] = __float_as_uint(pa_first ? v : __uint_as_float(x[NPART * 16 + j]) + v);
         }
-        tmem_st16(tpa + cc, o);
+        tmem_st16(tpa + (cc - NP), o);
       }
       tmem_wait_st();
       pa_first = false;
