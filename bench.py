@@ -24,7 +24,8 @@ Further workloads, one JSON line each:
   --batch           64 instances x 4 restarts, BF16, Piecewise AdaGrad
   --kmeans          spherical K-means on the n=20000 TPDM matrix, K=32
   --dependence      the |corr| build of n=1e5 variables over 500 observations
-  --rolling         10 windows: GPU |corr| build + warm-started solves
+  --rolling         10 windows: fused GPU |corr| build + rebind, warm-started solves
+  --rolling-batch   4 series of uneven n, 6 windows each, through the batched path
 """
 from __future__ import annotations
 
@@ -973,15 +974,83 @@ def run_dependence(args):
     }
 
 
+def run_rolling_batch(args):
+    """Rolling windows of several series of uneven n through the batched
+    path: 4 series (n = 5000, 10000, 15000, 20000 variables of the 50-factor
+    model, k = 32), windows of T = 500 sliding by 100, 6 windows each.  Per
+    round every handle moves to its next window with symnmf_window_update
+    (fused GPU build of |corr| + rebind, H kept as the warm start), then
+    symnmf_batch_step runs 100 AdaGrad iterations on all handles, each on
+    its own stream, launching every handle's iterations before any check
+    waits.  Reported: aggregate windows/s."""
+    import numpy as np
+    import torch
+    import gen
+    from paper_2607_24518_gb300 import build
+    build.build()
+    from paper_2607_24518_gb300 import symnmf as L
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ns, k, T, stride, W, iters = [5000, 10000, 15000, 20000], 32, 500, 100, 6, 100
+    Tt = T + (W - 1) * stride
+    series = []
+    for i, n in enumerate(ns):
+        rng = np.random.default_rng(100 + i)
+        A = np.zeros((n, 50), dtype=np.float32)
+        A[:, 0] = rng.uniform(0.4, 0.8, size=n)
+        mask = rng.random((n, 49)) < 0.1
+        A[:, 1:] = np.where(mask, rng.uniform(0.0, 0.5, size=(n, 49)), 0.0)
+        Z = rng.standard_normal((Tt, 50)).astype(np.float32)
+        Y = torch.tensor(Z @ A.T, device=dev) + torch.randn(
+            Tt, n, device=dev, generator=torch.Generator(dev).manual_seed(100 + i))
+        S = torch.empty(n, n, dtype=torch.float32, device=dev)
+        st = torch.cuda.Stream(dev)
+        L.symnmf_build_dependence(Y[:T], T, n, n, 1, L.F32, S, n, None, 0, None, st)
+        h = L.symnmf_create(S, n, k, L.F32)
+        L.symnmf_set_stream(h, st)
+        L.symnmf_set_H(h, torch.tensor(gen.init_scaled(0.1, n, k, seed=i), dtype=torch.float32,
+                                       device=dev))
+        series.append((n, Y, S, h))
+    handles = [x[3] for x in series]
+    hps = [L.symnmf_hparams_default(L.ADAGRAD, eta=2.0, tau_g=1e-30) for _ in handles]
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    Es = []
+    for w in range(W):
+        if w > 0:
+            for n, Y, S, h in series:
+                L.symnmf_window_update(h, Y[w * stride:w * stride + T], T, n, 1, S, n)
+        L.symnmf_batch_step(handles, hps, iters)
+        Es.append([L.symnmf_get_trace(h)[-1].E for h in handles])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ck = clocks.stop()
+    for h in handles:
+        L.symnmf_destroy(h)
+    return {
+        "metric": "rolling windows of uneven n, batched: aggregate windows/s (GPU build of |corr| "
+                  "+ 100 warm-started AdaGrad iterations per window)",
+        "value": len(ns) * W / wall, "unit": "windows/s", "n_gpus": 1, "steps": W, "warmup": 0,
+        "ms_per_step": 1e3 * wall / W, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded 50-factor model streams)",
+        "config": {"workload": "rolling_batch_corr_n5k-20k_T500_stride100_k32", "ns": ns, "k": k,
+                   "T": T, "stride": stride, "windows_per_series": W,
+                   "iterations_per_window": iters, "handles": len(handles)},
+        "mean_E_last_window": float(np.mean(Es[-1])), "clocks": ck, "status": "ok"}
+
+
 def run_rolling(args):
     """Rolling windows (the paper's next step, Sec. 8): n = 20000 variables
     of the 50-factor model (as the n = 1e5 correlation workload), windows of
-    T = 500 observations sliding by 100, 10 windows.  Per window the
-    absolute correlation is built on the GPU (symnmf_build_dependence, FP32,
-    into the one S buffer the handle reads) and AdaGrad (eta 2) runs a fixed
-    100 iterations, warm-started from the previous window's H
-    (symnmf_set_matrix) or cold from H0.  Reported: windows/s warm (build +
-    solve), and the mean E after the 100 iterations, warm against cold."""
+    T = 500 observations sliding by 100, 10 windows.  Per window one call,
+    symnmf_window_update, builds the absolute correlation on the GPU (FP32,
+    into the one S buffer the handle reads) and rebinds the handle with
+    ||S||^2 from the build; AdaGrad (eta 2) then runs a fixed 100
+    iterations, warm-started from the previous window's H, or cold from H0.
+    Reported: windows/s warm (build + solve), and the mean E after the 100
+    iterations, warm against cold."""
     import numpy as np
     import torch
     import gen
@@ -1017,16 +1086,15 @@ def run_rolling(args):
         e0.record(stream)
         for w in range(W):
             Yw = Y[w * stride:w * stride + T]
-            L.symnmf_build_dependence(Yw, T, n, n, 1, L.F32, S, n, None, 0, None, stream)
             if h is None:
+                L.symnmf_build_dependence(Yw, T, n, n, 1, L.F32, S, n, None, 0, None, stream)
                 h = L.symnmf_create(S, n, k, L.F32)
                 L.symnmf_set_stream(h, stream)
                 L.symnmf_set_H(h, H0)
-            elif mode == "warm":
-                L.symnmf_set_matrix(h, S, n)
             else:
-                L.symnmf_set_matrix(h, S, n)
-                L.symnmf_set_H(h, H0)
+                L.symnmf_window_update(h, Yw, T, n, 1, S, n)
+                if mode == "cold":
+                    L.symnmf_set_H(h, H0)
             _, st = L.symnmf_step(h, hp, iters)
             Es.append(L.symnmf_get_trace(h)[-1].E)
         e1.record(stream)
@@ -1113,6 +1181,9 @@ def main():
                     help="one handle per restart even where 4 k <= 64")
     ap.add_argument("--tune-iters", dest="tune_iters", type=int, default=10)
     ap.add_argument("--batch-cap", dest="batch_cap", type=int, default=3000)
+    ap.add_argument("--rolling-batch", dest="rolling_batch", action="store_true",
+                    help="rolling windows of 4 series of uneven n through the batched path "
+                         "(own JSON line)")
     ap.add_argument("--rolling", action="store_true",
                     help="rolling windows: GPU |corr| build + warm-started solves (own JSON line)")
     ap.add_argument("--dependence", action="store_true",
@@ -1143,6 +1214,9 @@ def main():
         return
     if args.rolling:
         print(json.dumps(run_rolling(args)), flush=True)
+        return
+    if args.rolling_batch:
+        print(json.dumps(run_rolling_batch(args)), flush=True)
         return
     if args.impl == "reference":
         out = run_reference(args, rank)

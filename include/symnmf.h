@@ -405,6 +405,28 @@ int symnmf_build_dependence(const float *Y, int64_t T, int64_t n, int64_t ldy, i
                             int32_t out_dtype, void *S, int64_t lds, float *scales,
                             int64_t ld_scales, double *normS2, void *stream);
 
+/* The next window of a rolling solve (Sec. 8, streaming SymNMF over rolling
+ * windows; Sec. 3 for S) in one call on the handle's stream: the dependence
+ * matrix of the window Y (as symnmf_build_dependence, in the handle's
+ * storage type) is written into S, the handle is rebound to it (as
+ * symnmf_set_matrix: H kept as the warm start, the optimizer state,
+ * controller and trace fresh), and ||S||^2 is taken from the build's own
+ * epilogue rather than from a second pass over S (FP32 / BF16: the stored
+ * values' squares summed as float-float pairs over runs of 32 entries,
+ * about 2^-44 relative, and in FP64 across runs; with FP8 storage, whose
+ * build sums the values before quantisation, it is recomputed from the
+ * stored codes).  S may be the buffer the handle reads
+ * now: the build is ordered after the handle's earlier launches.  The
+ * next symnmf_step is the window's first solver step.
+ * Arguments: Y (device FP32, T x n, pitch ldy >= n, n the handle's), center
+ * (1: absolute correlation, 0: TPDM from exceedance angles), S (device, n x
+ * n, pitch lds >= n, the alignment symnmf_build_dependence asks for), FP8:
+ * scales / ld_scales as there, else NULL / 0.  Synchronises the handle's
+ * stream once.
+ * Errors: those of symnmf_build_dependence and symnmf_set_matrix. */
+int symnmf_window_update(symnmf_t h, const float *Y, int64_t T, int64_t ldy, int32_t center,
+                         void *S, int64_t lds, float *scales, int64_t ld_scales);
+
 /* ------------------------------------------------ spherical K-means */
 
 typedef struct {

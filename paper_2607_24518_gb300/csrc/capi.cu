@@ -970,12 +970,11 @@ int symnmf_get_restart_stats(symnmf_t h, int32_t count, double *E, double *kkt,
   return SYMNMF_OK;
 }
 
-int symnmf_set_matrix(symnmf_t h, const void *S, int64_t lds, const float *scales,
-                      int64_t ld_scales) {
-  if (!h || !S || lds < h->n) return SYMNMF_ERR_INVALID;
-  if (h->dtype == SYMNMF_FP8E4M3 && (!scales || ld_scales < h->ntiles)) return SYMNMF_ERR_INVALID;
-  // every launch that reads the old matrix has finished
-  CK(cudaStreamSynchronize(h->stream));
+// Rebind h to S (stream-ordered; the caller has validated the arguments):
+// H stays as the warm start, the rest of the solver state starts afresh.
+// ||S||^2 is left to the caller.
+static int rebind_matrix(symnmf_t h, const void *S, int64_t lds, const float *scales,
+                         int64_t ld_scales) {
   h->S = S;
   h->lds = lds;
   h->tc_layout_ok = ((uintptr_t)S % 16 == 0) && ((lds * (int64_t)esize(h->dtype)) % 16 == 0);
@@ -1001,7 +1000,56 @@ int symnmf_set_matrix(symnmf_t h, const void *S, int64_t lds, const float *scale
     CK(launch_row_norms(h->S, h->n, h->lds, h->dtype, h->scales, h->ld_scales, h->km_rn,
                         h->stream));
   }
+  return SYMNMF_OK;
+}
+
+int symnmf_set_matrix(symnmf_t h, const void *S, int64_t lds, const float *scales,
+                      int64_t ld_scales) {
+  if (!h || !S || lds < h->n) return SYMNMF_ERR_INVALID;
+  if (h->dtype == SYMNMF_FP8E4M3 && (!scales || ld_scales < h->ntiles)) return SYMNMF_ERR_INVALID;
+  // every launch that reads the old matrix has finished
+  CK(cudaStreamSynchronize(h->stream));
+  int rc = rebind_matrix(h, S, lds, scales, ld_scales);
+  if (rc) return rc;
   return compute_norm(h);
+}
+
+int symnmf_window_update(symnmf_t h, const float *Y, int64_t T, int64_t ldy, int32_t center,
+                         void *S, int64_t lds, float *scales, int64_t ld_scales) {
+  if (!h || !Y || !S || T < 1 || ldy < h->n || lds < h->n) return SYMNMF_ERR_INVALID;
+  if (center && T < 2) return SYMNMF_ERR_INVALID;
+  const int64_t es = esize(h->dtype);
+  if ((lds * es) % 16 != 0 || reinterpret_cast<uintptr_t>(S) % 16 != 0) return SYMNMF_ERR_INVALID;
+  const bool f8 = (h->dtype == SYMNMF_FP8E4M3);
+  if (f8 && (!scales || ld_scales < h->ntiles)) return SYMNMF_ERR_INVALID;
+  if (h->n > 2097120 || T > (int64_t)1 << 30) return SYMNMF_ERR_UNSUPPORTED;
+  CK(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
+  // the build, ordered after every launch that reads the old matrix; it
+  // leaves ||S||^2 of the stored values in dsum (F32 / BF16)
+  const int dt = h->dtype == SYMNMF_F32 ? 0 : h->dtype == SYMNMF_BF16 ? 1 : 2;
+  cudaError_t e = launch_dependence(Y, T, h->n, ldy, center ? 1 : 0, dt, S, lds, scales,
+                                    ld_scales, f8 ? nullptr : h->dsum, h->dev_err, h->stream,
+                                    true);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(h, SYMNMF_ERR_OOM, "dependence build scratch");
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "dependence build");
+  CK(cudaMemcpyAsync(h->host_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  int rc = rebind_matrix(h, S, lds, scales, ld_scales);
+  if (rc) return rc;
+  if (f8) {
+    rc = compute_norm(h);  // synchronises the stream
+    if (rc) return rc;
+  } else {
+    CK(cudaMemcpyAsync(h->hsum, h->dsum, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->normS2 = h->hsum[0];
+  }
+  if (h->host_err[0] != 0)
+    return fail(h, SYMNMF_ERR_TIMEOUT,
+                "a bounded device wait gave up (code " + std::to_string(h->host_err[0]) + ")");
+  return SYMNMF_OK;
 }
 
 int symnmf_set_restarts(symnmf_t h, int32_t restarts) {

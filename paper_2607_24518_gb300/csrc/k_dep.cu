@@ -114,6 +114,7 @@ struct DepArgs {
   int64_t ld_scales;
   double *sq;       // per CTA
   int *err;
+  int exact_sq;     // F32 / BF16: run sums of squares as float-float pairs
 };
 
 __device__ __forceinline__ void dep_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
@@ -369,15 +370,33 @@ __global__ void __launch_bounds__(kDepThreads, 1)
           for (int u = 0; u < 4; ++u) tmem_ld8_nw(trow + c0 + 8 * u, x, 8 * u);
           tmem_wait_ld_all(x);
           float v[32];
-          float part = 0.f;
+          float ph = 0.f, pl = 0.f;
 #pragma unroll
           for (int u = 0; u < 32; ++u) {
             float s = sval(x[u], c0 + u);
             if (a.out == 1) s = __bfloat162float(__float2bfloat16_rn(s));
             v[u] = s;
-            part = fmaf(wgt(md, c0 + u) * s, s, part);
           }
-          sq += (double)part;
+          if (a.exact_sq) {
+            // the stored values' squares summed as a float-float pair
+            // (products split exactly by an FMA, Knuth's TwoSum on the high
+            // parts): the run's sum is exact to about 2^-44 before it joins
+            // the FP64 total, so ||S||^2 from here stands in for a pass over
+            // the stored matrix
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+              const float ws = wgt(md, c0 + u) * v[u];  // weight 0, 1 or 2: exact
+              const float pr = __fmul_rn(ws, v[u]), pe = fmaf(ws, v[u], -pr);
+              const float t = __fadd_rn(ph, pr), bv = __fsub_rn(t, ph);
+              pl = __fadd_rn(pl, __fadd_rn(__fadd_rn(__fsub_rn(ph, __fsub_rn(t, bv)),
+                                                     __fsub_rn(pr, bv)), pe));
+              ph = t;
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < 32; ++u) ph = fmaf(wgt(md, c0 + u) * v[u], v[u], ph);
+          }
+          sq += (double)ph + (double)pl;
           if (!vrow) continue;
           const bool whole = md == 2 && j0 + c0 + 32 <= a.n;
           if (a.out == 0) {
@@ -469,7 +488,7 @@ __global__ void __launch_bounds__(256) dep_sum_kernel(const double *x, int64_t m
 
 cudaError_t launch_dependence(const float *Y, int64_t T, int64_t n, int64_t ldy, int center,
                               int out, void *S, int64_t lds, float *scales, int64_t ld_scales,
-                              double *normS2, int *err, cudaStream_t s) {
+                              double *normS2, int *err, cudaStream_t s, bool exact_norm) {
   const int Tp = (int)((T + 31) / 32 * 32);
   const int nib = (int)((n + 127) / 128), njb = (int)((n + 255) / 256);
   if (nib >= 65536 || njb >= 65536) return cudaErrorInvalidValue;
@@ -527,6 +546,7 @@ cudaError_t launch_dependence(const float *Y, int64_t T, int64_t n, int64_t ldy,
       a.ld_scales = ld_scales;
       a.sq = sq;
       a.err = err;
+      a.exact_sq = exact_norm ? 1 : 0;
       dep_gemm_kernel<<<(unsigned)G, kDepThreads, kDepSmem, s>>>(mP, a);
       if (normS2) dep_sum_kernel<<<1, 256, 0, s>>>(sq, G, normS2);
       e = cudaGetLastError();

@@ -198,7 +198,8 @@ cudaError_t launch_sum_slot(const double *slots, int ntiles, int which, double *
 // device int the kernels set on a bounded-wait timeout
 cudaError_t launch_dependence(const float *Y, int64_t T, int64_t n, int64_t ldy, int center,
                               int out, void *S, int64_t lds, float *scales, int64_t ld_scales,
-                              double *normS2, int *err, cudaStream_t s);
+                              double *normS2, int *err, cudaStream_t s,
+                              bool exact_norm = false);
 
 // Spherical K-means (Sec. 6): the kernels around the two product passes of
 // one Lloyd iteration (k_kmeans.cu)

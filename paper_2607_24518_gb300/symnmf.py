@@ -116,6 +116,7 @@ def _load():
         "symnmf_sample_blocks": [u64, i64, i32, i64, i64, P(i64)],
         "symnmf_controller_check": [P(symnmf_ctrl), P(symnmf_hparams), i64, i64, dbl, dbl, dbl,
                                     dbl, P(i32), P(dbl)],
+        "symnmf_window_update": [vp, vp, i64, i64, i32, vp, i64, vp, i64],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -142,7 +143,7 @@ DECLARED = [
     "symnmf_controller_check", "symnmf_objective_noalloc", "symnmf_objective_noalloc_check",
     "symnmf_spkmeans",
     "symnmf_build_dependence", "symnmf_set_matrix", "symnmf_set_restarts",
-    "symnmf_get_restart_stats", "symnmf_selftest_wait_timeout",
+    "symnmf_get_restart_stats", "symnmf_selftest_wait_timeout", "symnmf_window_update",
 ]
 
 NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -268,6 +269,14 @@ def symnmf_get_restart_stats(h, count):
 def symnmf_set_matrix(h, S, lds, scales=None, ld_scales=0):
     """Rebind the handle to another S of the same n (warm start: H kept)."""
     return _check(LIB.symnmf_set_matrix(h, _ptr(S), lds, _ptr(scales), ld_scales), h)
+
+
+def symnmf_window_update(h, Y, T, ldy, center, S, lds, scales=None, ld_scales=0):
+    """Next rolling window in one call: build the window's dependence matrix
+    into S (the handle's storage type), rebind the handle to it with H as
+    the warm start and ||S||^2 from the build."""
+    return _check(LIB.symnmf_window_update(h, _ptr(Y), T, ldy, int(center), _ptr(S), lds,
+                                           _ptr(scales), ld_scales), h)
 
 
 def symnmf_set_norm(h, normS2):

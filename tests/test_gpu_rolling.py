@@ -145,3 +145,76 @@ def test_set_matrix_fp8_takes_the_new_scales(L):
     finally:
         L.symnmf_destroy(h)
         L.symnmf_destroy(h2)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_window_update_matches_the_oracles(L, storage):
+    """symnmf_window_update builds the next window's |corr| into the buffer
+    the handle reads, rebinds it with H kept and ||S||^2 from the build:
+    S matches the dependence oracle (Sec. 3) within the build's bound, the
+    norm is that of the stored matrix, and the warm-started window's E
+    trajectory and final H match the solver oracle run from the same warm
+    start on the same stored S (Sec. 8)."""
+    from oracle import dependence_oracle as D
+    n, k, T, stride, iters = 640, 8, 300, 40, 60
+    Tp = (T + 31) // 32 * 32
+    tolS = 2.0 ** -21 + 4.0 * (3 * Tp / 8) * 2.0 ** -24
+    Y = _window_stream(n, T, 2, stride, seed=5)
+    code, dt = {"f32": (L.F32, torch.float32), "bf16": (L.BF16, torch.bfloat16)}[storage]
+    S = torch.empty(n, n, dtype=dt, device=DEV)
+    L.symnmf_build_dependence(torch.tensor(Y[:T], device=DEV), T, n, n, 1, code, S, n)
+    H0 = np.random.default_rng(6).uniform(0.0, 0.1, size=(n, k)).astype(np.float32)
+    hp = L.symnmf_hparams_default(L.ADAGRAD, eta=0.1)
+    h = L.symnmf_create(S, n, k, code)
+    try:
+        L.symnmf_set_H(h, torch.tensor(H0, device=DEV))
+        L.symnmf_step(h, hp, iters)
+        Hw = torch.empty(n, k, device=DEV)
+        L.symnmf_get_H(h, Hw)
+        Y2 = torch.tensor(Y[stride:stride + T], device=DEV)
+        L.symnmf_window_update(h, Y2, T, n, 1, S, n)
+        nrm = L.symnmf_get_norm(h)
+        S2 = S.double().cpu().numpy()
+        L.symnmf_step(h, hp, iters)
+        tr = L.symnmf_get_trace(h)
+        Hg = torch.empty(n, k, device=DEV)
+        L.symnmf_get_H(h, Hg)
+        torch.cuda.synchronize()
+    finally:
+        L.symnmf_destroy(h)
+    ref = D.dependence(Y[stride:stride + T].astype(np.float64), True)
+    if storage == "f32":
+        assert np.max(np.abs(S2 - ref)) <= tolS
+    else:
+        lo = torch.tensor(ref - tolS).to(torch.bfloat16).double().numpy()
+        hi = torch.tensor(ref + tolS).to(torch.bfloat16).double().numpy()
+        assert np.all((S2 >= np.minimum(lo, hi)) & (S2 <= np.maximum(lo, hi)))
+    assert abs(nrm - float(np.sum(S2 * S2))) <= 1e-10 * nrm  # float-float runs, FP64 across
+    ohp = O.HParams.paper(O.ADAGRAD)
+    ohp.eta = 0.1
+    s = O.Solver(S2, Hw.double().cpu().numpy(), ohp)
+    s.run(iters)
+    assert len(tr) == iters and tr[0].t == 0
+    Eg = np.array([r.E for r in tr])
+    Er = np.array([r.E for r in s.records])
+    # E = 1 - (2 tr - ||H^T H||^2) / ||S||^2 carries twice the relative
+    # error of tr, and the FP32 S H products carry up to 2^-20 of it (three
+    # tf32 products, the dropped S_lo H_lo term); tr <= ||S||^2 from a warm
+    # start near the previous window's solution
+    assert np.max(np.abs(Eg - Er)) < 2.0 ** -19
+    assert O.rel_err(Hg.double().cpu().numpy(), s.H) < 1e-4
+
+
+def test_window_update_invalid(L):
+    n, k, T = 256, 4, 50
+    S = torch.eye(n, device=DEV)
+    Y = torch.zeros(T, n, device=DEV)
+    h = L.symnmf_create(S, n, k, L.F32)
+    try:
+        for args in ((None, T, n, 1, S, n), (Y, 1, n, 1, S, n), (Y, T, n - 1, 1, S, n),
+                     (Y, T, n, 1, None, n), (Y, T, n, 1, S, n - 1)):
+            with pytest.raises(L.SymNMFError) as e:
+                L.symnmf_window_update(h, *args)
+            assert e.value.status == L.ERR_INVALID
+    finally:
+        L.symnmf_destroy(h)
