@@ -24,6 +24,7 @@ using namespace symnmf;
 namespace {
 
 constexpr int kStages = 8;          // pinned/device staging slots for sampled lists
+constexpr int kListArrays = 9;      // ntiles-long int arrays per staging slot
 constexpr size_t kTraceCap = 1u << 20;
 constexpr uint64_t kMagic = 0x31764D4E4D59534EULL;  // "NSYMNMv1"
 
@@ -55,13 +56,13 @@ struct symnmf_ctx {
   float *gram32[2] = {nullptr, nullptr};
   int cur = 0;
   float *A = nullptr, *M = nullptr, *mu = nullptr, *g = nullptr, *tmp = nullptr;
-  float *P = nullptr, *Q = nullptr;
+  float *P = nullptr, *Q = nullptr, *R = nullptr;  // product partials
   int64_t pq_cap_tiles = 0;
   double *slots = nullptr, *chunk = nullptr;
   int nchunks = 1;
   float *gramI = nullptr, *gramJ = nullptr;
   float *minv = nullptr;    // ADMM: (2 Gram_t + rho I)^-1
-  int *dlists = nullptr;    // kStages x 4 x ntiles
+  int *dlists = nullptr;    // kStages x kListArrays x ntiles
   int *hlists = nullptr;    // pinned mirror
   cudaEvent_t stage_ev[kStages] = {};
   bool stage_used[kStages] = {};
@@ -162,7 +163,7 @@ void free_all(symnmf_t h) {
     cudaFree(h->gram32[i]);
   }
   for (void *p : {(void *)h->A, (void *)h->M, (void *)h->mu, (void *)h->g, (void *)h->tmp,
-                  (void *)h->P, (void *)h->Q, (void *)h->slots, (void *)h->chunk,
+                  (void *)h->P, (void *)h->Q, (void *)h->R, (void *)h->slots, (void *)h->chunk,
                   (void *)h->gramI, (void *)h->gramJ, (void *)h->minv, (void *)h->dlists, (void *)h->ring,
                   (void *)h->hist, (void *)h->sel, (void *)h->dmed, (void *)h->dsum,
                   (void *)h->norm_parts, (void *)h->dev_err, (void *)h->counters, (void *)h->tile_cnt,
@@ -338,14 +339,15 @@ int validate_hp(const symnmf_hparams *hp) {
 int stage_slot(symnmf_t h, int64_t t, int **hl, int **dl) {
   const int s = (int)(t % kStages);
   if (h->stage_used[s]) CK(cudaEventSynchronize(h->stage_ev[s]));
-  *hl = h->hlists + (size_t)s * 4 * h->ntiles;
-  *dl = h->dlists + (size_t)s * 4 * h->ntiles;
+  *hl = h->hlists + (size_t)s * kListArrays * h->ntiles;
+  *dl = h->dlists + (size_t)s * kListArrays * h->ntiles;
   return SYMNMF_OK;
 }
 
 int upload_slot(symnmf_t h, int64_t t, int *hl, int *dl) {
   const int s = (int)(t % kStages);
-  CK(cudaMemcpyAsync(dl, hl, sizeof(int) * 4 * h->ntiles, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(dl, hl, sizeof(int) * kListArrays * h->ntiles, cudaMemcpyHostToDevice,
+                      h->stream));
   CK(cudaEventRecord(h->stage_ev[s], h->stream));
   h->stage_used[s] = true;
   return SYMNMF_OK;
@@ -492,12 +494,13 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t, bool need_g) 
   } else {
     int *hl, *dl;
     if ((rc = stage_slot(h, t, &hl, &dl))) return rc;
-    int *hI = hl, *hJ = hl + h->ntiles, *hposI = hl + 2 * h->ntiles, *hposJ = hl + 3 * h->ntiles;
+    const int nt = h->ntiles;
+    int *hI = hl, *hJ = hl + nt, *hposI = hl + 2 * nt, *hposJ = hl + 3 * nt;
     const int64_t br = hp->block_rows;
     const int64_t nb = (h->n + br - 1) / br;
     std::vector<int64_t> bI, bJ;
     std::vector<int> tI, tJ;
-    for (int i = 0; i < h->ntiles; ++i) hposI[i] = hposJ[i] = -1;
+    for (int i = 0; i < nt; ++i) hposI[i] = hposJ[i] = -1;
     if (hp->method == SYMNMF_ROW_SVRG) {
       sample(hp->seed, t, 0, nb, sample_count(hp->row_frac, h->n, br), bI);
     } else {
@@ -515,8 +518,33 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t, bool need_g) 
       hJ[i] = tJ[i];
       hposJ[tJ[i]] = (int)i;
     }
+    // Block-SVRG: the rows of I need S_IJ, the rows of J need S_JI, and S
+    // is symmetric, so every tile position is read once.  With K = I n J
+    // the positions split into (I u J) x K, I x (J \ I) and J x (I \ J):
+    // alpha, beta and gamma.  S_IJ H_J = alpha + beta on the rows of I and
+    // S_JI H_I = alpha + gamma on the rows of J.
+    int *hU = hl + 4 * nt, *hposU = hl + 5 * nt, *hK = hl + 6 * nt, *hJmI = hl + 7 * nt,
+        *hImJ = hl + 8 * nt;
+    int nU = 0, nK = 0, nJmI = 0, nImJ = 0;
+    if (hp->method == SYMNMF_BLOCK_SVRG_ADAPTGROW) {
+      for (int i = 0; i < nt; ++i) hposU[i] = -1;
+      for (int x : tI) {
+        hposU[x] = nU;
+        hU[nU++] = x;
+        if (hposJ[x] >= 0) hK[nK++] = x;
+        else hImJ[nImJ++] = x;
+      }
+      for (int x : tJ)
+        if (hposI[x] < 0) {
+          hposU[x] = nU;
+          hU[nU++] = x;
+          hJmI[nJmI++] = x;
+        }
+    }
     if ((rc = upload_slot(h, t, hl, dl))) return rc;
-    int *dI = dl, *dJ = dl + h->ntiles, *dposI = dl + 2 * h->ntiles, *dposJ = dl + 3 * h->ntiles;
+    int *dI = dl, *dJ = dl + nt, *dposI = dl + 2 * nt, *dposJ = dl + 3 * nt;
+    int *dU = dl + 4 * nt, *dposU = dl + 5 * nt, *dK = dl + 6 * nt, *dJmI = dl + 7 * nt,
+        *dImJ = dl + 8 * nt;
     if (hp->method == SYMNMF_ROW_SVRG) {
       PartLayout ly;
       if ((rc = prod(h, dI, (int)tI.size(), nullptr, h->ntiles, h->P, &ly))) return rc;
@@ -533,9 +561,11 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t, bool need_g) 
                             h->gramI, h->gramJ, h->restarts > 1 ? h->k / h->restarts : 0,
                             h->stream));
       count_kernels(h, 1);
-      PartLayout l1, l2;
-      if ((rc = prod(h, dI, (int)tI.size(), dJ, (int)tJ.size(), h->P, &l1))) return rc;
-      if ((rc = prod(h, dJ, (int)tJ.size(), dI, (int)tI.size(), h->Q, &l2))) return rc;
+      // an empty list contributes zero (ncols = 0 in the layout)
+      PartLayout l1{}, l2{}, l3{};
+      if (nJmI > 0 && (rc = prod(h, dI, (int)tI.size(), dJmI, nJmI, h->P, &l1))) return rc;
+      if (nImJ > 0 && (rc = prod(h, dJ, (int)tJ.size(), dImJ, nImJ, h->Q, &l2))) return rc;
+      if (nK > 0 && (rc = prod(h, dU, nU, dK, nK, h->R, &l3))) return rc;
       e.mode = MODE_BLOCK;
       e.coef = 2.f;
       e.gramI = h->gramI;
@@ -552,6 +582,12 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t, bool need_g) 
       e.ncols2 = l2.ncols;
       e.pos2 = dposJ;
       e.n2 = (int)tJ.size();
+      e.R = h->R;
+      e.nsplit3 = l3.nsplit;
+      e.skG3 = l3.skG;
+      e.ncols3 = l3.ncols;
+      e.pos3 = dposU;
+      e.n3 = nU;
     }
   }
   if (!fused_done) CK(launch_epilogue(e, h->stream));
@@ -877,12 +913,13 @@ int symnmf_create_ld(const void *S, int64_t n, int64_t lds, int32_t k, int32_t d
   if (e == cudaSuccess) e = dalloc(&h->tmp, nkp);
   if (e == cudaSuccess) e = dalloc(&h->P, (size_t)h->pq_cap_tiles * kTileRows * h->kp);
   if (e == cudaSuccess) e = dalloc(&h->Q, (size_t)h->pq_cap_tiles * kTileRows * h->kp);
+  if (e == cudaSuccess) e = dalloc(&h->R, (size_t)h->pq_cap_tiles * kTileRows * h->kp);
   if (e == cudaSuccess) e = dalloc(&h->slots, (size_t)h->ntiles * kSlotStride);
   if (e == cudaSuccess) e = dalloc(&h->chunk, (size_t)h->nchunks * (4 + h->kp * h->kp));
   if (e == cudaSuccess) e = dalloc(&h->gramI, (size_t)h->kp * h->kp);
   if (e == cudaSuccess) e = dalloc(&h->gramJ, (size_t)h->kp * h->kp);
   if (e == cudaSuccess) e = dalloc(&h->minv, (size_t)h->kp * h->kp);
-  if (e == cudaSuccess) e = dalloc(&h->dlists, (size_t)kStages * 4 * h->ntiles);
+  if (e == cudaSuccess) e = dalloc(&h->dlists, (size_t)kStages * kListArrays * h->ntiles);
   if (e == cudaSuccess) e = dalloc(&h->ring, (size_t)kRing + 1);
   if (e == cudaSuccess) e = dalloc(&h->hist, 2048);
   if (e == cudaSuccess) e = dalloc(&h->sel, 4);
@@ -895,7 +932,7 @@ int symnmf_create_ld(const void *S, int64_t n, int64_t lds, int32_t k, int32_t d
   if (e == cudaSuccess) e = dalloc(&h->tile_cnt, (size_t)h->ntiles);
   if (e == cudaSuccess) e = dalloc(&h->lvl1, (size_t)h->ntc * (4 + h->kp * h->kp));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_err, sizeof(int) * 4);
-  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hlists, sizeof(int) * kStages * 4 * h->ntiles);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hlists, sizeof(int) * kStages * kListArrays * h->ntiles);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hring, sizeof(DevRecord) * (kRing + 1));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hsum, sizeof(double) * 4);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hmed, sizeof(float) * 4);

@@ -127,23 +127,35 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(EpiArgs a) {
     G1[e / KP][e % KP] = g1src[e];
     if (block) G2[e / KP][e % KP] = a.gramI[e];
   }
-  int p1 = -1, p2 = -1;
+  int p1 = -1, p2 = -1, p3 = -1;
   if (a.mode == MODE_FULL || a.mode == MODE_GRAD_ONLY) {
     p1 = tile;
   } else {
     p1 = a.pos1[tile];
-    if (block) p2 = a.pos2[tile];
+    if (block) {
+      p2 = a.pos2[tile];
+      p3 = a.pos3[tile];
+    }
   }
-  int64_t b10 = 0, b11 = 0, b20 = 0, b21 = 0;
-  if (p1 >= 0 && a.skG1 > 0) {
+  // block mode: a list whose column list was empty holds no partials
+  const bool has1 = p1 >= 0 && (!block || a.ncols1 > 0);
+  const bool has2 = p2 >= 0 && a.ncols2 > 0;
+  const bool has3 = p3 >= 0 && a.ncols3 > 0;
+  int64_t b10 = 0, b11 = 0, b20 = 0, b21 = 0, b30 = 0, b31 = 0;
+  if (has1 && a.skG1 > 0) {
     const int64_t W = (int64_t)a.n1 * a.ncols1;
     b10 = sk_cta((int64_t)p1 * a.ncols1, W, a.skG1);
     b11 = sk_cta((int64_t)p1 * a.ncols1 + a.ncols1 - 1, W, a.skG1);
   }
-  if (p2 >= 0 && a.skG2 > 0) {
+  if (has2 && a.skG2 > 0) {
     const int64_t W = (int64_t)a.n2 * a.ncols2;
     b20 = sk_cta((int64_t)p2 * a.ncols2, W, a.skG2);
     b21 = sk_cta((int64_t)p2 * a.ncols2 + a.ncols2 - 1, W, a.skG2);
+  }
+  if (has3 && a.skG3 > 0) {
+    const int64_t W = (int64_t)a.n3 * a.ncols3;
+    b30 = sk_cta((int64_t)p3 * a.ncols3, W, a.skG3);
+    b31 = sk_cta((int64_t)p3 * a.ncols3 + a.ncols3 - 1, W, a.skG3);
   }
 
   // phase 1: issue every global load of this thread's elements
@@ -156,12 +168,17 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(EpiArgs a) {
     const int r = e / KP, c = e % KP;
     const bool valid = (r < rows) && (c < a.k);
     const int64_t gi = (r0 + r) * KP + c;
-    pv[i] = (valid && p1 >= 0)
+    pv[i] = (valid && has1)
                 ? part_sum<KP>(a.P, a.nsplit, a.skG1, a.ncols1, a.n1, p1, r, c, b10, b11)
                 : 0.f;
-    qv[i] = (valid && p2 >= 0)
+    qv[i] = (valid && has2)
                 ? part_sum<KP>(a.Q, a.nsplit2, a.skG2, a.ncols2, a.n2, p2, r, c, b20, b21)
                 : 0.f;
+    if (valid && has3) {
+      const float rv = part_sum<KP>(a.R, a.nsplit3, a.skG3, a.ncols3, a.n3, p3, r, c, b30, b31);
+      pv[i] = (p1 >= 0) ? rv + pv[i] : 0.f;
+      qv[i] = (p2 >= 0) ? rv + qv[i] : 0.f;
+    }
     uv[i] = (valid && p1 < 0 && p2 < 0) ? a.mu[gi] : 0.f;
     av[i] = (valid && a.update) ? a.A[gi] : 0.f;
     mv[i] = (valid && a.update && rms) ? a.M[gi] : 0.f;

@@ -108,14 +108,22 @@ struct EpiArgs {
   const float *gramJ;    // block mode: H_J^T H_J
   const float *P;        // product partials for rows in list 1
   int nsplit;
-  int skG1, ncols1;      // stream-K layout of P (skG1 > 0)
+  int skG1, ncols1;      // stream-K layout of P (skG1 > 0); block mode: ncols1 = 0, no P
   const int *pos1;       // tile -> position in list 1 (or -1); nullptr in full mode
   int n1;                // length of list 1
-  const float *Q;        // block mode: partials of S_{J,I} H_I, list 2 = J
+  // block mode: list 1 = I, P = S_{I, J\I} H_{J\I}; list 2 = J,
+  // Q = S_{J, I\J} H_{I\J}; list 3 = I u J, R = S_{IuJ, K} H_K with K = I n J.
+  // S_IJ H_J = P + R on the rows of I, S_JI H_I = Q + R on the rows of J.
+  const float *Q;
   int nsplit2;
   int skG2, ncols2;
   const int *pos2;
   int n2;
+  const float *R;
+  int nsplit3;
+  int skG3, ncols3;
+  const int *pos3;
+  int n3;
   float coef;            // 4 (full/rows) or 2 (block)
   double *slots;         // per tile: [tr, kkt2, sumA, nonfinite]
   float *gram_part;      // per tile kp x kp partial of H_{t+1}^T H_{t+1} (nullptr: skip)

@@ -177,6 +177,47 @@ def test_teacher_forced_single_step(L, method, t0):
         assert eg < REL_FP32, eg
 
 
+def _block_lists(n, br, phi, t, seed):
+    nb = -(-n // br)
+    m = O.sample_count(np.sqrt(phi), n, br)
+    return set(O.sample_blocks(seed, t, 1, nb, m)), set(O.sample_blocks(seed, t, 2, nb, m))
+
+
+@pytest.mark.parametrize("case", ["disjoint", "equal", "overlap"])
+@pytest.mark.parametrize("n,k,br,phi", [(700, 8, 128, 0.3), (1100, 16, 256, 0.15)])
+def test_block_svrg_list_cases(L, case, n, k, br, phi):
+    """Block-SVRG reads each sampled tile position once: (I u J) x K, I x
+    (J \\ I) and J x (I \\ J) with K = I n J.  Seeds are picked with the
+    oracle's sampler so that the step's I and J are disjoint (K empty),
+    equal (only the K part) or overlap partly; one teacher-forced step is
+    compared with the oracle."""
+    t0 = 7
+    for seed in range(5000):
+        I, J = _block_lists(n, br, phi, t0, seed)
+        kind = "disjoint" if not (I & J) else "equal" if I == J else "overlap"
+        if kind == case:
+            break
+    else:
+        pytest.fail("no seed gives case " + case)
+    S_t, S64, H0_t, H64 = problem(n, k, seed=12)
+    hp = O.HParams.paper(O.BLOCK_SVRG)
+    hp.eta, hp.snapshot_period, hp.phi0, hp.block_rows, hp.seed = 0.05, 3, phi, br, seed
+    s = _rounded(_teacher_state(O.BLOCK_SVRG, S64, H64, t0, hp))
+    assert s.ctrl.t == t0 and not s.is_full(t0)
+    with Handle(L, S_t, n, k, L.F32) as hd:
+        _load_state(L, hd, s)
+        lhp = L.symnmf_hparams_default(O.BLOCK_SVRG, eta=hp.eta, snapshot_period=3, phi0=phi,
+                                       block_rows=br, seed=seed)
+        L.symnmf_step(hd.h, lhp, 1)
+        H_t = s.H.copy()
+        s.step()
+        for which, ref in [(None, s.H), (L.BUF_ACC, s.A), (L.BUF_SNAPSHOT, s.mu)]:
+            got = hd.get(which)
+            assert O.rel_err(got, ref) < REL_FP32, (which, O.rel_err(got, ref))
+        eg = grad_err(hd.get(L.BUF_GRAD), s.g, S64, H_t)
+        assert eg < REL_FP32, eg
+
+
 def test_free_running_adagrad_n512(L):
     """The n=512, k=8 planted correlation workload: 500 AdaGrad iterations
     from H0 ~ U[0, 0.1] (seed 0), eta = 2.0 and 0.1, against the oracle."""
