@@ -342,11 +342,17 @@ int symnmf_objective_noalloc_check(int64_t n, int64_t lds, int32_t dtype, int32_
  * every check each restart also gets its own E_r and KKT measure (from the
  * gradient the step wrote: f_r = ||S||^2 - ||Gram_rr||^2 + sum(H_r .* g_r) / 2)
  * and its own AND rule (Eq. 11); the handle stops (SYMNMF_CONVERGED) when
- * the concatenated problem or any restart meets it, with H_t kept.  The
- * Piecewise reset's median is taken over all blocks together.  Call before
- * stepping; the current H's Gram is recomputed.  Default 1.  The per-restart
- * check state (each restart's E0 and previous E) is not part of the
- * checkpoint blob: after symnmf_set_state it starts again at the next check.
+ * the concatenated problem or any restart meets it, with H_t kept.
+ * Piecewise AdaGrad resets each restart on its own (appendix, Family 3): at
+ * a check the restart's stagnation, KKT gate, loss-reduction test and
+ * cooldown use its E_r, KKT measure and sum(A_r), the median is that of
+ * g_r^2 over its n k/R entries, and only its columns of A are reset (the
+ * handle's own controller makes no reset; the record's reset flag says
+ * whether any restart reset).  No restart resets at a check where the handle
+ * stops.  Call before stepping; the current H's Gram is recomputed.
+ * Default 1.  The per-restart check state (each restart's E0, previous E
+ * and reset state) is not part of the checkpoint blob: after
+ * symnmf_set_state it starts again at the next check.
  * Errors: INVALID for restarts < 1 or > 8 or k not divisible by restarts;
  * OOM when the check scratch cannot be allocated. */
 int symnmf_set_restarts(symnmf_t h, int32_t restarts);
@@ -355,6 +361,13 @@ int symnmf_set_restarts(symnmf_t h, int32_t restarts);
  * the handle's own. */
 int symnmf_get_restart_stats(symnmf_t h, int32_t count, double *E, double *kkt,
                              int32_t *converged);
+/* Piecewise AdaGrad reset state of each restart (host arrays of count >=
+ * restarts entries, any may be NULL): resets fired, resets still enabled,
+ * cooldown running, sum(A_r) right after its last reset; with one restart
+ * the handle's own controller.  Errors: INVALID for a null handle or
+ * count < restarts. */
+int symnmf_get_restart_ctrl(symnmf_t h, int32_t count, int32_t *resets, int32_t *resets_enabled,
+                            int32_t *cooldown, double *sumA_post);
 
 /* Rolling windows: rebind the handle to another matrix S of the same n and
  * storage type (device, row pitch lds >= n; FP8 also takes its tile scales,

@@ -100,6 +100,10 @@ struct symnmf_ctx {
   struct RestartCtl {
     double E0 = NAN, E_prev = NAN;
     bool have_prev = false;
+    // Piecewise AdaGrad's reset state, per restart
+    bool cooldown = false, resets_enabled = true;
+    int resets = 0;
+    double E_at_reset = NAN, sumA_post = 0.0;
   };
   std::vector<RestartCtl> rctl;
   std::vector<double> rE, rkkt;
@@ -654,8 +658,10 @@ int sync_records(symnmf_t h, int64_t upto, const std::vector<double> &phis) {
   return finish_records(h, upto, phis);
 }
 
-int median_g2(symnmf_t h, double *out) {
-  CK(launch_median_g2(h->g, h->n, h->k, h->kp, h->hist, h->sel, h->dmed, h->stream));
+// lower median of g^2 over columns c0 .. c0 + kw - 1 (left on the device
+// in dmed for reset_columns)
+int median_g2(symnmf_t h, int c0, int kw, double *out) {
+  CK(launch_median_g2(h->g, h->n, c0, kw, h->kp, h->hist, h->sel, h->dmed, h->stream));
   count_kernels(h, 7);  // selection init + 3 x (histogram, select)
   CK(cudaMemcpyAsync(h->hmed, h->dmed, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -663,13 +669,15 @@ int median_g2(symnmf_t h, double *out) {
   return SYMNMF_OK;
 }
 
-int apply_reset(symnmf_t h, const symnmf_hparams *hp) {
-  CK(launch_reset(h->A, h->g, h->dmed, (float)hp->c, h->n, h->k, h->kp, h->slots, h->stream));
+// Piecewise reset of columns c0 .. c0 + kw - 1 with the median in dmed;
+// *sumA_post = the sum of the reset entries
+int reset_columns(symnmf_t h, const symnmf_hparams *hp, int c0, int kw, double *sumA_post) {
+  CK(launch_reset(h->A, h->g, h->dmed, (float)hp->c, h->n, c0, kw, h->kp, h->slots, h->stream));
   CK(launch_sum_slot(h->slots, h->ntiles, 2, h->dsum, h->stream));
   count_kernels(h, 2);
   CK(cudaMemcpyAsync(h->hsum, h->dsum, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  h->ctrl.sumA_post = h->hsum[0];
+  *sumA_post = h->hsum[0];
   return SYMNMF_OK;
 }
 
@@ -718,44 +726,72 @@ void reset_restart_checks(symnmf_t h) {
   h->rconv.assign(h->restarts, 0);
 }
 
-// Per-restart AND rule at check t (restarts > 1): H_t is in the other H
+// Per-restart checks at check t (restarts > 1): H_t is in the other H
 // buffer (the step has flipped cur) and g holds its gradient; the Gram of
 // H_t is block diagonal.  f_r = ||S||^2 - ||Gram_rr||^2 + sum(H_r .* g_r) / 2,
 // E_r = f_r / ||S||^2, kkt_r = ||grad_proj,r|| / (n kb).  Sets *any when a
 // restart meets Eq. 11 (E0 and the stagnation test per restart, as for a
-// handle of its own).
-int restart_checks(symnmf_t h, const symnmf_hparams *hp, int64_t t, bool *any) {
+// handle of its own).  Piecewise AdaGrad (appendix, Family 3) decides and
+// applies its reset per restart as ctrl_check does for a handle, on the
+// restart's E_r, kkt_r, sum(A_r) and the median of g_r^2 over its own n kb
+// entries; no restart resets at a check where the handle stops.
+int restart_checks(symnmf_t h, const symnmf_hparams *hp, int64_t t, bool stopping, bool *any,
+                   bool *any_reset) {
   *any = false;
+  *any_reset = false;
   const int R = h->restarts, kp = h->kp, kb = h->k / R;
   const int prev = 1 - h->cur;
-  CK(launch_restart_stats(h->H[prev], h->g, h->n, h->k, kp, R, h->rs_part, h->rs_out, h->stream));
-  CK(cudaMemcpyAsync(h->rs_host, h->rs_out, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost,
+  constexpr int Q = kRestartSums;
+  CK(launch_restart_stats(h->H[prev], h->g, h->A, h->n, h->k, kp, R, h->rs_part, h->rs_out,
+                          h->stream));
+  CK(cudaMemcpyAsync(h->rs_host, h->rs_out, sizeof(double) * Q * R, cudaMemcpyDeviceToHost,
                      h->stream));
-  CK(cudaMemcpyAsync(h->rs_host + 2 * R, h->gram64[prev], sizeof(double) * kp * kp,
+  CK(cudaMemcpyAsync(h->rs_host + Q * R, h->gram64[prev], sizeof(double) * kp * kp,
                      cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   count_kernels(h, 2);
-  const double *G = h->rs_host + 2 * R;
+  const double *G = h->rs_host + Q * R;
   const double tau_g = hp->tau_g > 0 ? hp->tau_g : 1e-4 * std::max(1.0, 1e4 / (double)h->n);
+  bool stag[8];
   for (int r = 0; r < R; ++r) {
     double g2 = 0.0;
     for (int c = r * kb; c < (r + 1) * kb; ++c)
       for (int d = r * kb; d < (r + 1) * kb; ++d) g2 += G[c * kp + d] * G[c * kp + d];
-    const double f = h->normS2 - g2 + 0.5 * h->rs_host[2 * r];
+    const double f = h->normS2 - g2 + 0.5 * h->rs_host[Q * r];
     const double E = f / h->normS2;
-    const double kkt = std::sqrt(h->rs_host[2 * r + 1]) / ((double)h->n * (double)kb);
+    const double kkt = std::sqrt(h->rs_host[Q * r + 1]) / ((double)h->n * (double)kb);
     symnmf_ctx::RestartCtl &c = h->rctl[r];
     if (t == 0 || !(c.E0 == c.E0)) c.E0 = E;
     const double ratio = c.have_prev ? (c.E_prev - E) / c.E0 : NAN;
-    const bool stag = c.have_prev && t >= hp->warmup && ratio < hp->tau_stag;
+    stag[r] = c.have_prev && t >= hp->warmup && ratio < hp->tau_stag;
     c.E_prev = E;
     c.have_prev = true;
     h->rE[r] = E;
     h->rkkt[r] = kkt;
-    if (E < hp->tau_E && kkt < tau_g && stag) {
+    if (E < hp->tau_E && kkt < tau_g && stag[r]) {
       h->rconv[r] = 1;
       *any = true;
     }
+  }
+  if (hp->method != SYMNMF_PIECEWISE_ADAGRAD || *any || stopping) return SYMNMF_OK;
+  for (int r = 0; r < R; ++r) {
+    symnmf_ctx::RestartCtl &c = h->rctl[r];
+    const double E = h->rE[r], sumA = h->rs_host[Q * r + 2];
+    if (c.cooldown && sumA >= 2.0 * c.sumA_post) c.cooldown = false;
+    if (c.cooldown || !c.resets_enabled || !stag[r] || !(h->rkkt[r] > hp->c_r * tau_g)) continue;
+    double med = NAN;
+    int rc = median_g2(h, r * kb, kb, &med);
+    if (rc) return rc;
+    if (!(med > hp->eps)) continue;
+    if (c.resets > 0 && !(E < c.E_at_reset - hp->tau_stag * c.E0)) {
+      c.resets_enabled = false;
+      continue;
+    }
+    if ((rc = reset_columns(h, hp, r * kb, kb, &c.sumA_post))) return rc;
+    c.cooldown = true;
+    c.E_at_reset = E;
+    c.resets += 1;
+    *any_reset = true;
   }
   return SYMNMF_OK;
 }
@@ -775,15 +811,20 @@ int iterate_finish(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &ph
     int mrc = SYMNMF_OK;
     auto med = [&]() {
       double m = NAN;
-      mrc = median_g2(h, &m);
+      mrc = median_g2(h, 0, h->k, &m);
       return m;
     };
-    ctrl_check(&h->ctrl, hp, h->n, t, rec.E, rec.kkt, rec.sumA, med, &o);
+    // with restarts concatenated the Piecewise reset is each restart's own
+    // (restart_checks); the handle's check keeps the AND rule
+    symnmf_hparams hpc = *hp;
+    if (h->restarts > 1 && hpc.method == SYMNMF_PIECEWISE_ADAGRAD) hpc.method = SYMNMF_ADAGRAD;
+    ctrl_check(&h->ctrl, &hpc, h->n, t, rec.E, rec.kkt, rec.sumA, med, &o);
     if (mrc) return mrc;
+    bool restart_reset = false;
     if (h->restarts > 1) {
       // a concatenated handle stops when any of its restarts converges
       bool any = false;
-      if ((rc = restart_checks(h, hp, t, &any))) return rc;
+      if ((rc = restart_checks(h, hp, t, o.converged, &any, &restart_reset))) return rc;
       if (any && !o.converged) {
         o.converged = true;
         o.reset = false;
@@ -794,14 +835,14 @@ int iterate_finish(symnmf_t h, const symnmf_hparams *hp, std::vector<double> &ph
     rec.median_g2 = o.median;
     rec.stag_ratio = o.ratio;
     rec.converged = o.converged ? 1 : 0;
-    rec.reset = o.reset ? 1 : 0;
+    rec.reset = (o.reset || restart_reset) ? 1 : 0;
     h->last_check = t;
     h->last_check_rec = rec;
     if (o.converged) {
       h->cur = 1 - h->cur;  // the certified iterate is H_t (its buffers are intact)
       return SYMNMF_CONVERGED;
     }
-    if (o.reset && (rc = apply_reset(h, hp))) return rc;
+    if (o.reset && (rc = reset_columns(h, hp, 0, h->k, &h->ctrl.sumA_post))) return rc;
   } else if (t + 1 - h->copied_upto >= kRing / 2) {
     if ((rc = finish_records(h, t + 1, phis))) return rc;
     phis.clear();
@@ -995,6 +1036,20 @@ int symnmf_quantize_fp8(const void *src, int32_t src_dtype, int64_t rows, int64_
   return e == cudaSuccess ? SYMNMF_OK : SYMNMF_ERR_CUDA;
 }
 
+int symnmf_get_restart_ctrl(symnmf_t h, int32_t count, int32_t *resets, int32_t *resets_enabled,
+                            int32_t *cooldown, double *sumA_post) {
+  if (!h || count < h->restarts) return SYMNMF_ERR_INVALID;
+  for (int r = 0; r < h->restarts; ++r) {
+    const bool have = h->restarts > 1 && r < (int)h->rctl.size();
+    const symnmf_ctx::RestartCtl c = have ? h->rctl[r] : symnmf_ctx::RestartCtl{};
+    if (resets) resets[r] = have ? c.resets : h->ctrl.resets;
+    if (resets_enabled) resets_enabled[r] = have ? (c.resets_enabled ? 1 : 0) : h->ctrl.resets_enabled;
+    if (cooldown) cooldown[r] = have ? (c.cooldown ? 1 : 0) : h->ctrl.cooldown;
+    if (sumA_post) sumA_post[r] = have ? c.sumA_post : h->ctrl.sumA_post;
+  }
+  return SYMNMF_OK;
+}
+
 int symnmf_get_restart_stats(symnmf_t h, int32_t count, double *E, double *kkt,
                              int32_t *converged) {
   if (!h || count < h->restarts) return SYMNMF_ERR_INVALID;
@@ -1092,10 +1147,10 @@ int symnmf_window_update(symnmf_t h, const float *Y, int64_t T, int64_t ldy, int
 int symnmf_set_restarts(symnmf_t h, int32_t restarts) {
   if (!h || restarts < 1 || restarts > 8 || h->k % restarts != 0) return SYMNMF_ERR_INVALID;
   if (restarts > 1 && !h->rs_part) {
-    cudaError_t e = dalloc(&h->rs_part, (size_t)h->ntiles * 16);
-    if (e == cudaSuccess) e = dalloc(&h->rs_out, 16);
+    cudaError_t e = dalloc(&h->rs_part, (size_t)h->ntiles * kRestartSums * 8);
+    if (e == cudaSuccess) e = dalloc(&h->rs_out, kRestartSums * 8);
     if (e == cudaSuccess)
-      e = cudaMallocHost((void **)&h->rs_host, sizeof(double) * (16 + 64 * 64));
+      e = cudaMallocHost((void **)&h->rs_host, sizeof(double) * (kRestartSums * 8 + 64 * 64));
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(h, SYMNMF_ERR_OOM, "restart check scratch");

@@ -457,21 +457,22 @@ __global__ void unpack_kernel(const float *src, float *dst, int64_t n, int k, in
   dst[e] = src[r * kp + c];
 }
 
-// radix select of the lower median of g^2 (FP32 bit patterns of non-negative
-// floats order like unsigned integers); three passes of 11, 11, 10 bits
-__global__ void __launch_bounds__(256) hist_kernel(const float *g, int64_t n, int k, int kp,
-                                                   int shift, int nbits, const unsigned *sel,
-                                                   unsigned *hist) {
+// radix select of the lower median of g^2 over columns c0 .. c0 + kw - 1
+// (FP32 bit patterns of non-negative floats order like unsigned integers);
+// three passes of 11, 11, 10 bits
+__global__ void __launch_bounds__(256) hist_kernel(const float *g, int64_t n, int c0, int kw,
+                                                   int kp, int shift, int nbits,
+                                                   const unsigned *sel, unsigned *hist) {
   __shared__ unsigned sh[2048];
   const int nb = 1 << nbits;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0u;
   __syncthreads();
   const unsigned mask = sel[0], val = sel[1];
-  const int64_t total = n * k;
+  const int64_t total = n * kw;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / k;
-    const int c = (int)(e % k);
+    const int64_t r = e / kw;
+    const int c = c0 + (int)(e % kw);
     const float x = g[r * kp + c];
     const float x2 = x * x;
     const unsigned u = __float_as_uint(x2);
@@ -510,9 +511,12 @@ __global__ void init_sel_kernel(unsigned *sel, unsigned rank, unsigned *hist) {
   for (int i = threadIdx.x; i < 2048; i += blockDim.x) hist[i] = 0u;
 }
 
+// A = c max(g^2, median) on columns c0 .. c0 + kw - 1; slot 2 of each tile
+// gets the tile's sum of the reset entries
 template <int KP>
 __global__ void __launch_bounds__(256) reset_kernel(float *A, const float *g, const float *med,
-                                                    float c, int64_t n, int k, double *slots) {
+                                                    float c, int64_t n, int c0, int kw,
+                                                    double *slots) {
   __shared__ double red[40];
   const int tile = blockIdx.x;
   const int64_t r0 = (int64_t)tile * kTileRows;
@@ -521,7 +525,7 @@ __global__ void __launch_bounds__(256) reset_kernel(float *A, const float *g, co
   float s = 0.f;
   for (int e = threadIdx.x; e < kTileRows * KP; e += blockDim.x) {
     const int r = e / KP, cc = e % KP;
-    if (r < rows && cc < k) {
+    if (r < rows && cc >= c0 && cc < c0 + kw) {
       const int64_t gi = (r0 + r) * KP + cc;
       const float x = g[gi];
       const float v = c * fmaxf(x * x, m);
@@ -664,25 +668,25 @@ cudaError_t launch_unpack(const float *src, float *dst, int64_t n, int k, int kp
   return cudaGetLastError();
 }
 
-cudaError_t launch_median_g2(const float *g, int64_t n, int k, int kp, unsigned *hist,
+cudaError_t launch_median_g2(const float *g, int64_t n, int c0, int kw, int kp, unsigned *hist,
                              unsigned *sel, float *out, cudaStream_t s) {
-  const int64_t total = n * k;
+  const int64_t total = n * kw;
   const unsigned rank = (unsigned)((total - 1) / 2);
   init_sel_kernel<<<1, 256, 0, s>>>(sel, rank, hist);
   const int grid = (int)std::min<int64_t>(1024, (total + 255) / 256);
   const int shifts[3] = {21, 10, 0};
   const int bits[3] = {11, 11, 10};
   for (int p = 0; p < 3; ++p) {
-    hist_kernel<<<grid, 256, 0, s>>>(g, n, k, kp, shifts[p], bits[p], sel, hist);
+    hist_kernel<<<grid, 256, 0, s>>>(g, n, c0, kw, kp, shifts[p], bits[p], sel, hist);
     select_kernel<<<1, 1, 0, s>>>(hist, shifts[p], bits[p], sel, out, p == 2);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_reset(float *A, const float *g, const float *med, float c, int64_t n, int k,
-                         int kp, double *slots, cudaStream_t s) {
+cudaError_t launch_reset(float *A, const float *g, const float *med, float c, int64_t n, int c0,
+                         int kw, int kp, double *slots, cudaStream_t s) {
   const int ntiles = (int)((n + kTileRows - 1) / kTileRows);
-  KP_SWITCH(kp, reset_kernel<KPV><<<ntiles, 256, 0, s>>>(A, g, med, c, n, k, slots));
+  KP_SWITCH(kp, reset_kernel<KPV><<<ntiles, 256, 0, s>>>(A, g, med, c, n, c0, kw, slots));
   return cudaGetLastError();
 }
 

@@ -188,13 +188,14 @@ cudaError_t launch_norm_s2(const void *S, int64_t n, int64_t lds, int dtype, con
 // n x k (pitch k) <-> n x kp (pitch kp, pads zeroed)
 cudaError_t launch_pack(const float *src, float *dst, int64_t n, int k, int kp, cudaStream_t s);
 cudaError_t launch_unpack(const float *src, float *dst, int64_t n, int k, int kp, cudaStream_t s);
-// lower median of g^2 over the n x k valid entries (radix select on the
-// FP32 bit patterns); result in *out (device)
-cudaError_t launch_median_g2(const float *g, int64_t n, int k, int kp, unsigned *hist,
+// lower median of g^2 over the n x kw entries in columns c0 .. c0 + kw - 1
+// (radix select on the FP32 bit patterns); result in *out (device)
+cudaError_t launch_median_g2(const float *g, int64_t n, int c0, int kw, int kp, unsigned *hist,
                              unsigned *sel, float *out, cudaStream_t s);
-// Piecewise reset: A = c * max(g^2, med); per-tile sum(A) into slots[.][2]
-cudaError_t launch_reset(float *A, const float *g, const float *med, float c, int64_t n, int k,
-                         int kp, double *slots, cudaStream_t s);
+// Piecewise reset of columns c0 .. c0 + kw - 1: A = c * max(g^2, med);
+// per-tile sum of those entries of A into slots[.][2]
+cudaError_t launch_reset(float *A, const float *g, const float *med, float c, int64_t n, int c0,
+                         int kw, int kp, double *slots, cudaStream_t s);
 // per-tile power-of-two scaled E4M3 codes of a rows x cols FP32 / BF16 matrix
 cudaError_t launch_quantize_fp8(const void *src, int src_dtype, int64_t rows, int64_t cols,
                                 int64_t ld_src, uint8_t *q, int64_t ldq, float *scales,

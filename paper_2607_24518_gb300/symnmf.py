@@ -81,6 +81,7 @@ def _load():
         "symnmf_set_matrix": [vp, vp, i64, vp, i64],
         "symnmf_set_restarts": [vp, i32],
         "symnmf_get_restart_stats": [vp, i32, P(dbl), P(dbl), P(i32)],
+        "symnmf_get_restart_ctrl": [vp, i32, P(i32), P(i32), P(i32), P(dbl)],
         "symnmf_selftest_wait_timeout": [dbl],
         "symnmf_objective_noalloc": [vp, i64, i64, i32, vp, i64, vp, i32, dbl, vp, vp],
         "symnmf_objective_noalloc_check": [i64, i64, i32, i32, i64, i32, P(C.c_size_t)],
@@ -144,6 +145,7 @@ DECLARED = [
     "symnmf_spkmeans",
     "symnmf_build_dependence", "symnmf_set_matrix", "symnmf_set_restarts",
     "symnmf_get_restart_stats", "symnmf_selftest_wait_timeout", "symnmf_window_update",
+    "symnmf_get_restart_ctrl",
 ]
 
 NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -264,6 +266,17 @@ def symnmf_get_restart_stats(h, count):
     cv = (C.c_int32 * count)()
     _check(LIB.symnmf_get_restart_stats(h, count, E, kkt, cv), h)
     return list(E), list(kkt), list(cv)
+
+
+def symnmf_get_restart_ctrl(h, count):
+    """Per-restart Piecewise reset state: (resets, resets_enabled, cooldown,
+    sumA_post) lists."""
+    rs = (C.c_int32 * count)()
+    en = (C.c_int32 * count)()
+    cd = (C.c_int32 * count)()
+    sp = (C.c_double * count)()
+    _check(LIB.symnmf_get_restart_ctrl(h, count, rs, en, cd, sp), h)
+    return list(rs), list(en), list(cd), list(sp)
 
 
 def symnmf_set_matrix(h, S, lds, scales=None, ld_scales=0):

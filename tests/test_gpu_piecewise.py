@@ -218,3 +218,55 @@ def test_free_running_reset_and_disable(L):
         assert L.symnmf_get_trace(h)[-1].reset == 0
     finally:
         L.symnmf_destroy(h)
+
+
+def test_joint_restarts_reset_on_their_own(L):
+    """Three Piecewise restarts of the n=256, k=4 TPDM (seed 3; c_r = 1)
+    concatenated in one handle of rank 12, from the starts of seeds 3, 7
+    and 10.  Solved alone by the oracle, restart 0 resets at iteration 520,
+    restart 1 at 480 and restart 2 never (within 530).  The joint handle
+    must reset each restart at its own iteration, leave the others'
+    accumulators alone, and disable a restart's resets when the oracle does."""
+    n, kb, seeds = 256, 4, (3, 7, 10)
+    R = len(seeds)
+    inst = gen.tpdm_groups(n=n, groups=kb, T=1024, q=0.05, seed=3)
+    S_t = to_dev(inst.S)
+    S64 = S_t.double().cpu().numpy()
+    H0 = np.concatenate([gen.init_scaled(float(S64.mean()), n, kb, seed=sd).astype(np.float32)
+                         for sd in seeds], axis=1)
+    hp = O.HParams.paper(O.PIECEWISE)
+    hp.c_r = 1.0
+    sols = [O.Solver(S64, H0[:, r * kb:(r + 1) * kb].astype(np.float64), hp) for r in range(R)]
+    lhp = L.symnmf_hparams_default(L.PIECEWISE_ADAGRAD, c_r=1.0)
+    h = L.symnmf_create(S_t, n, R * kb, L.F32)
+    try:
+        L.symnmf_set_restarts(h, R)
+        L.symnmf_set_H(h, to_dev(H0))
+        done = 0
+        # A is compared where no reset's large step lies more than one
+        # iteration back: after one the trajectories separate at the FP32
+        # rounding level amplified (0.7% in A 40 iterations after 480)
+        stages = ((481, [0, 1, 0], (0, 1, 2)), (521, [1, 1, 0], (0, 2)), (531, None, ()))
+        for upto, resets, cmpA in stages:
+            L.symnmf_step(h, lhp, upto - done)
+            for s in sols:
+                while s.ctrl.t < upto:
+                    s.step()
+            done = upto
+            rs, en, cd, sp = L.symnmf_get_restart_ctrl(h, R)
+            assert rs == [s.ctrl.resets for s in sols], (upto, rs)
+            if resets is not None:
+                assert rs == resets
+            assert en == [int(s.ctrl.resets_enabled) for s in sols], (upto, en)
+            assert cd == [int(s.ctrl.cooldown) for s in sols], (upto, cd)
+            for r, s in enumerate(sols):
+                if s.ctrl.resets:
+                    assert abs(sp[r] - s.ctrl.sumA_post) <= 1e-3 * s.ctrl.sumA_post, (upto, r)
+            A = get(L, h, n, R * kb, L.BUF_ACC).astype(np.float64)
+            for r in cmpA:
+                assert O.rel_err(A[:, r * kb:(r + 1) * kb], sols[r].A) < 1e-3, (upto, r)
+        tr = L.symnmf_get_trace(h)
+        assert [rec.t for rec in tr if rec.reset] == [480, 520]
+        assert L.symnmf_get_ctrl(h).resets == 0          # the handle's own controller
+    finally:
+        L.symnmf_destroy(h)

@@ -165,3 +165,59 @@ def test_joint_handle_stops_with_its_first_converged_restart(L):
     assert stj == L.CONVERGED and cv == [1, 0]
     assert sj.iter == s1.iter
     assert E[0] < 1e-3
+
+
+def test_batch_of_joint_handles_matches_the_oracle(L):
+    """Three instances stepped together by symnmf_batch_step, each on its
+    own handle and stream: k = 8 with four restarts concatenated (Piecewise
+    AdaGrad), k = 32 with two (AdaGrad), k = 64 alone (RMSprop).  Every
+    restart's column block is compared with the FP64 oracle solving that
+    restart alone from the same start, and each handle's E trace with the
+    mean of its restarts' oracle E."""
+    from oracle import symnmf_oracle as O
+    specs = [(384, 8, 4, O.PIECEWISE, 31), (520, 32, 2, O.ADAGRAD, 32), (300, 64, 1, O.RMSPROP, 33)]
+    iters = 40
+    hs, hps, refs, streams, mats = [], [], [], [], []   # the handles do not own S
+    try:
+        for n, k, R, method, seed in specs:
+            inst = gen.tpdm_groups(n=n, groups=min(k, 16), T=2000, q=0.05, seed=seed)
+            S = torch.tensor(inst.S, dtype=torch.float32, device=DEV)
+            S64 = S.double().cpu().numpy()
+            mats.append(S)
+            rng = np.random.default_rng(seed)
+            H0 = rng.uniform(0.0, np.sqrt(float(S64.mean()) / k), size=(n, R * k)).astype(np.float32)
+            st = torch.cuda.Stream(DEV)
+            h = L.symnmf_create(S, n, R * k, L.F32)
+            hs.append(h)
+            streams.append(st)
+            L.symnmf_set_stream(h, st)
+            if R > 1:
+                L.symnmf_set_restarts(h, R)
+            L.symnmf_set_H(h, torch.tensor(H0, device=DEV))
+            hps.append(L.symnmf_hparams_default(method))
+            sols = []
+            for r in range(R):
+                s = O.Solver(S64, H0[:, r * k:(r + 1) * k].astype(np.float64), O.HParams.paper(method))
+                s.run(iters)
+                sols.append(s)
+            refs.append((n, k, R, sols))
+        L.symnmf_batch_step(hs, hps, iters)
+        torch.cuda.synchronize()
+        for h, (n, k, R, sols) in zip(hs, refs):
+            Hg = _get(L, h, n, R * k).astype(np.float64)
+            for r, s in enumerate(sols):
+                assert O.rel_err(Hg[:, r * k:(r + 1) * k], s.H) < 1e-4, (k, r)
+            Eg = np.array([rec.E for rec in L.symnmf_get_trace(h)])
+            Er = np.mean(np.array([[rec.E for rec in s.records] for s in sols]), axis=0)
+            assert len(Eg) == len(Er) == iters
+            full = ~np.isnan(Eg)
+            assert full.any() and np.array_equal(full, ~np.isnan(Er))
+            # E = 1 - (2 tr(H^T S H) - ||H^T H||^2) / ||S||^2 near a fit: both
+            # terms are about ||S||^2 and carry the FP32 product's relative
+            # error (up to about 1e-6 at k = 64), so E holds to a few 1e-6
+            # (relative once E > 1, as after Piecewise's first large step)
+            err = np.abs(Eg[full] - Er[full]) / np.maximum(1.0, np.abs(Er[full]))
+            assert np.max(err) < 4e-6, (k, float(np.max(err)))
+    finally:
+        for h in hs:
+            L.symnmf_destroy(h)
