@@ -47,11 +47,13 @@ __device__ __forceinline__ float e4m3_tile_scale(float amax) {
   if (e < -100) e = -100;
   return ldexpf(1.f, e);
 }
-// two-piece E4M3 form of h at tile factor d: h ~ d (hi + lo / 16)
+// two-piece E4M3 form of h at tile factor d: h ~ d (hi + lo), hi the
+// E4M3 value of h / d and lo that of the remainder h / d - hi (exact in
+// FP32), both rounded to nearest even
 __device__ __forceinline__ void e4m3_pieces(float h, float inv_d, uint8_t &hi, uint8_t &lo) {
   const float x = h * inv_d;
   hi = e4m3_bits(x);
-  lo = e4m3_bits(16.f * (x - e4m3_val(hi)));
+  lo = e4m3_bits(x - e4m3_val(hi));
 }
 
 // CTA of a stream-K launch whose unit range [b W / G, (b+1) W / G) holds x

@@ -36,8 +36,9 @@
 //         lo parts
 //   FP8   kind::f8f6f4 on the E4M3 codes of S against H as two E4M3 pieces
 //         per entry at a power-of-two factor d per 128-row tile,
-//         H ~ d (hi + lo / 16); S's tile scale over d is applied per unit
-//         when the folders fold
+//         H ~ d (hi + lo); from kp = 16 up the two pieces go through two
+//         MMAs of N = kp into one accumulator; S's tile scale over d is
+//         applied per unit when the folders fold
 // Work: the row-major list of (row tile, 128-column tile) units is split
 // into equal contiguous ranges, one per CTA (stream-K), so every SM streams
 // the same number of S bytes.  A tile whose units span several CTAs is
@@ -93,7 +94,12 @@ struct Cfg {
   // S_lo (in TMEM) and a bf16 copy of H (N2 rows, zero past kp)
   static constexpr bool SLO16 = F32 && KP <= 32;
   static constexpr int N2 = SLO16 ? (KP < 16 ? 16 : KP) : 0;
-  static constexpr int N = 2 * KP;
+  static constexpr int N = 2 * KP;  // rows of the staged B: [H_hi | H_lo]
+  // FP8 from kp = 16: S H_hi and S H_lo accumulate into one accumulator
+  // (two MMAs of N = kp); kp = 8 keeps one MMA of N = 16 (M = 128 needs N
+  // a multiple of 16) and adds the two parts when folding
+  static constexpr bool JOIN = F8 && KP >= 16;
+  static constexpr int NA = JOIN ? KP : N;  // accumulator columns of the main product
   static constexpr int ATOM_COLS = F32 ? 32 : F8 ? 128 : 64;  // elements per 128-byte row
   static constexpr int APS = (KP == 64 || F8) ? 1 : 2;    // swizzle atoms per stage
   static constexpr int SPU = 128 / (APS * ATOM_COLS);    // stages per 128-column unit
@@ -137,7 +143,7 @@ struct Cfg {
   static constexpr int NABUF = SLO16 ? STAGES : F32 ? 2 : 1;
   static constexpr int NL = SLO16 ? N2 : 0;
   static constexpr uint32_t ACC0 = F32 ? NABUF * ABUF : 0u;
-  static constexpr uint32_t ACCW = N + NL;                // columns per accumulator buffer
+  static constexpr uint32_t ACCW = NA + NL;               // columns per accumulator buffer
   static constexpr uint32_t PB0 = ACC0 + 2 * ACCW;        // double-buffered P rows
   // kp = 64: the folders keep the running sum of a tile segment in tensor
   // memory (PA) instead of 64 registers per thread, which the 128-register
@@ -1139,7 +1145,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
     const uint32_t tb = tmem_base + lane_off + C::ACC0 + (uint32_t)acc * C::ACCW;
     // CW columns of each accumulator part per round: all of a round's
     // loads are in flight before its one wait
-    constexpr int NPART = 2 + (C::NL > 0 ? 1 : 0);
+    constexpr int NPART = (C::JOIN ? 1 : 2) + (C::NL > 0 ? 1 : 0);
     constexpr int CW = (KP < C::FOLD_CW) ? KP : C::FOLD_CW;
     if constexpr (C::PTMEM) {
       // columns [0, NP): p += this chain, 16 columns per round
@@ -1149,15 +1155,17 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
 #pragma unroll
         for (int u = 0; u < 16; u += 8) {
           tmem_ld8_nw(tb + cc + u, x, u);
-          tmem_ld8_nw(tb + KP + cc + u, x, 16 + u);
+          if constexpr (!C::JOIN) tmem_ld8_nw(tb + KP + cc + u, x, 16 + u);
           if constexpr (C::NL > 0) tmem_ld8_nw(tb + C::N + cc + u, x, 32 + u);
         }
         tmem_wait_ld_all(x);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           float v;
-          if constexpr (C::F8) {
-            v = fmaf(__uint_as_float(x[16 + j]), 0.0625f, __uint_as_float(x[j])) * sc;
+          if constexpr (C::JOIN) {
+            v = __uint_as_float(x[j]) * sc;
+          } else if constexpr (C::F8) {
+            v = (__uint_as_float(x[j]) + __uint_as_float(x[16 + j])) * sc;
           } else {
             v = __uint_as_float(x[j]) + __uint_as_float(x[16 + j]);
           }
@@ -1172,7 +1180,7 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
 #pragma unroll
         for (int u = 0; u < 16; u += 8) {
           tmem_ld8_nw(tb + cc + u, x, u);
-          tmem_ld8_nw(tb + KP + cc + u, x, 16 + u);
+          if constexpr (!C::JOIN) tmem_ld8_nw(tb + KP + cc + u, x, 16 + u);
           if constexpr (C::NL > 0) tmem_ld8_nw(tb + C::N + cc + u, x, 32 + u);
           if (!pa_first) tmem_ld8_nw(tpa + (cc - NP) + u, x, NPART * 16 + u);
         }
@@ -1181,8 +1189,10 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           float v;
-          if constexpr (C::F8) {
-            v = fmaf(__uint_as_float(x[16 + j]), 0.0625f, __uint_as_float(x[j])) * sc;
+          if constexpr (C::JOIN) {
+            v = __uint_as_float(x[j]) * sc;
+          } else if constexpr (C::F8) {
+            v = (__uint_as_float(x[j]) + __uint_as_float(x[16 + j])) * sc;
           } else {
             v = __uint_as_float(x[j]) + __uint_as_float(x[16 + j]);
           }
@@ -1199,8 +1209,9 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
       uint32_t x[NPART * CW];
 #pragma unroll
       for (int u = 0; u < CW; u += 8) {
-        tmem_ld8_nw(tb + cc + u, x, u);                 // [H_hi] part
-        tmem_ld8_nw(tb + KP + cc + u, x, CW + u);       // [H_lo] part
+        tmem_ld8_nw(tb + cc + u, x, u);                 // [H_hi] part (FP8 from kp = 16: the sum)
+        if constexpr (!C::JOIN)
+          tmem_ld8_nw(tb + KP + cc + u, x, CW + u);     // [H_lo] part
         if constexpr (C::NL > 0)                        // S_lo bf16(H)
           tmem_ld8_nw(tb + C::N + cc + u, x, 2 * CW + u);
       }
@@ -1208,8 +1219,10 @@ __device__ void folder_role(const TcArgs &a, uint32_t tmem_base, uint8_t *smem, 
 #pragma unroll
       for (int j = 0; j < CW; ++j) {
         float v;
-        if constexpr (C::F8) {
-          v = fmaf(__uint_as_float(x[CW + j]), 0.0625f, __uint_as_float(x[j])) * sc;
+        if constexpr (C::JOIN) {
+          v = __uint_as_float(x[j]) * sc;
+        } else if constexpr (C::F8) {
+          v = (__uint_as_float(x[j]) + __uint_as_float(x[CW + j])) * sc;
         } else {
           v = __uint_as_float(x[j]) + __uint_as_float(x[CW + j]);
         }
@@ -1334,7 +1347,8 @@ __device__ __noinline__ void mma_role(const TcArgs &a, const Segs &sg, uint8_t *
   constexpr int N = C::N;
   constexpr int FOLD = C::FOLD;
   constexpr uint32_t idesc =
-      C::F32 ? idesc_tf32(128, N) : C::F8 ? idesc_e4m3(128, N) : idesc_bf16(128, N);
+      C::F32 ? idesc_tf32(128, N) : C::F8 ? idesc_e4m3(128, C::NA) : idesc_bf16(128, N);
+  constexpr uint64_t kLoD = (uint64_t)(KP * 128) >> 4;  // H_lo rows of the staged B
   // descriptor units are 16 bytes; stage, atom and 32-byte K-slice offsets
   constexpr uint64_t kStageD = C::STAGE >> 4, kAtomD = kAtomBytes >> 4, kBAtomD = C::B_ATOM >> 4;
   const uint64_t ad_base = sdesc(smem_u32(smem));
@@ -1378,9 +1392,14 @@ __device__ __noinline__ void mma_role(const TcArgs &a, const Segs &sg, uint8_t *
         const uint64_t adj = ad + (uint64_t)(j >> 2) * kAtomD + off;
         const uint64_t bdj = bd + (uint64_t)(j >> 2) * kBAtomD + off;
         const uint32_t accum = (j == 0) ? first : 1u;
-        if constexpr (C::F32) mma_tf32_ss(d, adj, bdj, idesc, accum);
-        else if constexpr (C::F8) mma_e4m3(d, adj, bdj, idesc, accum);
-        else mma_bf16(d, adj, bdj, idesc, accum);
+        if constexpr (C::F32) {
+          mma_tf32_ss(d, adj, bdj, idesc, accum);
+        } else if constexpr (C::F8) {
+          mma_e4m3(d, adj, bdj, idesc, accum);
+          if constexpr (C::JOIN) mma_e4m3(d, adj, bdj + kLoD, idesc, 1u);
+        } else {
+          mma_bf16(d, adj, bdj, idesc, accum);
+        }
       }
       if constexpr (C::F32) {
         // S_lo H once the converter warps have stored S_lo in TMEM: as
