@@ -198,6 +198,23 @@ int symnmf_get_impl(symnmf_t h, int32_t *impl);
 int symnmf_set_H(symnmf_t h, const float *H);
 /* Copy the current factor to H (device, FP32, n x k). */
 int symnmf_get_H(symnmf_t h, float *H);
+/* One solve from host memory, the call for data that lives on the host:
+ * copies S (host, n rows of row pitch lds_host elements of the handle's
+ * storage type; FP8: also its tile scales, host, ceil(n/128) rows of pitch
+ * ld_scales_host) into the device buffers the handle was created on, which
+ * it overwrites; takes normS2 > 0 as ||S||^2, else computes it from the
+ * copied S as symnmf_create does; copies H_0 (host, n x k row-major FP32)
+ * and starts from it as symnmf_set_H; runs up to iters iterations as
+ * symnmf_step (stats: host, may be NULL); copies the final H (the certified
+ * iterate on convergence) to H_out (host, n x k).  Pinned host buffers make
+ * the copies asynchronous DMA on the handle's stream; pageable ones are
+ * staged by the driver.  Synchronises before returning.  Returns OK or
+ * CONVERGED.  Errors: INVALID for a null pointer, iters < 0, lds_host < n,
+ * or FP8 without scales (host, or set on the handle) or with ld_scales_host
+ * < ceil(n/128); otherwise those of symnmf_step. */
+int symnmf_solve_host(symnmf_t h, const void *S_host, int64_t lds_host, const float *scales_host,
+                      int64_t ld_scales_host, double normS2, const float *H0_host,
+                      const symnmf_hparams *hp, int32_t iters, float *H_out, symnmf_stats *stats);
 /* Read / write one handle buffer (enum symnmf_buffer) from / to device
  * memory (FP32 n x k).  Writing SYMNMF_BUF_H replaces H_t without touching
  * the optimizer state (teacher forcing); SYMNMF_BUF_GRAD is read-only. */

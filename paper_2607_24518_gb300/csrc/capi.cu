@@ -1220,6 +1220,47 @@ int symnmf_get_H(symnmf_t h, float *H) {
   return SYMNMF_OK;
 }
 
+int symnmf_solve_host(symnmf_t h, const void *S_host, int64_t lds_host, const float *scales_host,
+                      int64_t ld_scales_host, double normS2, const float *H0_host,
+                      const symnmf_hparams *hp, int32_t iters, float *H_out, symnmf_stats *stats) {
+  if (!h || !S_host || !H0_host || !H_out || !hp || iters < 0 || lds_host < h->n)
+    return SYMNMF_ERR_INVALID;
+  const bool f8 = (h->dtype == SYMNMF_FP8E4M3);
+  const int64_t nt = (h->n + kTileRows - 1) / kTileRows;
+  if (f8 && (!scales_host || !h->scales || ld_scales_host < nt)) return SYMNMF_ERR_INVALID;
+  const size_t es = esize(h->dtype);
+  // the device buffer the handle was created on (and its FP8 scales) take
+  // the caller's matrix; H_0 goes through the staging buffer
+  if (lds_host == h->lds) {
+    // one contiguous copy: a pitched copy of 2D rows moves far fewer bytes
+    // per second from pinned memory
+    const size_t bytes = ((size_t)(h->n - 1) * (size_t)h->lds + (size_t)h->n) * es;
+    CK(cudaMemcpyAsync(const_cast<void *>(h->S), S_host, bytes, cudaMemcpyHostToDevice,
+                       h->stream));
+  } else {
+    CK(cudaMemcpy2DAsync(const_cast<void *>(h->S), (size_t)h->lds * es, S_host,
+                         (size_t)lds_host * es, (size_t)h->n * es, (size_t)h->n,
+                         cudaMemcpyHostToDevice, h->stream));
+  }
+  if (f8)
+    CK(cudaMemcpy2DAsync(const_cast<float *>(h->scales), (size_t)h->ld_scales * 4, scales_host,
+                         (size_t)ld_scales_host * 4, (size_t)nt * 4, (size_t)nt,
+                         cudaMemcpyHostToDevice, h->stream));
+  const size_t nk = sizeof(float) * (size_t)h->n * (size_t)h->k;
+  CK(cudaMemcpyAsync(h->tmp, H0_host, nk, cudaMemcpyHostToDevice, h->stream));
+  int rc;
+  if (normS2 > 0 && std::isfinite(normS2)) h->normS2 = normS2;
+  else if ((rc = compute_norm(h))) return rc;
+  if ((rc = symnmf_set_H(h, h->tmp))) return rc;
+  symnmf_stats st{};
+  const int src = symnmf_step(h, hp, iters, stats ? stats : &st);
+  if (src < 0) return src;
+  CK(launch_unpack(h->H[h->cur], h->tmp, h->n, h->k, h->kp, h->stream));
+  CK(cudaMemcpyAsync(H_out, h->tmp, nk, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return src;
+}
+
 int symnmf_get_buffer(symnmf_t h, int32_t which, float *dst) {
   if (!h || !dst) return SYMNMF_ERR_INVALID;
   const float *src = which == SYMNMF_BUF_H ? h->H[h->cur]

@@ -82,6 +82,8 @@ def _load():
         "symnmf_set_restarts": [vp, i32],
         "symnmf_get_restart_stats": [vp, i32, P(dbl), P(dbl), P(i32)],
         "symnmf_get_restart_ctrl": [vp, i32, P(i32), P(i32), P(i32), P(dbl)],
+        "symnmf_solve_host": [vp, vp, i64, vp, i64, dbl, vp, P(symnmf_hparams), i32, vp,
+                              P(symnmf_stats)],
         "symnmf_selftest_wait_timeout": [dbl],
         "symnmf_objective_noalloc": [vp, i64, i64, i32, vp, i64, vp, i32, dbl, vp, vp],
         "symnmf_objective_noalloc_check": [i64, i64, i32, i32, i64, i32, P(C.c_size_t)],
@@ -145,7 +147,7 @@ DECLARED = [
     "symnmf_spkmeans",
     "symnmf_build_dependence", "symnmf_set_matrix", "symnmf_set_restarts",
     "symnmf_get_restart_stats", "symnmf_selftest_wait_timeout", "symnmf_window_update",
-    "symnmf_get_restart_ctrl",
+    "symnmf_get_restart_ctrl", "symnmf_solve_host",
 ]
 
 NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -359,6 +361,17 @@ def symnmf_hparams_default(method, **overrides):
 def symnmf_step(h, hp, iters):
     st = symnmf_stats()
     status = _check(LIB.symnmf_step(h, C.byref(hp), iters, C.byref(st)), h)
+    return status, st
+
+
+def symnmf_solve_host(h, S_host, lds_host, H0_host, hp, iters, H_out, scales_host=None,
+                      ld_scales_host=0, normS2=float("nan")):
+    """One solve from host memory (CPU tensors, pinned for asynchronous
+    copies): S and H_0 in, the final H out; returns (status, stats)."""
+    st = symnmf_stats()
+    status = _check(LIB.symnmf_solve_host(h, _ptr(S_host), lds_host, _ptr(scales_host),
+                                          ld_scales_host, normS2, _ptr(H0_host), C.byref(hp),
+                                          iters, _ptr(H_out), C.byref(st)), h)
     return status, st
 
 

@@ -218,6 +218,44 @@ def test_block_svrg_list_cases(L, case, n, k, br, phi):
         assert eg < REL_FP32, eg
 
 
+@pytest.mark.parametrize("dt,pinned", [("f32", True), ("bf16", False)])
+def test_solve_host_matches_the_device_calls(L, dt, pinned):
+    """symnmf_solve_host from host buffers (pinned or pageable) gives the
+    same H, bit for bit, as symnmf_set_H, symnmf_step and symnmf_get_H on a
+    handle over the same S in device memory; it overwrites the device
+    buffer its handle was created on and computes ||S||^2 from it."""
+    n, k, iters = 700, 8, 30
+    tdt, ldt = (torch.float32, L.F32) if dt == "f32" else (torch.bfloat16, L.BF16)
+    S_t, _, H0_t, _ = problem(n, k, seed=14, dtype=tdt)
+    hp = L.symnmf_hparams_default(L.ADAGRAD)
+    with Handle(L, S_t, n, k, ldt) as hd:
+        L.symnmf_set_H(hd.h, H0_t)
+        st_dev, stats_dev = L.symnmf_step(hd.h, hp, iters)
+        H_dev = hd.get()
+        norm_dev = L.symnmf_get_norm(hd.h)
+    S_host, H0_host = S_t.cpu(), H0_t.cpu()
+    H_out = torch.empty(n, k, dtype=torch.float32)
+    if pinned:
+        S_host, H0_host, H_out = S_host.pin_memory(), H0_host.pin_memory(), H_out.pin_memory()
+    S_buf = torch.zeros_like(S_t)
+    h = L.symnmf_create(S_buf, n, k, ldt)
+    try:
+        st, stats = L.symnmf_solve_host(h, S_host, n, H0_host, hp, iters, H_out)
+        assert st == st_dev and stats.iter == stats_dev.iter
+        assert torch.equal(S_buf, S_t)
+        assert L.symnmf_get_norm(h) == norm_dev
+        assert np.array_equal(H_out.numpy(), H_dev)
+        for bad in (dict(S_host=None), dict(lds_host=n - 1), dict(iters=-1)):
+            args = dict(S_host=S_host, lds_host=n, iters=iters)
+            args.update(bad)
+            with pytest.raises(L.SymNMFError) as e:
+                L.symnmf_solve_host(h, args["S_host"], args["lds_host"], H0_host, hp,
+                                    args["iters"], H_out)
+            assert e.value.status == L.ERR_INVALID
+    finally:
+        L.symnmf_destroy(h)
+
+
 def test_free_running_adagrad_n512(L):
     """The n=512, k=8 planted correlation workload: 500 AdaGrad iterations
     from H0 ~ U[0, 0.1] (seed 0), eta = 2.0 and 0.1, against the oracle."""
