@@ -496,7 +496,7 @@ int run_iteration(symnmf_t h, const symnmf_hparams *hp, int64_t t, bool need_g) 
       e.ncols1 = ly.ncols;
     }
   } else {
-    int *hl, *dl;
+    int *hl = nullptr, *dl = nullptr;
     if ((rc = stage_slot(h, t, &hl, &dl))) return rc;
     const int nt = h->ntiles;
     int *hI = hl, *hJ = hl + nt, *hposI = hl + 2 * nt, *hposJ = hl + 3 * nt;
