@@ -256,6 +256,38 @@ def test_solve_host_matches_the_device_calls(L, dt, pinned):
         L.symnmf_destroy(h)
 
 
+def test_solve_host_fp8_with_tile_scales(L):
+    """FP8 storage: symnmf_solve_host also uploads the tile scales (host
+    pitch nt) into the handle's scale buffer; H equals the device calls'
+    bit for bit."""
+    n, k, iters = 700, 16, 20
+    ldq, nt = 704, (700 + 127) // 128
+    S_t, _, H0_t, _ = problem(n, k, seed=15)
+    q = torch.zeros(n, ldq, dtype=torch.uint8, device=DEV)
+    sc = torch.zeros(nt, nt, dtype=torch.float32, device=DEV)
+    L.symnmf_quantize_fp8(S_t, L.F32, n, n, n, q, ldq, sc, nt, None)
+    hp = L.symnmf_hparams_default(L.ADAGRAD)
+    with Handle(L, q, n, k, L.FP8E4M3, lds=ldq) as hd:
+        L.symnmf_set_tile_scales(hd.h, sc, nt)
+        L.symnmf_set_H(hd.h, H0_t)
+        L.symnmf_step(hd.h, hp, iters)
+        H_dev = hd.get()
+    q_buf, sc_buf = torch.zeros_like(q), torch.ones_like(sc)
+    h = L.symnmf_create_ld(q_buf, n, ldq, k, L.FP8E4M3)
+    try:
+        L.symnmf_set_tile_scales(h, sc_buf, nt)
+        H_out = torch.empty(n, k, dtype=torch.float32).pin_memory()
+        L.symnmf_solve_host(h, q.cpu().pin_memory(), ldq, H0_t.cpu().pin_memory(), hp, iters,
+                            H_out, sc.cpu().pin_memory(), nt)
+        assert torch.equal(q_buf, q) and torch.equal(sc_buf, sc)
+        assert np.array_equal(H_out.numpy(), H_dev)
+        with pytest.raises(L.SymNMFError) as e:   # FP8 without host scales
+            L.symnmf_solve_host(h, q.cpu(), ldq, H0_t.cpu(), hp, iters, H_out)
+        assert e.value.status == L.ERR_INVALID
+    finally:
+        L.symnmf_destroy(h)
+
+
 def test_free_running_adagrad_n512(L):
     """The n=512, k=8 planted correlation workload: 500 AdaGrad iterations
     from H0 ~ U[0, 0.1] (seed 0), eta = 2.0 and 0.1, against the oracle."""
