@@ -1220,14 +1220,14 @@ int symnmf_get_H(symnmf_t h, float *H) {
   return SYMNMF_OK;
 }
 
-int symnmf_solve_host(symnmf_t h, const void *S_host, int64_t lds_host, const float *scales_host,
-                      int64_t ld_scales_host, double normS2, const float *H0_host,
-                      const symnmf_hparams *hp, int32_t iters, float *H_out, symnmf_stats *stats) {
-  if (!h || !S_host || !H0_host || !H_out || !hp || iters < 0 || lds_host < h->n)
-    return SYMNMF_ERR_INVALID;
+// symnmf_solve_host after its argument checks: the uploads, the solve and
+// the copy of H back (see the header)
+static int solve_host_run(symnmf_t h, const void *S_host, int64_t lds_host,
+                          const float *scales_host, int64_t ld_scales_host, double normS2,
+                          const float *H0_host, const symnmf_hparams *hp, int32_t iters,
+                          float *H_out, symnmf_stats *stats) {
   const bool f8 = (h->dtype == SYMNMF_FP8E4M3);
   const int64_t nt = (h->n + kTileRows - 1) / kTileRows;
-  if (f8 && (!scales_host || !h->scales || ld_scales_host < nt)) return SYMNMF_ERR_INVALID;
   const size_t es = esize(h->dtype);
   // the device buffer the handle was created on (and its FP8 scales) take
   // the caller's matrix; H_0 goes through the staging buffer
@@ -1259,6 +1259,21 @@ int symnmf_solve_host(symnmf_t h, const void *S_host, int64_t lds_host, const fl
   CK(cudaMemcpyAsync(H_out, h->tmp, nk, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return src;
+}
+
+int symnmf_solve_host(symnmf_t h, const void *S_host, int64_t lds_host, const float *scales_host,
+                      int64_t ld_scales_host, double normS2, const float *H0_host,
+                      const symnmf_hparams *hp, int32_t iters, float *H_out, symnmf_stats *stats) {
+  if (!h || !S_host || !H0_host || !H_out || !hp || iters < 0 || lds_host < h->n)
+    return SYMNMF_ERR_INVALID;
+  const int64_t nt = (h->n + kTileRows - 1) / kTileRows;
+  if (h->dtype == SYMNMF_FP8E4M3 && (!scales_host || !h->scales || ld_scales_host < nt))
+    return SYMNMF_ERR_INVALID;
+  const int rc = solve_host_run(h, S_host, lds_host, scales_host, ld_scales_host, normS2, H0_host,
+                                hp, iters, H_out, stats);
+  // on an error no copy may still be reading the caller's host buffers
+  if (rc < 0) cudaStreamSynchronize(h->stream);
+  return rc;
 }
 
 int symnmf_get_buffer(symnmf_t h, int32_t which, float *dst) {
