@@ -2,6 +2,7 @@
 include/symnmf.h is exported, argument errors are reported before any CUDA
 call, and the host-side pure functions (SplitMix64 sampling, controller)
 agree with the oracle on the same inputs."""
+import ctypes
 import math
 import os
 import re
@@ -74,9 +75,15 @@ def test_next_row_argument_errors_without_gpu(L):
         with pytest.raises(L.SymNMFError) as e:
             L.symnmf_build_dependence(*args)
         assert e.value.status == L.ERR_INVALID, args
+    hp = L.symnmf_hparams_default(L.ADAGRAD)
+    st = L.symnmf_stats()
     for fn, args in ((L.LIB.symnmf_spkmeans, (None, None, None, 1, 1e-4, None, None)),
                      (L.LIB.symnmf_set_matrix, (None, None, 64, None, 0)),
-                     (L.LIB.symnmf_set_restarts, (None, 2))):
+                     (L.LIB.symnmf_set_restarts, (None, 2)),
+                     (L.LIB.symnmf_window_update, (None, None, 10, 64, 1, None, 64, None, 0)),
+                     (L.LIB.symnmf_get_restart_ctrl, (None, 2, None, None, None, None)),
+                     (L.LIB.symnmf_solve_host, (None, Y, 64, None, 0, 0.0, Y, ctypes.byref(hp), 1,
+                                                Y, ctypes.byref(st)))):
         assert fn(*args) == L.ERR_INVALID
 
 
